@@ -1,0 +1,75 @@
+"""Flexible GMRES (oracle).
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring.
+
+The paper wraps its multigrid cycle in flexible GMRES (Sec. 3.1, Sec. 4.2),
+right-preconditioned, from a zero initial guess, stopping on the relative
+residual.  Readings (also in the design notes):
+  K1  Orthogonalisation is classical Gram-Schmidt applied twice (the paper is
+      silent); the least-squares problem is reduced with Givens rotations.
+  K2  Inside a cycle the stop test uses the Givens residual estimate
+      |g_{j+1}| / |b|; at the end of every cycle the residual b - A x is
+      recomputed explicitly and the solve stops when it meets the tolerance
+      or the iteration budget is spent.
+  K3  A cycle ends after `restart` iterations, on convergence of the
+      estimate, on an exact breakdown, or when the budget is spent.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .multigrid import back_substitution, cgs2, givens
+
+
+def fgmres(A, b, precond, x0=None, tol=1e-8, restart=20, maxit=500):
+    """Solve A x = b.  Returns (x, iterations, final relative residual, history).
+
+    `history` holds the estimate |g_{j+1}|/|b| after every iteration.
+    """
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros(n, dtype=np.complex128), 0, 0.0, []
+    history = []
+    its = 0
+    r = b - A @ x
+    beta = np.linalg.norm(r)
+    while beta > tol * bnorm and its < maxit:
+        V = np.zeros((n, restart + 1), dtype=np.complex128)
+        Z = np.zeros((n, restart), dtype=np.complex128)
+        H = np.zeros((restart + 1, restart), dtype=np.complex128)
+        cs = np.zeros(restart)
+        sn = np.zeros(restart, dtype=np.complex128)
+        g = np.zeros(restart + 1, dtype=np.complex128)
+        V[:, 0] = r / beta
+        g[0] = beta
+        k = 0
+        for j in range(restart):
+            Z[:, j] = precond(V[:, j])
+            w = A @ Z[:, j]
+            hcol, w = cgs2(V[:, : j + 1], w)
+            H[: j + 1, j] = hcol
+            H[j + 1, j] = np.linalg.norm(w)
+            for i in range(j):
+                a, bb = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * a + sn[i] * bb
+                H[i + 1, j] = -np.conj(sn[i]) * a + cs[i] * bb
+            hn = H[j + 1, j].real
+            cs[j], sn[j], H[j, j] = givens(H[j, j], H[j + 1, j])
+            H[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(sn[j]) * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            k = j + 1
+            history.append(abs(g[j + 1]) / bnorm)
+            if hn == 0.0:
+                break
+            V[:, j + 1] = w / hn
+            if abs(g[j + 1]) <= tol * bnorm or its >= maxit:
+                break
+        y = back_substitution(H[:k, :k], g[:k])
+        x = x + Z[:, :k] @ y
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+    return x, its, beta / bnorm, history
