@@ -1,0 +1,226 @@
+/*
+ * adr.h -- C ABI of the GB300 amplitude solver for the point-source Helmholtz
+ * equation (Treister & Haber, "A multigrid solver to the Helmholtz equation
+ * with a point source based on travel time and amplitude").
+ *
+ * The library solves the complex advection-diffusion-reaction (ADR) equation
+ * for the amplitude a (Eq. ADR, paper sign convention u = a exp(-i w tau),
+ * Eq. new_u):
+ *     Delta a - 2 i w grad(tau).grad(a) - i w (Delta tau) a
+ *             - w^2 (|grad tau|^2 - kappa^2) a - i w gamma kappa^2 a = q_hat
+ * discretised with the second-order upwind advection of Eq. londUpwindDiff
+ * (the matrix H_2up of Eq. ADRLinSystemUpwind), by flexible GMRES
+ * preconditioned with a geometric multigrid cycle on
+ * (1 - beta) H_2up + beta H_1up (Eq. precADRup) whose coarse operators are
+ * Galerkin products P^T A P (Eq. coarseGridMatrix).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grids are nodal, dim = 2 or 3, n[d] nodes along axis d (axis 0 fastest,
+ *   the last axis is depth), spacing h[d].  Node (i0, i1[, i2]) is element
+ *   i0 + n0*(i1 + n1*i2) of every array.  Every n[d] must be >= 4.
+ * - Real arrays are float64.  Complex arrays are interleaved (re, im) pairs
+ *   of float64 (precision ADR_F64, same layout as torch.complex128) or of
+ *   float32 (ADR_F32, torch.complex64).
+ * - Unless an entry point says "host", every array argument is a DEVICE
+ *   pointer on the device that was current when the operator was created,
+ *   allocated and owned by the caller; the library never frees it and keeps
+ *   no reference to it after the call returns.
+ * - The library owns the operator's hierarchy and workspace (one device
+ *   arena per operator), released by adr_operator_destroy.
+ * - Work is issued on the stream given at creation; calls return after the
+ *   stream has been synchronised only where documented (adr_solve reads one
+ *   residual estimate per iteration).
+ * - Every entry point returns ADR_OK or a negative ADR_ERR_* code; the text
+ *   of the most recent error of the calling thread is kept for
+ *   adr_last_error.  Invalid arguments are rejected before any device work.
+ */
+#ifndef ADR_H_
+#define ADR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADR_OK 0
+#define ADR_ERR_ARG (-1)            /* invalid argument (null, size, range) */
+#define ADR_ERR_CUDA (-2)           /* a CUDA runtime call failed */
+#define ADR_ERR_OOM (-3)            /* device allocation failed */
+#define ADR_ERR_NOT_CONVERGED (-4)  /* iteration budget spent above tolerance */
+#define ADR_ERR_NAN (-5)            /* NaN or Inf met in a Krylov scalar */
+#define ADR_ERR_STATE (-6)          /* operation not valid for this operator */
+
+#define ADR_F64 0
+#define ADR_F32 1
+
+/* Discrete operators on the finest grid. */
+#define ADR_SCHEME_2UP 0   /* H_2up, Eq. ADRLinSystemUpwind (the solved system) */
+#define ADR_SCHEME_1UP 1   /* H_1up, Eq. 1up */
+#define ADR_SCHEME_CEN 2   /* H_cen, Eq. ADRLinSystemCentral */
+#define ADR_SCHEME_PREC 3  /* (1 - beta) H_2up + beta H_1up, Eq. precADRup */
+
+/* Multigrid cycle shape (Sec. 3: Alg. TwoGrid applied recursively, Alg. Kcycle). */
+#define ADR_CYCLE_V 0
+#define ADR_CYCLE_K 1
+
+/* Relaxation (Sec. 3.1). */
+#define ADR_RELAX_JACOBI 0  /* damped Jacobi with the fixed weight jacobi_weight[l] */
+#define ADR_RELAX_MR 1      /* one step of Jacobi-preconditioned GMRES per sweep:
+                               Jacobi with the minimal-residual complex weight */
+
+#define ADR_MAX_LEVELS 8
+
+typedef struct adr_params {
+  int levels;                          /* maximum number of grid levels (>= 1) */
+  double beta;                         /* blend of Eq. precADRup */
+  int cycle;                           /* ADR_CYCLE_V or ADR_CYCLE_K */
+  int relax;                           /* ADR_RELAX_JACOBI or ADR_RELAX_MR */
+  int pre_sweeps[ADR_MAX_LEVELS];      /* relaxations before restriction, per level */
+  int post_sweeps[ADR_MAX_LEVELS];     /* relaxations after the correction, per level */
+  double jacobi_weight[ADR_MAX_LEVELS];/* ADR_RELAX_JACOBI weight per level */
+  int coarse_iterations;               /* fixed Jacobi-GMRES steps on the coarsest grid */
+  int kcycle_iterations;               /* inner FGMRES steps of the K-cycle */
+  int restart;                         /* outer FGMRES restart length m (1..64) */
+  int precond_precision;               /* ADR_F64 or ADR_F32: arithmetic of the cycle */
+  int near_source;                     /* rows within this Chebyshev distance of the
+                                          source use central advection (Sec. 2.2 says
+                                          "distance of one node"; 1..4, default 1) */
+} adr_params_t;
+
+typedef struct adr_level_info {
+  int n[3];            /* nodes per axis (n[2] = 1 in 2D) */
+  int64_t nodes;
+  int stencil_points;  /* 0 on the finest level (matrix-free), 21 (2D) or 81 (3D) */
+} adr_level_info_t;
+
+typedef struct adr_op_info {
+  int dim;
+  int levels;
+  adr_level_info_t level[ADR_MAX_LEVELS];
+  int64_t arena_bytes;     /* device bytes owned by the operator */
+} adr_op_info_t;
+
+typedef struct adr_solve_info {
+  int iterations;          /* outer FGMRES iterations performed */
+  int restarts;            /* completed restart cycles */
+  double rel_residual;     /* |q - H_2up a| / |q|, recomputed explicitly at exit */
+  double rel_estimate;     /* last Givens estimate |g_{j+1}| / |q| */
+  int status;              /* ADR_OK, ADR_ERR_NOT_CONVERGED or ADR_ERR_NAN */
+} adr_solve_info_t;
+
+typedef struct adr_op_s* adr_op_t;
+
+/* Fills *p with the defaults: 5 levels, beta = 0.25 (Sec. 4.2), K-cycle with
+ * ADR_RELAX_MR, l+1 pre/post relaxations on level l counted from 1 (Sec. 4.2),
+ * 10 coarsest-grid iterations (Sec. 4.2), 2 inner K-cycle steps (Alg. Kcycle),
+ * restart 20, FP32 cycle.  Returns ADR_ERR_ARG if p is NULL. */
+int adr_params_default(adr_params_t* p);
+
+/* Builds the operator for one point source (Sec. 2.1 coefficients,
+ * Eq. travel_time_coeff; Sec. 3 hierarchy, Eq. coarseGridMatrix).
+ *   kappa, tau1, gamma: device float64[N], slowness, travel-time factor
+ *       (tau = |x - x0| * tau1) and absorbing-layer profile; read during the
+ *       call only.
+ *   src: node index per axis of the source x0 (inside the grid).
+ *   omega > 0: angular frequency.  params: NULL selects the defaults.
+ *   stream: cudaStream_t used for all work of this operator (NULL = legacy
+ *       default stream).
+ * On success *out receives a handle to destroy with adr_operator_destroy.
+ * Errors: ADR_ERR_ARG for bad sizes/pointers/parameters, ADR_ERR_OOM,
+ * ADR_ERR_CUDA. */
+int adr_operator_create(int dim, const int* n, const double* h, const int* src, double omega,
+                        const double* kappa, const double* tau1, const double* gamma,
+                        const adr_params_t* params, void* stream, adr_op_t* out);
+
+/* Rebuilds the coefficients and the whole Galerkin hierarchy of an existing
+ * operator for a new source, frequency and medium on the same grid, inside
+ * the operator's arena (no allocation, no synchronisation).  Arguments as in
+ * adr_operator_create.  Errors: ADR_ERR_ARG, ADR_ERR_CUDA. */
+int adr_operator_update(adr_op_t op, const int* src, double omega, const double* kappa, const double* tau1,
+                        const double* gamma);
+
+/* Releases the operator and its device arena (after synchronising its stream). */
+int adr_operator_destroy(adr_op_t op);
+
+/* Describes the hierarchy built for op. */
+int adr_operator_info(adr_op_t op, adr_op_info_t* info);
+
+/* Copies the fine-level coefficients (Eq. travel_time_coeff and the reaction
+ * term of Eq. ADR) to the device float64 array out of (2*dim + 3) * N values:
+ * d_d tau for each axis, d_dd tau for each axis, Re rho, Im rho, tau. */
+int adr_coefficients(adr_op_t op, double* out);
+
+/* y = A x on the finest grid for scheme ADR_SCHEME_* (Eqs. ADR, londDiff,
+ * londUpwindDiff, 1up, precADRup), complex vectors of N entries in the given
+ * precision (ADR_F32 uses the float32 copies of the coefficients). */
+int adr_apply(adr_op_t op, int scheme, int precision, const void* x, void* y);
+
+/* Copies the Galerkin stencil of level l >= 1 (precision of the cycle) to the
+ * device array out: stencil_points * nodes complex values, point-major
+ * (entry for point p of node j at p * nodes + j).  Point p enumerates the
+ * offsets (o0, o1[, o2]) in [-2, 2]^dim with at most one |o_d| = 2, axis 0
+ * fastest, in lexicographic order of (o_{dim-1}, ..., o0). */
+int adr_level_stencil(adr_op_t op, int level, void* out);
+
+/* One application of the multigrid preconditioner: z = B^{-1} r on the
+ * finest grid (complex, precision of the cycle).  z may not alias r. */
+int adr_vcycle(adr_op_t op, const void* r, void* z);
+
+/* q_hat = delta_{x0} / prod(h) (float64 complex, N entries, Sec. 4.1). */
+int adr_point_source_rhs(adr_op_t op, void* q);
+
+/* Solves H_2up a = rhs by right-preconditioned flexible GMRES(m).
+ *   rhs: float64 complex device vector, or NULL for the point source.
+ *   a: float64 complex device vector; input initial guess if use_x0 != 0,
+ *      output solution.
+ *   Stops when |rhs - H_2up a| / |rhs| <= tol (checked on the Givens estimate
+ *   inside a cycle and explicitly at the end of each cycle) or after maxit
+ *   iterations (then ADR_ERR_NOT_CONVERGED, a still holds the iterate).
+ *   info may be NULL. */
+int adr_solve(adr_op_t op, const void* rhs, void* a, int use_x0, double tol, int maxit,
+              adr_solve_info_t* info);
+
+/* u = a exp(-i w tau) (Eq. new_u), float64 complex device vectors. */
+int adr_reconstruct(adr_op_t op, const void* a, void* u);
+
+/* The whole pipeline on HOST buffers: copies kappa, tau1, gamma (host
+ * float64[N]) to the device, builds the operator, solves for the point
+ * source from a zero guess, reconstructs u, and copies u (and a, if not
+ * NULL) back to host float64 complex arrays of N entries.  Host buffers may
+ * be pageable or pinned.  The operator is destroyed before returning. */
+int adr_solve_host(int dim, const int* n, const double* h, const int* src, double omega,
+                   const double* kappa, const double* tau1, const double* gamma,
+                   const adr_params_t* params, double tol, int maxit, void* stream,
+                   double* u_host, double* a_host, adr_solve_info_t* info);
+
+/* Travel-time factor for the point source at node src (input preparation,
+ * not part of the solve): tau1 (device float64[N], output) with
+ * tau = |x - x0| * tau1 solving the first-order upwind (Godunov)
+ * discretisation of the factored eikonal equation
+ * |tau0 grad tau1 + tau1 grad tau0|^2 = kappa^2 (Eq. factoredEikonal),
+ * relaxed in place on the device until no node changes (at most max_sweeps
+ * sweeps; *sweeps_done, if not NULL, receives the count).  kappa: device
+ * float64[N] slowness.  Returns ADR_ERR_NOT_CONVERGED if max_sweeps was
+ * reached while values still changed, ADR_ERR_ARG / ADR_ERR_OOM /
+ * ADR_ERR_CUDA on failure.  Allocates (and frees) one int of device memory. */
+int adr_traveltime(int dim, const int* n, const double* h, const int* src, const double* kappa, double* tau1,
+                   int max_sweeps, void* stream, int* sweeps_done);
+
+/* Number of CUDA kernels the library has launched since it was loaded (all
+ * threads, all operators); an instrumentation counter, never reset. */
+long long adr_kernel_launches(void);
+
+/* Text of the calling thread's most recent error ("" if none). */
+const char* adr_last_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* adr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADR_H_ */

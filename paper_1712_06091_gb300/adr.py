@@ -1,0 +1,242 @@
+"""Python binding of libadr: same operations as include/adr.h, argument marshalling only.
+
+Device memory and streams come from PyTorch; every computation runs in the
+library's CUDA kernels.  Complex vectors are torch.complex128 (float64 path)
+or torch.complex64 (float32 cycle), flat with N = prod(n) entries, axis 0
+fastest.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+ADRError = L.ADRError
+
+
+def default_params(**overrides) -> L.Params:
+    """adr_params_t with the library defaults, then `overrides` applied.
+
+    Per-level lists (pre_sweeps, post_sweeps, jacobi_weight) may be given as
+    Python sequences; cycle in {'V', 'K'}, relax in {'jacobi', 'mr'},
+    precision in {'f64', 'f32'}.
+    """
+    p = L.Params()
+    L.check(L.load().adr_params_default(ctypes.byref(p)))
+    for key, val in overrides.items():
+        if key == "cycle":
+            p.cycle = L.CYCLES[val] if isinstance(val, str) else int(val)
+        elif key == "relax":
+            p.relax = L.RELAX[val] if isinstance(val, str) else int(val)
+        elif key in ("precision", "precond_precision"):
+            p.precond_precision = {"f64": L.ADR_F64, "f32": L.ADR_F32}.get(val, val)
+        elif key in ("pre_sweeps", "post_sweeps", "jacobi_weight"):
+            arr = getattr(p, key)
+            vals = list(val) if hasattr(val, "__len__") else [val] * L.MAX_LEVELS
+            for k in range(L.MAX_LEVELS):
+                arr[k] = vals[min(k, len(vals) - 1)]
+        elif key == "sweeps":
+            vals = list(val) if hasattr(val, "__len__") else [val] * L.MAX_LEVELS
+            for k in range(L.MAX_LEVELS):
+                p.pre_sweeps[k] = p.post_sweeps[k] = vals[min(k, len(vals) - 1)]
+        else:
+            setattr(p, key, val)
+    return p
+
+
+def params_dict(p: L.Params) -> dict:
+    return {
+        "levels": p.levels, "beta": p.beta, "cycle": "VK"[p.cycle], "relax": ["jacobi", "mr"][p.relax],
+        "pre_sweeps": list(p.pre_sweeps), "post_sweeps": list(p.post_sweeps),
+        "jacobi_weight": list(p.jacobi_weight), "coarse_iterations": p.coarse_iterations,
+        "kcycle_iterations": p.kcycle_iterations, "restart": p.restart,
+        "precision": ["f64", "f32"][p.precond_precision],
+    }
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_real(x, N, device):
+    t = torch.as_tensor(x, dtype=torch.float64, device=device).reshape(-1).contiguous()
+    if t.numel() != N:
+        raise ValueError(f"expected {N} values, got {t.numel()}")
+    return t
+
+
+class Operator:
+    """H_2up and its multigrid hierarchy for one point source (adr_operator_create)."""
+
+    def __init__(self, n, h, src, omega, kappa, tau1, gamma, params=None, device="cuda", stream=None):
+        self._lib = L.load()
+        self.dim = len(n)
+        self.n = tuple(int(v) for v in n)
+        self.h = tuple(float(v) for v in h)
+        self.src = tuple(int(v) for v in src)
+        self.omega = float(omega)
+        self.N = int(np.prod(self.n))
+        self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.params = params if params is not None else default_params()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        k = _dev_real(kappa, self.N, self.device)
+        t = _dev_real(tau1, self.N, self.device)
+        g = _dev_real(gamma, self.N, self.device)
+        nn = (ctypes.c_int * 3)(*self.n, *([1] * (3 - self.dim)))
+        hh = (ctypes.c_double * 3)(*self.h, *([1.0] * (3 - self.dim)))
+        ss = (ctypes.c_int * 3)(*self.src, *([0] * (3 - self.dim)))
+        handle = ctypes.c_void_p()
+        L.check(self._lib.adr_operator_create(self.dim, nn, hh, ss, self.omega, _ptr(k), _ptr(t), _ptr(g),
+                                              ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream),
+                                              ctypes.byref(handle)))
+        self._h = handle
+        self.cycle_dtype = torch.complex128 if self.params.precond_precision == L.ADR_F64 else torch.complex64
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            L.check(self._lib.adr_operator_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def update(self, src, omega, kappa, tau1, gamma):
+        """adr_operator_update: new source / frequency / medium, same grid and arena."""
+        k = _dev_real(kappa, self.N, self.device)
+        t = _dev_real(tau1, self.N, self.device)
+        g = _dev_real(gamma, self.N, self.device)
+        ss = (ctypes.c_int * 3)(*src, *([0] * (3 - self.dim)))
+        L.check(self._lib.adr_operator_update(self._h, ss, float(omega), _ptr(k), _ptr(t), _ptr(g)))
+        self.src = tuple(int(v) for v in src)
+        self.omega = float(omega)
+
+    # -- queries ----------------------------------------------------------
+    def info(self) -> dict:
+        i = L.OpInfo()
+        L.check(self._lib.adr_operator_info(self._h, ctypes.byref(i)))
+        levels = [{"n": tuple(i.level[l].n[: self.dim]), "nodes": i.level[l].nodes,
+                   "stencil_points": i.level[l].stencil_points} for l in range(i.levels)]
+        return {"dim": i.dim, "levels": levels, "arena_bytes": i.arena_bytes}
+
+    def coefficients(self) -> torch.Tensor:
+        """(2*dim + 3, N) float64: d tau per axis, d^2 tau per axis, Re rho, Im rho, tau."""
+        out = torch.empty((2 * self.dim + 3, self.N), dtype=torch.float64, device=self.device)
+        L.check(self._lib.adr_coefficients(self._h, _ptr(out)))
+        return out
+
+    def level_stencil(self, level) -> torch.Tensor:
+        info = self.info()["levels"][level]
+        out = torch.empty((info["stencil_points"], info["nodes"]), dtype=self.cycle_dtype, device=self.device)
+        L.check(self._lib.adr_level_stencil(self._h, int(level), _ptr(out)))
+        return out
+
+    # -- operations -------------------------------------------------------
+    def _vec(self, x, dtype):
+        if x.dtype != dtype or x.device != self.device or not x.is_contiguous() or x.numel() != self.N:
+            raise ValueError(f"expected a contiguous {dtype} tensor of {self.N} entries on {self.device}")
+        return x
+
+    def apply(self, x, scheme="2up"):
+        prec = L.ADR_F64 if x.dtype == torch.complex128 else L.ADR_F32
+        x = self._vec(x.reshape(-1), x.dtype)
+        y = torch.empty_like(x)
+        L.check(self._lib.adr_apply(self._h, L.SCHEMES[scheme], prec, _ptr(x), _ptr(y)))
+        return y
+
+    def vcycle(self, r):
+        r = self._vec(r.reshape(-1), self.cycle_dtype)
+        z = torch.empty_like(r)
+        L.check(self._lib.adr_vcycle(self._h, _ptr(r), _ptr(z)))
+        return z
+
+    def point_source_rhs(self):
+        q = torch.empty(self.N, dtype=torch.complex128, device=self.device)
+        L.check(self._lib.adr_point_source_rhs(self._h, _ptr(q)))
+        return q
+
+    def solve(self, rhs=None, x0=None, tol=1e-8, maxit=500, out=None, raise_on_fail=True):
+        """(a, info dict).  rhs=None solves for the point source."""
+        a = out if out is not None else torch.empty(self.N, dtype=torch.complex128, device=self.device)
+        self._vec(a, torch.complex128)
+        if x0 is not None:
+            a.copy_(x0.reshape(-1))
+        rp = ctypes.c_void_p(0) if rhs is None else _ptr(self._vec(rhs.reshape(-1), torch.complex128))
+        info = L.SolveInfo()
+        rc = self._lib.adr_solve(self._h, rp, _ptr(a), 1 if x0 is not None else 0, float(tol), int(maxit),
+                                 ctypes.byref(info))
+        allow = () if raise_on_fail else (L.ADR_ERR_NOT_CONVERGED,)
+        L.check(rc, allow)
+        return a, {"iterations": info.iterations, "restarts": info.restarts, "rel_residual": info.rel_residual,
+                   "rel_estimate": info.rel_estimate, "status": info.status}
+
+    def reconstruct(self, a):
+        a = self._vec(a.reshape(-1), torch.complex128)
+        u = torch.empty_like(a)
+        L.check(self._lib.adr_reconstruct(self._h, _ptr(a), _ptr(u)))
+        return u
+
+
+def kernel_launches() -> int:
+    """adr_kernel_launches: kernels launched by the library so far."""
+    return int(L.load().adr_kernel_launches())
+
+
+def traveltime(n, h, src, kappa, max_sweeps=None, device="cuda", stream=None):
+    """adr_traveltime: device float64 tau1 for slowness `kappa` (first-order factored eikonal)."""
+    lib = L.load()
+    dim = len(n)
+    N = int(np.prod(n))
+    k = _dev_real(kappa, N, torch.device(device))
+    tau1 = torch.empty(N, dtype=torch.float64, device=k.device)
+    nn = (ctypes.c_int * 3)(*n, *([1] * (3 - dim)))
+    hh = (ctypes.c_double * 3)(*h, *([1.0] * (3 - dim)))
+    ss = (ctypes.c_int * 3)(*src, *([0] * (3 - dim)))
+    st = stream if stream is not None else torch.cuda.current_stream(k.device)
+    sweeps = ctypes.c_int(0)
+    limit = max_sweeps if max_sweeps is not None else 8 * sum(n) + 64
+    L.check(lib.adr_traveltime(dim, nn, hh, ss, _ptr(k), _ptr(tau1), int(limit), ctypes.c_void_p(st.cuda_stream),
+                               ctypes.byref(sweeps)))
+    return tau1, sweeps.value
+
+
+def solve_host(n, h, src, omega, kappa, tau1, gamma, params=None, tol=1e-8, maxit=500, stream=None,
+               want_amplitude=False):
+    """adr_solve_host: host numpy arrays in, host complex128 u (and a) out."""
+    lib = L.load()
+    dim = len(n)
+    N = int(np.prod(n))
+    k = np.ascontiguousarray(kappa, dtype=np.float64).reshape(-1)
+    t = np.ascontiguousarray(tau1, dtype=np.float64).reshape(-1)
+    g = np.ascontiguousarray(gamma, dtype=np.float64).reshape(-1)
+    u = np.empty(N, dtype=np.complex128)
+    a = np.empty(N, dtype=np.complex128) if want_amplitude else None
+    p = params if params is not None else default_params()
+    nn = (ctypes.c_int * 3)(*n, *([1] * (3 - dim)))
+    hh = (ctypes.c_double * 3)(*h, *([1.0] * (3 - dim)))
+    ss = (ctypes.c_int * 3)(*src, *([0] * (3 - dim)))
+    st = ctypes.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    info = L.SolveInfo()
+    rc = lib.adr_solve_host(dim, nn, hh, ss, float(omega), k.ctypes.data_as(ctypes.c_void_p),
+                            t.ctypes.data_as(ctypes.c_void_p), g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(p),
+                            float(tol), int(maxit), st, u.ctypes.data_as(ctypes.c_void_p),
+                            a.ctypes.data_as(ctypes.c_void_p) if a is not None else ctypes.c_void_p(0),
+                            ctypes.byref(info))
+    L.check(rc)
+    res = {"iterations": info.iterations, "restarts": info.restarts, "rel_residual": info.rel_residual,
+           "status": info.status}
+    return (u, a, res) if want_amplitude else (u, res)

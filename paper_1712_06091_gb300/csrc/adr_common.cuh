@@ -1,0 +1,236 @@
+// Internal declarations shared by the CUDA translation units of libadr.
+//
+// Data layout in device memory (one arena per operator):
+//   * complex vectors: interleaved (re, im) of T = double or float, i.e.
+//     double2 / float2 per node, node j = i0 + n0*(i1 + n1*i2);
+//   * fine-level coefficients (matrix-free level): structure of arrays
+//     g[d][N] = d_d tau, t[d][N] = d_dd tau, rho[N] (complex reaction);
+//   * Galerkin levels: point-major stencils A[p][N] (p over the 21 / 81
+//     offsets of the coarse pattern), plus the inverse diagonal dinv[N].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "adr.h"
+
+namespace adr {
+
+// ---------------------------------------------------------------------------
+// Complex helpers on double2 / float2
+// ---------------------------------------------------------------------------
+template <typename T> struct cvec;
+template <> struct cvec<double> { using type = double2; };
+template <> struct cvec<float> { using type = float2; };
+template <typename T> using C = typename cvec<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> mk(T re, T im) {
+  C<T> z; z.x = re; z.y = im; return z;
+}
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) {
+  V z; z.x = a.x + b.x; z.y = a.y + b.y; return z;
+}
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) {
+  V z; z.x = a.x - b.x; z.y = a.y - b.y; return z;
+}
+template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
+  V z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;
+}
+// acc + a * b
+template <typename V> __host__ __device__ __forceinline__ V cfma(V a, V b, V acc) {
+  V z;
+  z.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  z.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+  return z;
+}
+// acc + conj(a) * b
+template <typename V> __host__ __device__ __forceinline__ V cfma_conj(V a, V b, V acc) {
+  V z;
+  z.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+  z.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+  return z;
+}
+template <typename V, typename T> __host__ __device__ __forceinline__ V cscale(V a, T s) {
+  V z; z.x = a.x * s; z.y = a.y * s; return z;
+}
+template <typename V> __host__ __device__ __forceinline__ V cinv(V a) {
+  // 1 / a, scaled to avoid overflow in |a|^2
+  auto m = fabs(a.x) > fabs(a.y) ? fabs(a.x) : fabs(a.y);
+  V b; b.x = a.x / m; b.y = a.y / m;
+  auto d = (b.x * b.x + b.y * b.y) * m;
+  V z; z.x = b.x / d; z.y = -b.y / d; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> czero() { return mk<T>(T(0), T(0)); }
+
+template <typename Dst, typename Src> __host__ __device__ __forceinline__ Dst ccast(Src a) {
+  Dst z; z.x = a.x; z.y = a.y; return z;
+}
+
+// ---------------------------------------------------------------------------
+// Grid descriptor
+// ---------------------------------------------------------------------------
+struct Dims {
+  int dim;
+  int n[3];
+  int64_t N;
+  int64_t s1, s2;  // strides of axes 1 and 2
+};
+
+inline Dims make_dims(int dim, const int* n) {
+  Dims g;
+  g.dim = dim;
+  g.n[0] = n[0];
+  g.n[1] = dim > 1 ? n[1] : 1;
+  g.n[2] = dim > 2 ? n[2] : 1;
+  g.s1 = g.n[0];
+  g.s2 = (int64_t)g.n[0] * g.n[1];
+  g.N = g.s2 * g.n[2];
+  return g;
+}
+
+__device__ __forceinline__ void unravel(const Dims& g, int64_t j, int& i0, int& i1, int& i2) {
+  i0 = (int)(j % g.n[0]);
+  int64_t q = j / g.n[0];
+  i1 = (int)(q % g.n[1]);
+  i2 = (int)(q / g.n[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin stencil pattern: offsets in [-2,2]^dim with at most one |o_d| = 2
+// (21 points in 2D, 81 in 3D), enumerated with axis 0 fastest.
+// ---------------------------------------------------------------------------
+constexpr int kPattern2 = 21;
+constexpr int kPattern3 = 81;
+template <int DIM> struct PatternSize { static constexpr int value = DIM == 2 ? kPattern2 : kPattern3; };
+
+// Offsets of each pattern point (third component 0 in 2D) and the inverse map
+// from (o0+2) + 5 (o1+2) + 25 (o2+2) to the point index (-1 outside).
+struct PatternTables {
+  int8_t off2[kPattern2][3];
+  int8_t off3[kPattern3][3];
+  int8_t slot2[25];
+  int8_t slot3[125];
+};
+
+constexpr PatternTables make_pattern_tables() {
+  PatternTables t{};
+  for (int k = 0; k < 25; ++k) t.slot2[k] = -1;
+  for (int k = 0; k < 125; ++k) t.slot3[k] = -1;
+  int p = 0;
+  for (int o1 = -2; o1 <= 2; ++o1)
+    for (int o0 = -2; o0 <= 2; ++o0) {
+      const int twos = (o0 == 2 || o0 == -2) + (o1 == 2 || o1 == -2);
+      if (twos > 1) continue;
+      t.off2[p][0] = (int8_t)o0; t.off2[p][1] = (int8_t)o1; t.off2[p][2] = 0;
+      t.slot2[(o0 + 2) + 5 * (o1 + 2)] = (int8_t)p;
+      ++p;
+    }
+  p = 0;
+  for (int o2 = -2; o2 <= 2; ++o2)
+    for (int o1 = -2; o1 <= 2; ++o1)
+      for (int o0 = -2; o0 <= 2; ++o0) {
+        const int twos = (o0 == 2 || o0 == -2) + (o1 == 2 || o1 == -2) + (o2 == 2 || o2 == -2);
+        if (twos > 1) continue;
+        t.off3[p][0] = (int8_t)o0; t.off3[p][1] = (int8_t)o1; t.off3[p][2] = (int8_t)o2;
+        t.slot3[(o0 + 2) + 5 * (o1 + 2) + 25 * (o2 + 2)] = (int8_t)p;
+        ++p;
+      }
+  return t;
+}
+
+// One copy per translation unit (internal linkage), so no device linking is needed.
+static __constant__ PatternTables c_pattern = make_pattern_tables();
+
+template <int DIM> __device__ __forceinline__ const int8_t* pattern_offset(int p) {
+  return DIM == 2 ? c_pattern.off2[p] : c_pattern.off3[p];
+}
+template <int DIM> __device__ __forceinline__ int pattern_slot(int o0, int o1, int o2) {
+  return DIM == 2 ? c_pattern.slot2[(o0 + 2) + 5 * (o1 + 2)]
+                  : c_pattern.slot3[(o0 + 2) + 5 * (o1 + 2) + 25 * (o2 + 2)];
+}
+
+// ---------------------------------------------------------------------------
+// Fine (matrix-free) level
+// ---------------------------------------------------------------------------
+// Row of the fine operator in "cross" form: entry 0 is the centre, entry
+// 1 + 4 d + {0,1,2,3} the neighbour at offset {-1,+1,-2,+2} along axis d.
+constexpr int kCross2 = 9;
+constexpr int kCross3 = 13;
+template <int DIM> struct CrossSize { static constexpr int value = 1 + 4 * DIM; };
+
+template <typename T> struct FineOp {
+  const T* g[3];     // d_d tau
+  const T* t[3];     // d_dd tau
+  const C<T>* rho;   // w^2 (kappa^2 - |grad tau|^2) - i w gamma kappa^2
+  const C<T>* src_row;    // row of M^{-1} H M at the source (cross form, device)
+  int src[3];
+  int64_t src_index;
+  T omega;
+  T h[3];
+  T ih2[3];
+  T w2, w1;          // weights of the second- and first-order upwind differences
+  int central;       // 1: central ADR scheme (upwind only on boundary nodes)
+  int near;          // Chebyshev radius around the source with central advection
+};
+
+// Scheme -> upwind weights.
+template <typename T> inline void set_scheme(FineOp<T>& f, int scheme, double beta) {
+  f.central = 0;
+  if (scheme == ADR_SCHEME_2UP) { f.w2 = T(1); f.w1 = T(0); }
+  else if (scheme == ADR_SCHEME_1UP) { f.w2 = T(0); f.w1 = T(1); }
+  else if (scheme == ADR_SCHEME_PREC) { f.w2 = T(1.0 - beta); f.w1 = T(beta); }
+  else { f.w2 = T(1); f.w1 = T(0); f.central = 1; }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (all asynchronous on `st`)
+// ---------------------------------------------------------------------------
+struct FineInputs {
+  const double* kappa;
+  const double* tau1;
+  const double* gamma;
+  int src[3];
+  double omega;
+  double h[3];
+};
+
+// Fine coefficients in float64 (g, t, rho, tau) and the source row.
+void launch_coefficients(const Dims& g, const FineInputs& in, double* const gd[3], double* const td[3],
+                         double2* rho, double* tau, double2* src_row, cudaStream_t st);
+// float64 -> float32 copy of n reals.
+void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+
+// Level-0 operations; x, y, b complex of T.
+template <typename T> void launch_fine_apply(const Dims& g, const FineOp<T>& f, const C<T>* x, C<T>* y, cudaStream_t st);
+template <typename T> void launch_fine_residual(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* x, C<T>* r, cudaStream_t st);
+// xout = xin + w D^{-1} (b - A xin); xin may be null (zero guess).
+template <typename T> void launch_fine_jacobi(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* xin, C<T>* xout, T w, cudaStream_t st);
+// z = D^{-1} v, or z = diag(A)^{-1} itself when v is null
+template <typename T> void launch_fine_dinv(const Dims& g, const FineOp<T>& f, const C<T>* v, C<T>* z, cudaStream_t st);
+// Galerkin product of the fine operator into the stored stencil of level 1.
+template <typename T> void launch_galerkin_fine(const Dims& gf, const Dims& gc, const FineOp<T>& f, C<T>* stencil, C<T>* dinv, cudaStream_t st);
+
+// Stored-stencil levels.
+template <typename T> void launch_stencil_apply(const Dims& g, const C<T>* A, const C<T>* x, C<T>* y, cudaStream_t st);
+template <typename T> void launch_stencil_residual(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x, C<T>* r, cudaStream_t st);
+template <typename T> void launch_stencil_jacobi(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, const C<T>* xin, C<T>* xout, T w, cudaStream_t st);
+template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st);
+
+// Transfers.
+template <typename T> void launch_restrict(const Dims& gf, const Dims& gc, const C<T>* rf, C<T>* rc, cudaStream_t st);
+template <typename T> void launch_prolong_add(const Dims& gf, const Dims& gc, const C<T>* ec, C<T>* xf, cudaStream_t st);
+
+// Counts kernel launches issued by the library (all threads).
+void count_launches(int n);
+
+// Vector kernels.
+template <typename T> void launch_cmul_vec(const C<T>* a, const C<T>* b, C<T>* out, int64_t n, cudaStream_t st);  // out = a .* b
+template <typename Ts, typename Td> void launch_ccast(const C<Ts>* src, C<Td>* dst, int64_t n, cudaStream_t st);
+
+void launch_rhs_point(double2* q, int64_t N, int64_t src_index, double value, cudaStream_t st);
+void launch_reconstruct(const double2* a, const double* tau, double omega, double2* u, int64_t N, cudaStream_t st);
+void launch_pack_coefficients(const Dims& g, const double* const gd[3], const double* const td[3], const double2* rho,
+                              const double* tau, double* out, cudaStream_t st);
+
+}  // namespace adr

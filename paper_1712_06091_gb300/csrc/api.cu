@@ -1,0 +1,788 @@
+// C ABI, operator lifetime and the solver drivers of libadr.
+//
+//  * adr_operator_create: fine coefficients (Eq. travel_time_coeff), the
+//    multigrid hierarchy with Galerkin coarse operators of the blend
+//    (1 - beta) H_2up + beta H_1up (Eqs. precADRup, coarseGridMatrix).
+//  * the cycle: Alg. TwoGrid applied recursively (V) or with an inner
+//    flexible GMRES on every coarse level but the last (Alg. Kcycle);
+//    relaxation by damped Jacobi or by one Jacobi-preconditioned GMRES step
+//    (Sec. 3.1); fixed-count Jacobi-preconditioned GMRES on the coarsest
+//    level (Sec. 3.1, Sec. 4.2).
+//  * adr_solve: right-preconditioned flexible GMRES(m) in float64 on H_2up,
+//    classical Gram-Schmidt applied twice, Givens rotations on the device.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "krylov.cuh"
+
+namespace adr {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define ADR_CUDA(call)                                                                            \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(ADR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define ADR_TRY(expr)              \
+  do {                             \
+    int rc_ = (expr);              \
+    if (rc_ != ADR_OK) return rc_; \
+  } while (0)
+
+static int check_launch(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ADR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return ADR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Arena: one device allocation carved into 256-byte aligned pieces.  The
+// layout is computed twice: once with a null base to size it, once for real.
+// ---------------------------------------------------------------------------
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0;
+  template <typename X> X* take(size_t count) {
+    used = (used + 255) & ~size_t(255);
+    X* p = base ? reinterpret_cast<X*>(base + used) : nullptr;
+    used += count * sizeof(X);
+    return p;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Hierarchy in one precision
+// ---------------------------------------------------------------------------
+template <typename T> struct Level {
+  Dims g;
+  C<T>* A = nullptr;     // Galerkin stencil (levels >= 1)
+  C<T>* dinv = nullptr;  // inverse diagonal
+  C<T>* b = nullptr;     // right-hand side handed down by restriction
+  C<T>* x = nullptr;     // correction handed up to prolongation
+  C<T>* r = nullptr;     // residual
+  C<T>* t = nullptr;     // scratch: Jacobi ping-pong, A z of the MR step, Krylov w
+  C<T>* z = nullptr;     // MR search direction / preconditioned vector
+  C<T>* KV = nullptr;    // Krylov basis (K-cycle or coarsest GMRES)
+  C<T>* KZ = nullptr;    // K-cycle preconditioned basis
+  int kdim = 0;          // Krylov dimension used on this level
+  ArnoldiState ks{};
+};
+
+struct Scratch {
+  double2* partial = nullptr;  // kMaxReduceBlocks x kMaxDots
+  double2* ha = nullptr;       // first Gram-Schmidt pass
+  double2* hb = nullptr;       // second pass
+  double2* nrm2 = nullptr;     // squared norm
+  double2* d2 = nullptr;       // MR dots
+  double2* alpha = nullptr;    // MR weight
+};
+constexpr int kMaxDots = 66;
+
+static void take_arnoldi(Arena& a, ArnoldiState& s, int m) {
+  s.m = m;
+  s.H = a.take<double2>((size_t)(m + 1) * m);
+  s.cs = a.take<double>(m);
+  s.sn = a.take<double2>(m);
+  s.g = a.take<double2>(m + 1);
+  s.y = a.take<double2>(m);
+  s.scal = a.take<double>(kNumScal);
+  s.iscal = a.take<int>(kNumIScal);
+}
+
+template <typename T> struct Hier {
+  int L = 0;
+  Level<T> lv[ADR_MAX_LEVELS];
+  FineOp<T> prec{};   // level-0 operator of the cycle: (1 - beta) H_2up + beta H_1up
+};
+
+struct Op {
+  int dim = 0;
+  Dims g0{};
+  adr_params_t p{};
+  cudaStream_t st = nullptr;
+  double omega = 0;
+  double h[3] = {0, 0, 0};
+  int src[3] = {0, 0, 0};
+  int64_t src_index = 0;
+  // fine coefficients
+  double* gd[3] = {nullptr, nullptr, nullptr};
+  double* td[3] = {nullptr, nullptr, nullptr};
+  double2* rho = nullptr;
+  double* tau = nullptr;
+  double2* srow = nullptr;
+  float* srowf = nullptr;  // float2 view
+  float* gf[3] = {nullptr, nullptr, nullptr};
+  float* tf[3] = {nullptr, nullptr, nullptr};
+  float* rhof = nullptr;  // float2 view
+  Hier<double> h64;
+  Hier<float> h32;
+  // outer FGMRES
+  double2* V = nullptr;
+  double2* Z = nullptr;
+  double2* b = nullptr;  // point-source right-hand side
+  double2* r = nullptr;
+  ArnoldiState ost{};
+  Scratch sc;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  double* host_scal = nullptr;  // pinned: [0] estimate, [1] hn, [2] norm^2
+};
+
+static bool can_coarsen(const Dims& g) {
+  for (int d = 0; d < g.dim; ++d)
+    if (g.n[d] % 2 == 0 || g.n[d] < 5) return false;
+  return true;
+}
+
+template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
+  const adr_params_t& p = op.p;
+  Dims g = op.g0;
+  H.L = 0;
+  for (int l = 0; l < p.levels; ++l) {
+    if (l > 0) {
+      if (!can_coarsen(H.lv[l - 1].g)) break;
+      int nc[3];
+      for (int d = 0; d < 3; ++d) nc[d] = (H.lv[l - 1].g.n[d] - 1) / 2 + 1;
+      g = make_dims(op.dim, nc);
+    }
+    H.L = l + 1;
+    H.lv[l].g = g;
+  }
+  const int S = op.dim == 2 ? kPattern2 : kPattern3;
+  for (int l = 0; l < H.L; ++l) {
+    Level<T>& L = H.lv[l];
+    const size_t N = (size_t)L.g.N;
+    L.A = l > 0 ? a.take<C<T>>((size_t)S * N) : nullptr;
+    L.dinv = a.take<C<T>>(N);
+    L.b = a.take<C<T>>(N);
+    L.x = a.take<C<T>>(N);
+    L.r = a.take<C<T>>(N);
+    L.t = a.take<C<T>>(N);
+    L.z = a.take<C<T>>(N);
+    L.kdim = 0;
+    if (l == H.L - 1) L.kdim = p.coarse_iterations;
+    else if (p.cycle == ADR_CYCLE_K && l > 0) L.kdim = p.kcycle_iterations;
+    if (L.kdim > 0) {
+      L.KV = a.take<C<T>>((size_t)(L.kdim + 1) * N);
+      L.KZ = (l == H.L - 1) ? nullptr : a.take<C<T>>((size_t)L.kdim * N);
+      take_arnoldi(a, L.ks, L.kdim);
+    }
+  }
+}
+
+static void plan(Op& op, Arena& a) {
+  const size_t N = (size_t)op.g0.N;
+  for (int d = 0; d < op.dim; ++d) {
+    op.gd[d] = a.take<double>(N);
+    op.td[d] = a.take<double>(N);
+    op.gf[d] = a.take<float>(N);
+    op.tf[d] = a.take<float>(N);
+  }
+  op.rho = a.take<double2>(N);
+  op.rhof = a.take<float>(2 * N);
+  op.tau = a.take<double>(N);
+  op.srow = a.take<double2>(kCross3);
+  op.srowf = a.take<float>(2 * kCross3);
+  if (op.p.precond_precision == ADR_F64) plan_hierarchy(op, op.h64, a);
+  else plan_hierarchy(op, op.h32, a);
+  const int m = op.p.restart;
+  op.V = a.take<double2>((size_t)(m + 1) * N);
+  op.Z = a.take<double2>((size_t)m * N);
+  op.b = a.take<double2>(N);
+  op.r = a.take<double2>(N);
+  take_arnoldi(a, op.ost, m);
+  op.sc.partial = a.take<double2>((size_t)kMaxReduceBlocks * kMaxDots);
+  op.sc.ha = a.take<double2>(kMaxDots);
+  op.sc.hb = a.take<double2>(kMaxDots);
+  op.sc.nrm2 = a.take<double2>(1);
+  op.sc.d2 = a.take<double2>(2);
+  op.sc.alpha = a.take<double2>(1);
+}
+
+template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool f32) {
+  FineOp<T> f{};
+  for (int d = 0; d < 3; ++d) {
+    if (d < op.dim) {
+      f.g[d] = f32 ? (const T*)(const void*)op.gf[d] : (const T*)(const void*)op.gd[d];
+      f.t[d] = f32 ? (const T*)(const void*)op.tf[d] : (const T*)(const void*)op.td[d];
+      f.h[d] = (T)op.h[d];
+      f.ih2[d] = (T)(1.0 / (op.h[d] * op.h[d]));
+    } else {
+      f.g[d] = nullptr; f.t[d] = nullptr; f.h[d] = T(1); f.ih2[d] = T(0);
+    }
+    f.src[d] = op.src[d];
+  }
+  f.rho = f32 ? (const C<T>*)(const void*)op.rhof : (const C<T>*)(const void*)op.rho;
+  f.src_row = f32 ? (const C<T>*)(const void*)op.srowf : (const C<T>*)(const void*)op.srow;
+  f.src_index = op.src_index;
+  f.omega = (T)op.omega;
+  f.near = op.p.near_source;
+  set_scheme(f, scheme, op.p.beta);
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Level operations
+// ---------------------------------------------------------------------------
+template <typename T> struct Cycle {
+  Op& op;
+  Hier<T>& H;
+  cudaStream_t st;
+
+  void apply(int l, const C<T>* x, C<T>* y) {
+    if (l == 0) launch_fine_apply<T>(H.lv[0].g, H.prec, x, y, st);
+    else launch_stencil_apply<T>(H.lv[l].g, H.lv[l].A, x, y, st);
+  }
+  void residual(int l, const C<T>* b, const C<T>* x, C<T>* r) {
+    if (l == 0) launch_fine_residual<T>(H.lv[0].g, H.prec, b, x, r, st);
+    else launch_stencil_residual<T>(H.lv[l].g, H.lv[l].A, b, x, r, st);
+  }
+  void jacobi(int l, const C<T>* b, const C<T>* xin, C<T>* xout, T w) {
+    if (l == 0) launch_fine_jacobi<T>(H.lv[0].g, H.prec, b, xin, xout, w, st);
+    else launch_stencil_jacobi<T>(H.lv[l].g, H.lv[l].A, H.lv[l].dinv, b, xin, xout, w, st);
+  }
+  void norm2(const C<T>* v, int64_t n, double2* out) {
+    launch_dots<T>(v, 0, 1, v, n, op.sc.partial, out, st);
+  }
+
+  // `sweeps` relaxations on A_l x = b; x_zero says x holds zero on entry.
+  void relax(int l, const C<T>* b, C<T>* x, int sweeps, bool& x_zero) {
+    Level<T>& L = H.lv[l];
+    const int64_t n = L.g.N;
+    if (sweeps <= 0) return;
+    if (op.p.relax == ADR_RELAX_JACOBI) {
+      const T w = (T)op.p.jacobi_weight[l];
+      C<T>* cur = x;
+      C<T>* oth = L.t;
+      for (int s = 0; s < sweeps; ++s) {
+        jacobi(l, b, x_zero ? nullptr : cur, oth, w);
+        x_zero = false;
+        C<T>* tmp = cur; cur = oth; oth = tmp;
+      }
+      if (cur != x) launch_copy<T>(cur, x, n, st);
+      return;
+    }
+    // Minimal-residual Jacobi: x += alpha z, z = D^{-1} r, alpha = (Az)^H r / |Az|^2
+    if (x_zero) launch_copy<T>(b, L.r, n, st);
+    else residual(l, b, x, L.r);
+    if (x_zero) launch_zero<T>(x, n, st);
+    x_zero = false;
+    launch_cmul_vec<T>(L.dinv, L.r, L.z, n, st);
+    for (int s = 0; s < sweeps; ++s) {
+      apply(l, L.z, L.t);
+      launch_dot2<T>(L.t, L.r, L.t, n, op.sc.partial, op.sc.d2, st);
+      launch_mr_alpha(op.sc.d2, op.sc.alpha, st);
+      launch_mr_update<T>(x, L.z, L.r, L.t, op.sc.alpha, L.dinv, s + 1 < sweeps ? L.z : nullptr, n, st);
+    }
+  }
+
+  // Arnoldi step j on level l: w (in/out, orthogonalised) against V_0..V_j; V_{j+1} = w / |w|.
+  void arnoldi(ArnoldiState& ks, C<T>* Vb, int64_t ld, int j, C<T>* w, int64_t n, bool store_next) {
+    launch_dots<T>(Vb, ld, j + 1, w, n, op.sc.partial, op.sc.ha, st);
+    launch_axpy_multi<T>(w, Vb, ld, j + 1, op.sc.ha, -1.0, n, st);
+    launch_dots<T>(Vb, ld, j + 1, w, n, op.sc.partial, op.sc.hb, st);
+    launch_axpy_multi<T>(w, Vb, ld, j + 1, op.sc.hb, -1.0, n, st);
+    norm2(w, n, op.sc.nrm2);
+    launch_arnoldi_column(ks, j, op.sc.ha, op.sc.hb, op.sc.nrm2, st);
+    if (store_next) launch_scale_inv_norm<T>(w, Vb + (int64_t)(j + 1) * ld, op.sc.nrm2, n, st);
+  }
+
+  // Fixed-count GMRES from zero, right-preconditioned by D^{-1} (coarsest level).
+  void coarse_solve(int l, const C<T>* b, C<T>* x) {
+    Level<T>& L = H.lv[l];
+    const int64_t n = L.g.N;
+    const int k = L.kdim;
+    norm2(b, n, op.sc.nrm2);
+    launch_cycle_start(L.ks, op.sc.nrm2, st);
+    launch_scale_inv_norm<T>(b, L.KV, op.sc.nrm2, n, st);
+    for (int j = 0; j < k; ++j) {
+      launch_cmul_vec<T>(L.dinv, L.KV + (int64_t)j * n, L.z, n, st);
+      apply(l, L.z, L.t);
+      arnoldi(L.ks, L.KV, n, j, L.t, n, j + 1 < k);
+    }
+    launch_backsolve(L.ks, k, st);
+    launch_zero<T>(L.t, n, st);
+    launch_axpy_multi<T>(L.t, L.KV, n, k, L.ks.y, 1.0, n, st);
+    launch_cmul_vec<T>(L.dinv, L.t, x, n, st);
+  }
+
+  // Inner flexible GMRES of the K-cycle on level l, from zero, fixed count.
+  void kcycle(int l, const C<T>* b, C<T>* x) {
+    Level<T>& L = H.lv[l];
+    const int64_t n = L.g.N;
+    const int k = L.kdim;
+    norm2(b, n, op.sc.nrm2);
+    launch_cycle_start(L.ks, op.sc.nrm2, st);
+    launch_scale_inv_norm<T>(b, L.KV, op.sc.nrm2, n, st);
+    for (int j = 0; j < k; ++j) {
+      C<T>* zj = L.KZ + (int64_t)j * n;
+      cycle(l, L.KV + (int64_t)j * n, zj);
+      apply(l, zj, L.t);
+      arnoldi(L.ks, L.KV, n, j, L.t, n, j + 1 < k);
+    }
+    launch_backsolve(L.ks, k, st);
+    launch_zero<T>(x, n, st);
+    launch_axpy_multi<T>(x, L.KZ, n, k, L.ks.y, 1.0, n, st);
+  }
+
+  // x = B_l^{-1} b, zero initial guess (Alg. TwoGrid / Alg. Kcycle).
+  void cycle(int l, const C<T>* b, C<T>* x) {
+    if (l == H.L - 1) { coarse_solve(l, b, x); return; }
+    Level<T>& L = H.lv[l];
+    Level<T>& Lc = H.lv[l + 1];
+    const int64_t n = L.g.N;
+    bool x_zero = true;
+    relax(l, b, x, op.p.pre_sweeps[l], x_zero);
+    if (x_zero) launch_restrict<T>(L.g, Lc.g, b, Lc.b, st);
+    else {
+      residual(l, b, x, L.r);
+      launch_restrict<T>(L.g, Lc.g, L.r, Lc.b, st);
+    }
+    if (op.p.cycle == ADR_CYCLE_K && l + 1 < H.L - 1) kcycle(l + 1, Lc.b, Lc.x);
+    else cycle(l + 1, Lc.b, Lc.x);
+    if (x_zero) { launch_zero<T>(x, n, st); x_zero = false; }
+    launch_prolong_add<T>(L.g, Lc.g, Lc.x, x, st);
+    relax(l, b, x, op.p.post_sweeps[l], x_zero);
+  }
+};
+
+template <typename T> static int build_hierarchy(Op& op, Hier<T>& H) {
+  const bool f32 = sizeof(T) == 4;
+  H.prec = make_fine<T>(op, ADR_SCHEME_PREC, f32);
+  Level<T>& L0 = H.lv[0];
+  launch_fine_dinv<T>(L0.g, H.prec, nullptr, L0.dinv, op.st);
+  for (int l = 1; l < H.L; ++l) {
+    if (l == 1) launch_galerkin_fine<T>(H.lv[0].g, H.lv[1].g, H.prec, H.lv[1].A, H.lv[1].dinv, op.st);
+    else launch_galerkin_stored<T>(H.lv[l - 1].g, H.lv[l].g, H.lv[l - 1].A, H.lv[l].A, H.lv[l].dinv, op.st);
+  }
+  return check_launch("hierarchy setup");
+}
+
+// Coefficients, their float32 copies and the Galerkin hierarchy for the
+// current source / frequency, written into the operator's arena (no sync).
+static int setup(Op& op, const double* kappa, const double* tau1, const double* gamma) {
+  const int64_t N = op.g0.N;
+  FineInputs in{};
+  in.kappa = kappa; in.tau1 = tau1; in.gamma = gamma;
+  for (int d = 0; d < 3; ++d) { in.src[d] = op.src[d]; in.h[d] = op.h[d]; }
+  in.omega = op.omega;
+  launch_coefficients(op.g0, in, op.gd, op.td, op.rho, op.tau, op.srow, op.st);
+  for (int d = 0; d < op.dim; ++d) {
+    launch_to_f32(op.gd[d], op.gf[d], N, op.st);
+    launch_to_f32(op.td[d], op.tf[d], N, op.st);
+  }
+  launch_to_f32((const double*)op.rho, op.rhof, 2 * N, op.st);
+  launch_to_f32((const double*)op.srow, op.srowf, 2 * kCross3, op.st);
+  ADR_TRY(check_launch("coefficients"));
+  return op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32);
+}
+
+// One preconditioner application on float64 vectors (casting for a float32 cycle).
+static void precondition(Op& op, const double2* v, double2* z) {
+  if (op.p.precond_precision == ADR_F64) {
+    Cycle<double> c{op, op.h64, op.st};
+    c.cycle(0, v, z);
+  } else {
+    Cycle<float> c{op, op.h32, op.st};
+    Level<float>& L0 = op.h32.lv[0];
+    launch_ccast<double, float>(v, L0.b, op.g0.N, op.st);
+    c.cycle(0, L0.b, L0.x);
+    launch_ccast<float, double>(L0.x, z, op.g0.N, op.st);
+  }
+}
+
+static int read_scalars(Op& op, const double* dev, int count) {
+  ADR_CUDA(cudaMemcpyAsync(op.host_scal, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, op.st));
+  ADR_CUDA(cudaStreamSynchronize(op.st));
+  return ADR_OK;
+}
+
+static int validate_params(const adr_params_t& p) {
+  if (p.levels < 1 || p.levels > ADR_MAX_LEVELS) return fail(ADR_ERR_ARG, "levels must be in [1, 8]");
+  if (!(p.beta >= 0.0 && p.beta <= 1.0)) return fail(ADR_ERR_ARG, "beta must be in [0, 1]");
+  if (p.cycle != ADR_CYCLE_V && p.cycle != ADR_CYCLE_K) return fail(ADR_ERR_ARG, "unknown cycle");
+  if (p.relax != ADR_RELAX_JACOBI && p.relax != ADR_RELAX_MR) return fail(ADR_ERR_ARG, "unknown relaxation");
+  if (p.coarse_iterations < 1 || p.coarse_iterations > 64) return fail(ADR_ERR_ARG, "coarse_iterations must be in [1, 64]");
+  if (p.kcycle_iterations < 1 || p.kcycle_iterations > 16) return fail(ADR_ERR_ARG, "kcycle_iterations must be in [1, 16]");
+  if (p.restart < 1 || p.restart > 64) return fail(ADR_ERR_ARG, "restart must be in [1, 64]");
+  if (p.precond_precision != ADR_F64 && p.precond_precision != ADR_F32) return fail(ADR_ERR_ARG, "unknown precision");
+  if (p.near_source < 1 || p.near_source > 4) return fail(ADR_ERR_ARG, "near_source must be in [1, 4]");
+  for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
+    if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
+      return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");
+    if (!(p.jacobi_weight[l] > 0.0 && p.jacobi_weight[l] <= 2.0)) return fail(ADR_ERR_ARG, "jacobi_weight must be in (0, 2]");
+  }
+  return ADR_OK;
+}
+
+}  // namespace adr
+
+using namespace adr;
+
+struct adr_op_s {
+  Op op;
+};
+
+extern "C" {
+
+const char* adr_last_error(void) { return g_last_error.c_str(); }
+const char* adr_version(void) { return "0.1.0"; }
+
+int adr_params_default(adr_params_t* p) {
+  if (!p) return fail(ADR_ERR_ARG, "params is null");
+  std::memset(p, 0, sizeof(*p));
+  p->levels = 5;
+  p->beta = 0.25;
+  p->cycle = ADR_CYCLE_K;
+  p->relax = ADR_RELAX_MR;
+  for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
+    p->pre_sweeps[l] = l + 2;   // level l+1 in the paper's numbering gets l+2 relaxations
+    p->post_sweeps[l] = l + 2;
+    p->jacobi_weight[l] = 0.5;
+  }
+  p->coarse_iterations = 10;
+  p->kcycle_iterations = 2;
+  p->restart = 20;
+  p->precond_precision = ADR_F32;
+  p->near_source = 1;
+  return ADR_OK;
+}
+
+int adr_operator_create(int dim, const int* n, const double* h, const int* src, double omega, const double* kappa,
+                        const double* tau1, const double* gamma, const adr_params_t* params, void* stream, adr_op_t* out) {
+  if (!out) return fail(ADR_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fail(ADR_ERR_ARG, "dim must be 2 or 3");
+  if (!n || !h || !src || !kappa || !tau1 || !gamma) return fail(ADR_ERR_ARG, "null argument");
+  if (!(omega > 0.0)) return fail(ADR_ERR_ARG, "omega must be positive");
+  for (int d = 0; d < dim; ++d) {
+    if (n[d] < 4) return fail(ADR_ERR_ARG, "every axis needs at least 4 nodes");
+    if (!(h[d] > 0.0)) return fail(ADR_ERR_ARG, "spacings must be positive");
+    if (src[d] < 0 || src[d] >= n[d]) return fail(ADR_ERR_ARG, "source outside the grid");
+  }
+  adr_params_t p;
+  if (params) p = *params;
+  else adr_params_default(&p);
+  ADR_TRY(validate_params(p));
+  const int64_t N = (int64_t)n[0] * n[1] * (dim > 2 ? n[2] : 1);
+  if (N > ((int64_t)1 << 31) - 1) return fail(ADR_ERR_ARG, "grid too large (more than 2^31 - 1 nodes)");
+
+  adr_op_s* h_ = new (std::nothrow) adr_op_s();
+  if (!h_) return fail(ADR_ERR_OOM, "host allocation failed");
+  Op& op = h_->op;
+  op.dim = dim;
+  op.g0 = make_dims(dim, n);
+  op.p = p;
+  op.st = (cudaStream_t)stream;
+  op.omega = omega;
+  for (int d = 0; d < 3; ++d) {
+    op.h[d] = d < dim ? h[d] : 1.0;
+    op.src[d] = d < dim ? src[d] : 0;
+  }
+  op.src_index = op.src[0] + op.g0.s1 * op.src[1] + op.g0.s2 * op.src[2];
+
+  Arena sizing;
+  plan(op, sizing);
+  op.arena_bytes = sizing.used + 256;
+  cudaError_t e = cudaMalloc(&op.arena, op.arena_bytes);
+  if (e != cudaSuccess) {
+    delete h_;
+    cudaGetLastError();
+    return fail(ADR_ERR_OOM, std::string("cudaMalloc of the operator arena failed: ") + cudaGetErrorString(e));
+  }
+  e = cudaMallocHost(&op.host_scal, 8 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(op.arena);
+    delete h_;
+    return fail(ADR_ERR_OOM, "pinned host allocation failed");
+  }
+  Arena real;
+  real.base = (char*)op.arena;
+  plan(op, real);
+
+  int rc = setup(op, kappa, tau1, gamma);
+  if (rc != ADR_OK) {
+    cudaStreamSynchronize(op.st);
+    cudaFree(op.arena);
+    cudaFreeHost(op.host_scal);
+    delete h_;
+    return rc;
+  }
+  *out = h_;
+  return ADR_OK;
+}
+
+int adr_operator_update(adr_op_t h, const int* src, double omega, const double* kappa, const double* tau1,
+                        const double* gamma) {
+  if (!h || !src || !kappa || !tau1 || !gamma) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  if (!(omega > 0.0)) return fail(ADR_ERR_ARG, "omega must be positive");
+  for (int d = 0; d < op.dim; ++d)
+    if (src[d] < 0 || src[d] >= op.g0.n[d]) return fail(ADR_ERR_ARG, "source outside the grid");
+  for (int d = 0; d < 3; ++d) op.src[d] = d < op.dim ? src[d] : 0;
+  op.src_index = op.src[0] + op.g0.s1 * op.src[1] + op.g0.s2 * op.src[2];
+  op.omega = omega;
+  return setup(op, kappa, tau1, gamma);
+}
+
+long long adr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int adr_operator_destroy(adr_op_t h) {
+  if (!h) return ADR_OK;
+  Op& op = h->op;
+  cudaStreamSynchronize(op.st);
+  cudaError_t e1 = cudaFree(op.arena);
+  cudaError_t e2 = cudaFreeHost(op.host_scal);
+  delete h;
+  if (e1 != cudaSuccess) return fail(ADR_ERR_CUDA, std::string("cudaFree: ") + cudaGetErrorString(e1));
+  if (e2 != cudaSuccess) return fail(ADR_ERR_CUDA, std::string("cudaFreeHost: ") + cudaGetErrorString(e2));
+  return ADR_OK;
+}
+
+int adr_operator_info(adr_op_t h, adr_op_info_t* info) {
+  if (!h || !info) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  std::memset(info, 0, sizeof(*info));
+  info->dim = op.dim;
+  const int L = op.p.precond_precision == ADR_F64 ? op.h64.L : op.h32.L;
+  info->levels = L;
+  for (int l = 0; l < L; ++l) {
+    const Dims& g = op.p.precond_precision == ADR_F64 ? op.h64.lv[l].g : op.h32.lv[l].g;
+    for (int d = 0; d < 3; ++d) info->level[l].n[d] = g.n[d];
+    info->level[l].nodes = g.N;
+    info->level[l].stencil_points = l == 0 ? 0 : (op.dim == 2 ? kPattern2 : kPattern3);
+  }
+  info->arena_bytes = (int64_t)op.arena_bytes;
+  return ADR_OK;
+}
+
+int adr_coefficients(adr_op_t h, double* out) {
+  if (!h || !out) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  launch_pack_coefficients(op.g0, op.gd, op.td, op.rho, op.tau, out, op.st);
+  return check_launch("adr_coefficients");
+}
+
+int adr_apply(adr_op_t h, int scheme, int precision, const void* x, void* y) {
+  if (!h || !x || !y) return fail(ADR_ERR_ARG, "null argument");
+  if (scheme < ADR_SCHEME_2UP || scheme > ADR_SCHEME_PREC) return fail(ADR_ERR_ARG, "unknown scheme");
+  Op& op = h->op;
+  if (precision == ADR_F64) {
+    FineOp<double> f = make_fine<double>(op, scheme, false);
+    launch_fine_apply<double>(op.g0, f, (const double2*)x, (double2*)y, op.st);
+  } else if (precision == ADR_F32) {
+    FineOp<float> f = make_fine<float>(op, scheme, true);
+    launch_fine_apply<float>(op.g0, f, (const float2*)x, (float2*)y, op.st);
+  } else {
+    return fail(ADR_ERR_ARG, "unknown precision");
+  }
+  return check_launch("adr_apply");
+}
+
+int adr_level_stencil(adr_op_t h, int level, void* out) {
+  if (!h || !out) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  const int L = op.p.precond_precision == ADR_F64 ? op.h64.L : op.h32.L;
+  if (level < 1 || level >= L) return fail(ADR_ERR_ARG, "level must be in [1, levels)");
+  const int S = op.dim == 2 ? kPattern2 : kPattern3;
+  size_t bytes;
+  const void* src;
+  if (op.p.precond_precision == ADR_F64) {
+    bytes = sizeof(double2) * (size_t)S * op.h64.lv[level].g.N;
+    src = op.h64.lv[level].A;
+  } else {
+    bytes = sizeof(float2) * (size_t)S * op.h32.lv[level].g.N;
+    src = op.h32.lv[level].A;
+  }
+  ADR_CUDA(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, op.st));
+  return ADR_OK;
+}
+
+int adr_vcycle(adr_op_t h, const void* r, void* z) {
+  if (!h || !r || !z) return fail(ADR_ERR_ARG, "null argument");
+  if (r == z) return fail(ADR_ERR_ARG, "z may not alias r");
+  Op& op = h->op;
+  if (op.p.precond_precision == ADR_F64) {
+    Cycle<double> c{op, op.h64, op.st};
+    c.cycle(0, (const double2*)r, (double2*)z);
+  } else {
+    Cycle<float> c{op, op.h32, op.st};
+    c.cycle(0, (const float2*)r, (float2*)z);
+  }
+  return check_launch("adr_vcycle");
+}
+
+int adr_point_source_rhs(adr_op_t h, void* q) {
+  if (!h || !q) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  double vol = 1.0;
+  for (int d = 0; d < op.dim; ++d) vol *= op.h[d];
+  launch_rhs_point((double2*)q, op.g0.N, op.src_index, 1.0 / vol, op.st);
+  return check_launch("adr_point_source_rhs");
+}
+
+int adr_reconstruct(adr_op_t h, const void* a, void* u) {
+  if (!h || !a || !u) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  launch_reconstruct((const double2*)a, op.tau, op.omega, (double2*)u, op.g0.N, op.st);
+  return check_launch("adr_reconstruct");
+}
+
+int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double tol, int maxit, adr_solve_info_t* info) {
+  if (!h || !a_out) return fail(ADR_ERR_ARG, "null argument");
+  if (!(tol >= 0.0) || maxit < 0) return fail(ADR_ERR_ARG, "tol must be >= 0 and maxit >= 0");
+  Op& op = h->op;
+  cudaStream_t st = op.st;
+  const int64_t N = op.g0.N;
+  const int m = op.p.restart;
+  double2* a = (double2*)a_out;
+  const double2* b = (const double2*)rhs_in;
+  if (!b) {
+    ADR_TRY(adr_point_source_rhs(h, op.b));
+    b = op.b;
+  }
+  const FineOp<double> A = make_fine<double>(op, ADR_SCHEME_2UP, false);
+  auto norm2 = [&](const double2* v) { launch_dots<double>(v, 0, 1, v, N, op.sc.partial, op.sc.nrm2, st); };
+
+  norm2(b);
+  ADR_TRY(read_scalars(op, (const double*)op.sc.nrm2, 1));
+  const double bnorm = sqrt(op.host_scal[0]);
+  adr_solve_info_t res{};
+  if (bnorm == 0.0) {
+    launch_zero<double>(a, N, st);
+    if (info) *info = res;
+    return check_launch("adr_solve");
+  }
+  if (use_x0) {
+    launch_fine_residual<double>(op.g0, A, b, a, op.r, st);
+  } else {
+    launch_zero<double>(a, N, st);
+    launch_copy<double>(b, op.r, N, st);
+  }
+  norm2(op.r);
+  ADR_TRY(read_scalars(op, (const double*)op.sc.nrm2, 1));
+  double beta = sqrt(op.host_scal[0]);
+  int its = 0, cycles = 0;
+  double est = beta / bnorm;
+  int status = ADR_OK;
+  while (beta > tol * bnorm && its < maxit) {
+    // op.sc.nrm2 holds |r|^2 here
+    launch_cycle_start(op.ost, op.sc.nrm2, st);
+    launch_scale_inv_norm<double>(op.r, op.V, op.sc.nrm2, N, st);
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double2* vj = op.V + (int64_t)j * N;
+      double2* zj = op.Z + (int64_t)j * N;
+      double2* w = op.V + (int64_t)(j + 1) * N;  // A z_j, orthogonalised and normalised in place
+      precondition(op, vj, zj);
+      launch_fine_apply<double>(op.g0, A, zj, w, st);
+      launch_dots<double>(op.V, N, j + 1, w, N, op.sc.partial, op.sc.ha, st);
+      launch_axpy_multi<double>(w, op.V, N, j + 1, op.sc.ha, -1.0, N, st);
+      launch_dots<double>(op.V, N, j + 1, w, N, op.sc.partial, op.sc.hb, st);
+      launch_axpy_multi<double>(w, op.V, N, j + 1, op.sc.hb, -1.0, N, st);
+      norm2(w);
+      launch_arnoldi_column(op.ost, j, op.sc.ha, op.sc.hb, op.sc.nrm2, st);
+      launch_scale_inv_norm<double>(w, w, op.sc.nrm2, N, st);
+      ADR_TRY(check_launch("adr_solve iteration"));
+      ADR_TRY(read_scalars(op, op.ost.scal, kNumScal));
+      ++its;
+      k = j + 1;
+      est = op.host_scal[kScalEst] / bnorm;
+      const double hn = op.host_scal[kScalHn];
+      if (!std::isfinite(est) || !std::isfinite(hn)) { status = ADR_ERR_NAN; break; }
+      if (hn == 0.0) break;
+      if (op.host_scal[kScalEst] <= tol * bnorm || its >= maxit) break;
+    }
+    if (status == ADR_ERR_NAN) break;
+    launch_backsolve(op.ost, k, st);
+    launch_axpy_multi<double>(a, op.Z, N, k, op.ost.y, 1.0, N, st);
+    launch_fine_residual<double>(op.g0, A, b, a, op.r, st);
+    norm2(op.r);
+    ADR_TRY(read_scalars(op, (const double*)op.sc.nrm2, 1));
+    beta = sqrt(op.host_scal[0]);
+    ++cycles;
+    if (!std::isfinite(beta)) { status = ADR_ERR_NAN; break; }
+  }
+  ADR_TRY(check_launch("adr_solve"));
+  res.iterations = its;
+  res.restarts = cycles;
+  res.rel_residual = beta / bnorm;
+  res.rel_estimate = est;
+  if (status == ADR_OK && beta > tol * bnorm) status = ADR_ERR_NOT_CONVERGED;
+  res.status = status;
+  if (info) *info = res;
+  if (status == ADR_ERR_NAN) return fail(ADR_ERR_NAN, "NaN or Inf in the Krylov iteration");
+  if (status == ADR_ERR_NOT_CONVERGED) return fail(ADR_ERR_NOT_CONVERGED, "iteration budget spent above the tolerance");
+  return ADR_OK;
+}
+
+int adr_solve_host(int dim, const int* n, const double* h, const int* src, double omega, const double* kappa,
+                   const double* tau1, const double* gamma, const adr_params_t* params, double tol, int maxit,
+                   void* stream, double* u_host, double* a_host, adr_solve_info_t* info) {
+  if (!n || !kappa || !tau1 || !gamma || !u_host) return fail(ADR_ERR_ARG, "null argument");
+  if (dim != 2 && dim != 3) return fail(ADR_ERR_ARG, "dim must be 2 or 3");
+  int64_t N = 1;
+  for (int d = 0; d < dim; ++d) {
+    if (n[d] < 4) return fail(ADR_ERR_ARG, "every axis needs at least 4 nodes");
+    N *= n[d];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // one allocation, each piece on a 256-byte boundary (complex pieces are read as double2)
+  const size_t real_bytes = sizeof(double) * (size_t)N;
+  const size_t real_slot = (real_bytes + 255) & ~size_t(255);
+  const size_t cplx_slot = (2 * real_bytes + 255) & ~size_t(255);
+  char* dev = nullptr;
+  ADR_CUDA(cudaMalloc(&dev, 3 * real_slot + 2 * cplx_slot));
+  double* dk = (double*)(dev);
+  double* dt = (double*)(dev + real_slot);
+  double* dg = (double*)(dev + 2 * real_slot);
+  double* da = (double*)(dev + 3 * real_slot);
+  double* du = (double*)(dev + 3 * real_slot + cplx_slot);
+  int rc = ADR_OK;
+  cudaError_t e = cudaMemcpyAsync(dk, kappa, real_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tau1, real_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dg, gamma, real_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) rc = fail(ADR_ERR_CUDA, std::string("host to device copy: ") + cudaGetErrorString(e));
+  adr_op_t op = nullptr;
+  if (rc == ADR_OK) rc = adr_operator_create(dim, n, h, src, omega, dk, dt, dg, params, stream, &op);
+  adr_solve_info_t res{};
+  int solve_rc = ADR_OK;
+  if (rc == ADR_OK) {
+    solve_rc = adr_solve(op, nullptr, da, 0, tol, maxit, &res);
+    if (solve_rc == ADR_OK || solve_rc == ADR_ERR_NOT_CONVERGED) {
+      rc = adr_reconstruct(op, da, du);
+      if (rc == ADR_OK) {
+        e = cudaMemcpyAsync(u_host, du, 2 * real_bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && a_host) e = cudaMemcpyAsync(a_host, da, 2 * real_bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(ADR_ERR_CUDA, std::string("device to host copy: ") + cudaGetErrorString(e));
+      }
+    } else {
+      rc = solve_rc;
+    }
+  }
+  if (op) adr_operator_destroy(op);
+  cudaStreamSynchronize(st);
+  cudaFree(dev);
+  if (info) *info = res;
+  if (rc != ADR_OK) return rc;
+  return solve_rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Travel-time factor tau1 on the device: the first-order upwind (Godunov)
+// discretisation of the factored eikonal equation
+//   |tau0 grad(tau1) + tau1 grad(tau0)|^2 = kappa^2   (Eq. factoredEikonal),
+// tau0 = |x - x0| with analytic gradient, relaxed in place to its fixed point.
+// Every node repeatedly solves its local quadratic from the current values
+// of its face neighbours and keeps the smaller of the old and new value, so
+// the iterate decreases monotonically from +inf and stops changing once the
+// discrete system is satisfied (the same fixed point a fast-marching ordering
+// reaches, without the sequential heap).  Axes whose neighbours are not
+// smaller contribute nothing (Godunov); a root that would be smaller than a
+// neighbour it used drops that axis.
+#include <cmath>
+#include <string>
+
+#include "adr_common.cuh"
+
+namespace adr {
+
+static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+struct EikParams {
+  int src[3];
+  double h[3];
+  int64_t js;
+};
+
+__global__ void k_eik_init(double* tau1, int64_t N, int64_t js, const double* kappa) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) tau1[i] = i == js ? kappa[js] : INFINITY;
+}
+
+template <int DIM>
+__global__ void k_eik_sweep(Dims g, EikParams P, const double* __restrict__ kappa, double* tau1, int* changed) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N || j == P.js) return;
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  double dx[3], r2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    dx[d] = (ii[d] - P.src[d]) * P.h[d];
+    r2 += dx[d] * dx[d];
+  }
+  const double r = sqrt(r2);
+  // best (smallest tau) neighbour per axis
+  double tnb[3], t1nb[3];
+  int side[3], ax[3];
+  int na = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int64_t stride = d == 0 ? 1 : (d == 1 ? g.s1 : g.s2);
+    double best = INFINITY, best1 = INFINITY;
+    int bs = 0;
+    for (int s = -1; s <= 1; s += 2) {
+      const int k = ii[d] + s;
+      if (k < 0 || k >= g.n[d]) continue;
+      const double t1 = tau1[j + s * stride];
+      if (!(t1 < INFINITY)) continue;
+      double rr = 0.0;
+#pragma unroll
+      for (int e = 0; e < DIM; ++e) {
+        const double de = (e == d) ? dx[e] + s * P.h[e] : dx[e];
+        rr += de * de;
+      }
+      const double t = sqrt(rr) * t1;
+      if (t < best) { best = t; best1 = t1; bs = s; }
+    }
+    if (bs != 0) { tnb[na] = best; t1nb[na] = best1; side[na] = bs; ax[na] = d; ++na; }
+  }
+  if (na == 0) return;
+  // sort the used axes by neighbour tau (insertion sort, <= 3 entries)
+  for (int a = 1; a < na; ++a)
+    for (int b = a; b > 0 && tnb[b] < tnb[b - 1]; --b) {
+      double t = tnb[b]; tnb[b] = tnb[b - 1]; tnb[b - 1] = t;
+      t = t1nb[b]; t1nb[b] = t1nb[b - 1]; t1nb[b - 1] = t;
+      int q = side[b]; side[b] = side[b - 1]; side[b - 1] = q;
+      q = ax[b]; ax[b] = ax[b - 1]; ax[b - 1] = q;
+    }
+  const double kj = kappa[j];
+  double cand = INFINITY;
+  for (int use = na; use >= 1; --use) {
+    double a2 = 0.0, a1 = 0.0, a0 = -kj * kj;
+    for (int a = 0; a < use; ++a) {
+      const int d = ax[a];
+      const double d0 = dx[d] / r;
+      const double A = -side[a] * r / P.h[d] + d0;
+      const double B = side[a] * r * t1nb[a] / P.h[d];
+      a2 += A * A;
+      a1 += 2.0 * A * B;
+      a0 += B * B;
+    }
+    double disc = a1 * a1 - 4.0 * a2 * a0;
+    if (disc < 0.0 && use == 1) disc = 0.0;
+    if (disc < 0.0) continue;
+    const double t = (-a1 + sqrt(disc)) / (2.0 * a2);
+    bool causal = true;
+    for (int a = 0; a < use; ++a) causal = causal && (r * t >= tnb[a]);
+    if (causal || use == 1) { cand = t; break; }
+  }
+  if (cand < tau1[j]) {
+    tau1[j] = cand;
+    *changed = 1;
+  }
+}
+
+}  // namespace adr
+
+using namespace adr;
+
+extern "C" int adr_traveltime(int dim, const int* n, const double* h, const int* src, const double* kappa, double* tau1,
+                              int max_sweeps, void* stream, int* sweeps_done) {
+  if ((dim != 2 && dim != 3) || !n || !h || !src || !kappa || !tau1 || max_sweeps < 1) return ADR_ERR_ARG;
+  for (int d = 0; d < dim; ++d)
+    if (n[d] < 2 || !(h[d] > 0.0) || src[d] < 0 || src[d] >= n[d]) return ADR_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Dims g = make_dims(dim, n);
+  EikParams P{};
+  for (int d = 0; d < 3; ++d) {
+    P.src[d] = d < dim ? src[d] : 0;
+    P.h[d] = d < dim ? h[d] : 1.0;
+  }
+  P.js = P.src[0] + g.s1 * P.src[1] + g.s2 * P.src[2];
+  int* flag = nullptr;
+  int* host_flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return ADR_ERR_OOM;
+  if (cudaMallocHost(&host_flag, sizeof(int)) != cudaSuccess) {
+    cudaFree(flag);
+    return ADR_ERR_OOM;
+  }
+  count_launches(1), k_eik_init<<<blocks_for(g.N, 256), 256, 0, st>>>(tau1, g.N, P.js, kappa);
+  int done = 0;
+  int rc = ADR_OK;
+  const int check_every = 16;
+  while (done < max_sweeps) {
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    for (int k = 0; k < check_every && done < max_sweeps; ++k, ++done) {
+      if (dim == 2) count_launches(1), k_eik_sweep<2><<<blocks_for(g.N, 256), 256, 0, st>>>(g, P, kappa, tau1, flag);
+      else count_launches(1), k_eik_sweep<3><<<blocks_for(g.N, 256), 256, 0, st>>>(g, P, kappa, tau1, flag);
+    }
+    if (cudaMemcpyAsync(host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = ADR_ERR_CUDA;
+      break;
+    }
+    if (*host_flag == 0) break;
+  }
+  if (rc == ADR_OK && cudaGetLastError() != cudaSuccess) rc = ADR_ERR_CUDA;
+  cudaFree(flag);
+  cudaFreeHost(host_flag);
+  if (sweeps_done) *sweeps_done = done;
+  if (rc == ADR_OK && done >= max_sweeps) rc = ADR_ERR_NOT_CONVERGED;
+  return rc;
+}

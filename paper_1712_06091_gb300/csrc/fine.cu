@@ -1,0 +1,420 @@
+// Fine-level (matrix-free) kernels of the ADR amplitude operator.
+//
+// Coefficients: Eq. travel_time_coeff with tau = tau0 tau1, tau0 = |x - x0|
+// (analytic derivatives), d tau1 by central differences (first-order
+// one-sided on the boundary), d^2 tau1 by central differences (second-order
+// one-sided on the boundary).  Rows: Eq. ADR with the Laplacian, the
+// advection of Eqs. londDiff / londUpwindDiff / 1up, the averaging mass of
+// Sec. 2.3 for the Delta-tau term, central advection next to the source
+// (Sec. 2.2), the Neumann condition of Eq. BCADR (n.grad a = i w (n.grad tau) a)
+// by ghost elimination, and the row of M^{-1} H M at the source (Eq. helmADR2).
+#include "adr_common.cuh"
+
+namespace adr {
+
+static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// ---------------------------------------------------------------------------
+// Coefficients
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double tau1_at(const Dims& g, const double* tau1, int64_t j, int d, int k_from, int k_to) {
+  const int64_t stride = d == 0 ? 1 : (d == 1 ? g.s1 : g.s2);
+  return tau1[j + (int64_t)(k_to - k_from) * stride];
+}
+
+__global__ void k_coefficients(Dims g, FineInputs in, double* g0, double* g1, double* g2, double* t0, double* t1,
+                               double* t2, double2* rho, double* tau) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  double dx[3], r2 = 0.0;
+  for (int d = 0; d < g.dim; ++d) {
+    dx[d] = (ii[d] - in.src[d]) * in.h[d];
+    r2 += dx[d] * dx[d];
+  }
+  const double r = sqrt(r2);
+  const double T1 = in.tau1[j];
+  double* gout[3] = {g0, g1, g2};
+  double* tout[3] = {t0, t1, t2};
+  double grad2 = 0.0;
+  for (int d = 0; d < g.dim; ++d) {
+    const int k = ii[d], n = g.n[d];
+    const double h = in.h[d];
+    double d1, dd1;
+    if (k == 0) {
+      d1 = (tau1_at(g, in.tau1, j, d, k, 1) - tau1_at(g, in.tau1, j, d, k, 0)) / h;
+      dd1 = (2.0 * tau1_at(g, in.tau1, j, d, k, 0) - 5.0 * tau1_at(g, in.tau1, j, d, k, 1) +
+             4.0 * tau1_at(g, in.tau1, j, d, k, 2) - tau1_at(g, in.tau1, j, d, k, 3)) / (h * h);
+    } else if (k == n - 1) {
+      d1 = (tau1_at(g, in.tau1, j, d, k, n - 1) - tau1_at(g, in.tau1, j, d, k, n - 2)) / h;
+      dd1 = (2.0 * tau1_at(g, in.tau1, j, d, k, n - 1) - 5.0 * tau1_at(g, in.tau1, j, d, k, n - 2) +
+             4.0 * tau1_at(g, in.tau1, j, d, k, n - 3) - tau1_at(g, in.tau1, j, d, k, n - 4)) / (h * h);
+    } else {
+      d1 = (tau1_at(g, in.tau1, j, d, k, k + 1) - tau1_at(g, in.tau1, j, d, k, k - 1)) / (2.0 * h);
+      dd1 = (tau1_at(g, in.tau1, j, d, k, k + 1) - 2.0 * T1 + tau1_at(g, in.tau1, j, d, k, k - 1)) / (h * h);
+    }
+    double d0 = 0.0, dd0 = 0.0;
+    if (r > 0.0) {
+      d0 = dx[d] / r;
+      dd0 = (1.0 - d0 * d0) / r;
+    }
+    const double gd = __dadd_rn(__dmul_rn(r, d1), __dmul_rn(T1, d0));
+    const double td = T1 * dd0 + 2.0 * d0 * d1 + r * dd1;
+    gout[d][j] = gd;
+    tout[d][j] = td;
+    grad2 += gd * gd;
+  }
+  const double k2 = in.kappa[j] * in.kappa[j];
+  rho[j] = make_double2(in.omega * in.omega * (k2 - grad2), -in.omega * in.gamma[j] * k2);
+  tau[j] = r * T1;
+}
+
+// Row of M^{-1} H M at the source (one thread).  H has its own Neumann ghost
+// u_{b+s} = u_{b-s}, so an off-grid neighbour folds onto its mirror.
+__global__ void k_source_row(Dims g, FineInputs in, const double* tau, double2* row) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k < kCross3; ++k) row[k] = make_double2(0.0, 0.0);
+  const int64_t js = in.src[0] + g.s1 * in.src[1] + g.s2 * in.src[2];
+  double cre = 0.0;
+  for (int d = 0; d < g.dim; ++d) {
+    const int64_t stride = d == 0 ? 1 : (d == 1 ? g.s1 : g.s2);
+    const double ih2 = 1.0 / (in.h[d] * in.h[d]);
+    for (int s = -1; s <= 1; s += 2) {
+      int k = in.src[d] + s;
+      int slot_s = s;  // slot that receives the coefficient
+      if (k < 0 || k >= g.n[d]) { k = in.src[d] - s; slot_s = -s; }
+      const double tn = tau[js + (int64_t)(k - in.src[d]) * stride];
+      double sn, cs;
+      sincos(in.omega * (0.0 - tn), &sn, &cs);
+      const int slot = 1 + 4 * d + (slot_s < 0 ? 0 : 1);
+      row[slot].x += cs * ih2;
+      row[slot].y += sn * ih2;
+      cre -= ih2;
+    }
+  }
+  const double k2 = in.kappa[js] * in.kappa[js];
+  row[0] = make_double2(cre + in.omega * in.omega * k2, -in.omega * in.gamma[js] * k2);
+}
+
+void launch_coefficients(const Dims& g, const FineInputs& in, double* const gd[3], double* const td[3], double2* rho,
+                         double* tau, double2* src_row, cudaStream_t st) {
+  const int th = 256;
+  count_launches(1), k_coefficients<<<blocks_for(g.N, th), th, 0, st>>>(g, in, gd[0], gd[1], gd[2], td[0], td[1], td[2], rho, tau);
+  count_launches(1), k_source_row<<<1, 32, 0, st>>>(g, in, tau, src_row);
+}
+
+__global__ void k_to_f32(const double* s, float* d, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (float)s[i];
+}
+void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
+  count_launches(1), k_to_f32<<<blocks_for(n, 256), 256, 0, st>>>(src, dst, n);
+}
+
+// ---------------------------------------------------------------------------
+// The fine row
+// ---------------------------------------------------------------------------
+// Writes the row of node j (coordinates ii) in cross form into c[1 + 4*DIM].
+template <int DIM, typename T>
+__device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int64_t j, const int ii[3], C<T>* c) {
+  if (j == f.src_index) {
+    c[0] = f.src_row[0];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[1 + 4 * d + q] = f.src_row[1 + 4 * d + q];
+    }
+    return;
+  }
+  bool near = true;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) near = near && (abs(ii[d] - f.src[d]) <= f.near);
+  const C<T> rho = f.rho[j];
+  T cre = rho.x, cim = rho.y;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const T gd = f.g[d][j];
+    const T td = f.t[d][j];
+    const T h = f.h[d];
+    const T ih2 = f.ih2[d];
+    const int k = ii[d], n = g.n[d];
+    T re_m1 = ih2, re_p1 = ih2;
+    T im_m1 = T(-0.5) * f.omega * td, im_p1 = im_m1;
+    cre -= T(2) * ih2;
+    // advection difference weights at offsets -2..+2
+    T wm2 = 0, wm1 = 0, w0 = 0, wp1 = 0, wp2 = 0;
+    const T half_ih = T(0.5) / h;
+    if (near || gd == T(0) || (f.central && k > 0 && k < n - 1)) {
+      wp1 = half_ih; wm1 = -half_ih;
+    } else {
+      const T a2 = f.central ? T(1) : f.w2;
+      const T a1 = f.central ? T(0) : f.w1;
+      if (a2 != T(0)) {
+        if (gd > T(0)) {
+          if (k >= 2) { w0 += a2 * T(3) * half_ih; wm1 -= a2 * T(4) * half_ih; wm2 += a2 * half_ih; }
+          else { wp1 += a2 * half_ih; wm1 -= a2 * half_ih; }
+        } else {
+          if (k <= n - 3) { w0 -= a2 * T(3) * half_ih; wp1 += a2 * T(4) * half_ih; wp2 -= a2 * half_ih; }
+          else { wp1 += a2 * half_ih; wm1 -= a2 * half_ih; }
+        }
+      }
+      if (a1 != T(0)) {
+        const T ih = T(1) / h;
+        if (gd > T(0)) {
+          if (k >= 1) { w0 += a1 * ih; wm1 -= a1 * ih; }
+          else { wp1 += a1 * half_ih; wm1 -= a1 * half_ih; }
+        } else {
+          if (k <= n - 2) { w0 -= a1 * ih; wp1 += a1 * ih; }
+          else { wp1 += a1 * half_ih; wm1 -= a1 * half_ih; }
+        }
+      }
+    }
+    const T adv = T(-2) * f.omega * gd;  // -2 i w (d_d tau) D_d: imaginary factor
+    im_m1 += adv * wm1;
+    im_p1 += adv * wp1;
+    cim += adv * w0;
+    const T im_m2 = adv * wm2, im_p2 = adv * wp2;
+    // Neumann ghost (Eq. BCADR read with the factor a): a_{b+s} = a_{b-s} + s 2 h i w g a_b
+    if (k == 0) {
+      const T fac = T(-2) * h * f.omega * gd;  // ghost adds (i fac) a_b per unit coefficient
+      re_p1 += re_m1; im_p1 += im_m1;
+      cre -= im_m1 * fac; cim += re_m1 * fac;
+      re_m1 = 0; im_m1 = 0;
+    }
+    if (k == n - 1) {
+      const T fac = T(2) * h * f.omega * gd;
+      re_m1 += re_p1; im_m1 += im_p1;
+      cre -= im_p1 * fac; cim += re_p1 * fac;
+      re_p1 = 0; im_p1 = 0;
+    }
+    c[1 + 4 * d + 0] = mk<T>(re_m1, im_m1);
+    c[1 + 4 * d + 1] = mk<T>(re_p1, im_p1);
+    c[1 + 4 * d + 2] = mk<T>(T(0), im_m2);
+    c[1 + 4 * d + 3] = mk<T>(T(0), im_p2);
+  }
+  c[0] = mk<T>(cre, cim);
+}
+
+template <int DIM> __device__ __forceinline__ int64_t axis_stride(const Dims& g, int d) {
+  return d == 0 ? 1 : (d == 1 ? g.s1 : g.s2);
+}
+
+// sum_k c_k x_{j + o_k} over the in-grid cross entries
+template <int DIM, typename T>
+__device__ __forceinline__ C<T> cross_dot(const Dims& g, const C<T>* c, const int ii[3], int64_t j, const C<T>* x) {
+  C<T> acc = cmul(c[0], x[j]);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int64_t s = axis_stride<DIM>(g, d);
+    const int k = ii[d], n = g.n[d];
+    if (k >= 1) acc = cfma(c[1 + 4 * d + 0], x[j - s], acc);
+    if (k <= n - 2) acc = cfma(c[1 + 4 * d + 1], x[j + s], acc);
+    if (k >= 2) acc = cfma(c[1 + 4 * d + 2], x[j - 2 * s], acc);
+    if (k <= n - 3) acc = cfma(c[1 + 4 * d + 3], x[j + 2 * s], acc);
+  }
+  return acc;
+}
+
+template <int DIM, typename T>
+__global__ void k_fine_apply(Dims g, FineOp<T> f, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  C<T> c[1 + 4 * DIM];
+  fine_row<DIM, T>(g, f, j, ii, c);
+  y[j] = cross_dot<DIM, T>(g, c, ii, j, x);
+}
+
+template <int DIM, typename T>
+__global__ void k_fine_residual(Dims g, FineOp<T> f, const C<T>* __restrict__ b, const C<T>* __restrict__ x,
+                                C<T>* __restrict__ r) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  C<T> c[1 + 4 * DIM];
+  fine_row<DIM, T>(g, f, j, ii, c);
+  r[j] = csub(b[j], cross_dot<DIM, T>(g, c, ii, j, x));
+}
+
+template <int DIM, typename T>
+__global__ void k_fine_jacobi(Dims g, FineOp<T> f, const C<T>* __restrict__ b, const C<T>* __restrict__ xin,
+                              C<T>* __restrict__ xout, T w) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  C<T> c[1 + 4 * DIM];
+  fine_row<DIM, T>(g, f, j, ii, c);
+  const C<T> dinv = cinv(c[0]);
+  if (xin == nullptr) {
+    xout[j] = cscale(cmul(dinv, b[j]), w);
+  } else {
+    const C<T> r = csub(b[j], cross_dot<DIM, T>(g, c, ii, j, xin));
+    xout[j] = cadd(xin[j], cscale(cmul(dinv, r), w));
+  }
+}
+
+template <int DIM, typename T>
+__global__ void k_fine_dinv(Dims g, FineOp<T> f, const C<T>* __restrict__ v, C<T>* __restrict__ z) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  C<T> c[1 + 4 * DIM];
+  fine_row<DIM, T>(g, f, j, ii, c);
+  const C<T> dinv = cinv(c[0]);
+  z[j] = v ? cmul(dinv, v[j]) : dinv;
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin product P^T A P from the fine operator (Eq. coarseGridMatrix).
+// One thread per coarse node I accumulates the point-major stencil row
+//   A_c[I, J] = sum_i sum_k P[i, I] A[i, k] P[k, J]
+// over the fine nodes i next to 2I and the entries k of their rows.
+// ---------------------------------------------------------------------------
+template <int DIM, typename T, typename RowFn>
+__device__ __forceinline__ void galerkin_accumulate(const Dims& gf, const Dims& gc, int64_t I, const int Ii[3],
+                                                    RowFn row_of, C<T>* acc) {
+  constexpr int S = PatternSize<DIM>::value;
+  for (int p = 0; p < S; ++p) acc[p] = czero<T>();
+  const int dlo2 = DIM > 2 ? -1 : 0, dhi2 = DIM > 2 ? 1 : 0;
+  for (int e2 = dlo2; e2 <= dhi2; ++e2)
+    for (int e1 = -1; e1 <= 1; ++e1)
+      for (int e0 = -1; e0 <= 1; ++e0) {
+        int fi[3] = {2 * Ii[0] + e0, 2 * Ii[1] + e1, DIM > 2 ? 2 * Ii[2] + e2 : 0};
+        bool ok = true;
+        for (int d = 0; d < DIM; ++d) ok = ok && fi[d] >= 0 && fi[d] < gf.n[d];
+        if (!ok) continue;
+        const T wi = (e0 ? T(0.5) : T(1)) * (e1 ? T(0.5) : T(1)) * (e2 ? T(0.5) : T(1));
+        const int64_t fj = fi[0] + gf.s1 * fi[1] + gf.s2 * fi[2];
+        row_of(fj, fi, [&](int o0, int o1, int o2, C<T> a) {
+          const int k[3] = {fi[0] + o0, fi[1] + o1, fi[2] + o2};
+          const C<T> wa = cscale(a, wi);
+          // parents of k along each axis
+          int pj[3][2];
+          T pw[3][2];
+          int pc[3];
+          for (int d = 0; d < 3; ++d) {
+            if (d >= DIM) { pj[d][0] = 0; pw[d][0] = T(1); pc[d] = 1; continue; }
+            if ((k[d] & 1) == 0) { pj[d][0] = k[d] >> 1; pw[d][0] = T(1); pc[d] = 1; }
+            else { pj[d][0] = (k[d] - 1) >> 1; pj[d][1] = (k[d] + 1) >> 1; pw[d][0] = pw[d][1] = T(0.5); pc[d] = 2; }
+          }
+          for (int q2 = 0; q2 < pc[2]; ++q2)
+            for (int q1 = 0; q1 < pc[1]; ++q1)
+              for (int q0 = 0; q0 < pc[0]; ++q0) {
+                const int s = pattern_slot<DIM>(pj[0][q0] - Ii[0], pj[1][q1] - Ii[1], DIM > 2 ? pj[2][q2] - Ii[2] : 0);
+                const T pwt = pw[0][q0] * pw[1][q1] * pw[2][q2];
+                acc[s] = cadd(acc[s], cscale(wa, pwt));
+              }
+        });
+      }
+}
+
+template <int DIM, typename T>
+__global__ void k_galerkin_fine(Dims gf, Dims gc, FineOp<T> f, C<T>* __restrict__ out, C<T>* __restrict__ dinv) {
+  constexpr int S = PatternSize<DIM>::value;
+  int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= gc.N) return;
+  int Ii[3];
+  unravel(gc, I, Ii[0], Ii[1], Ii[2]);
+  C<T> acc[S];
+  auto row_of = [&](int64_t fj, const int fi[3], auto emit) {
+    C<T> c[1 + 4 * DIM];
+    fine_row<DIM, T>(gf, f, fj, fi, c);
+    emit(0, 0, 0, c[0]);
+    for (int d = 0; d < DIM; ++d) {
+      const int k = fi[d], n = gf.n[d];
+      int o[3] = {0, 0, 0};
+      if (k >= 1) { o[d] = -1; emit(o[0], o[1], o[2], c[1 + 4 * d + 0]); }
+      if (k <= n - 2) { o[d] = 1; emit(o[0], o[1], o[2], c[1 + 4 * d + 1]); }
+      if (k >= 2) { o[d] = -2; emit(o[0], o[1], o[2], c[1 + 4 * d + 2]); }
+      if (k <= n - 3) { o[d] = 2; emit(o[0], o[1], o[2], c[1 + 4 * d + 3]); }
+    }
+  };
+  galerkin_accumulate<DIM, T>(gf, gc, I, Ii, row_of, acc);
+  for (int p = 0; p < S; ++p) out[(int64_t)p * gc.N + I] = acc[p];
+  dinv[I] = cinv(acc[(S - 1) / 2]);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename T> void launch_fine_apply(const Dims& g, const FineOp<T>& f, const C<T>* x, C<T>* y, cudaStream_t st) {
+  const int th = 256;
+  if (g.dim == 2) count_launches(1), k_fine_apply<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, x, y);
+  else count_launches(1), k_fine_apply<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, x, y);
+}
+template <typename T> void launch_fine_residual(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* x, C<T>* r, cudaStream_t st) {
+  const int th = 256;
+  if (g.dim == 2) count_launches(1), k_fine_residual<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, b, x, r);
+  else count_launches(1), k_fine_residual<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, b, x, r);
+}
+template <typename T> void launch_fine_jacobi(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* xin, C<T>* xout, T w, cudaStream_t st) {
+  const int th = 256;
+  if (g.dim == 2) count_launches(1), k_fine_jacobi<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, b, xin, xout, w);
+  else count_launches(1), k_fine_jacobi<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, b, xin, xout, w);
+}
+template <typename T> void launch_fine_dinv(const Dims& g, const FineOp<T>& f, const C<T>* v, C<T>* z, cudaStream_t st) {
+  const int th = 256;
+  if (g.dim == 2) count_launches(1), k_fine_dinv<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, v, z);
+  else count_launches(1), k_fine_dinv<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, v, z);
+}
+template <typename T> void launch_galerkin_fine(const Dims& gf, const Dims& gc, const FineOp<T>& f, C<T>* stencil, C<T>* dinv, cudaStream_t st) {
+  const int th = 64;
+  if (gf.dim == 2) count_launches(1), k_galerkin_fine<2, T><<<blocks_for(gc.N, th), th, 0, st>>>(gf, gc, f, stencil, dinv);
+  else count_launches(1), k_galerkin_fine<3, T><<<blocks_for(gc.N, th), th, 0, st>>>(gf, gc, f, stencil, dinv);
+}
+
+#define ADR_INSTANTIATE_FINE(T)                                                                                     \
+  template void launch_fine_apply<T>(const Dims&, const FineOp<T>&, const C<T>*, C<T>*, cudaStream_t);               \
+  template void launch_fine_residual<T>(const Dims&, const FineOp<T>&, const C<T>*, const C<T>*, C<T>*, cudaStream_t); \
+  template void launch_fine_jacobi<T>(const Dims&, const FineOp<T>&, const C<T>*, const C<T>*, C<T>*, T, cudaStream_t); \
+  template void launch_fine_dinv<T>(const Dims&, const FineOp<T>&, const C<T>*, C<T>*, cudaStream_t);                \
+  template void launch_galerkin_fine<T>(const Dims&, const Dims&, const FineOp<T>&, C<T>*, C<T>*, cudaStream_t);
+ADR_INSTANTIATE_FINE(double)
+ADR_INSTANTIATE_FINE(float)
+
+// ---------------------------------------------------------------------------
+// Point source, reconstruction, coefficient export
+// ---------------------------------------------------------------------------
+__global__ void k_rhs_point(double2* q, int64_t N, int64_t src, double value) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) q[i] = make_double2(i == src ? value : 0.0, 0.0);
+}
+void launch_rhs_point(double2* q, int64_t N, int64_t src_index, double value, cudaStream_t st) {
+  count_launches(1), k_rhs_point<<<blocks_for(N, 256), 256, 0, st>>>(q, N, src_index, value);
+}
+
+__global__ void k_reconstruct(const double2* a, const double* tau, double omega, double2* u, int64_t N) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double s, c;
+  sincos(-omega * tau[i], &s, &c);
+  u[i] = cmul(a[i], make_double2(c, s));
+}
+void launch_reconstruct(const double2* a, const double* tau, double omega, double2* u, int64_t N, cudaStream_t st) {
+  count_launches(1), k_reconstruct<<<blocks_for(N, 256), 256, 0, st>>>(a, tau, omega, u, N);
+}
+
+__global__ void k_pack(Dims g, const double* g0, const double* g1, const double* g2, const double* t0, const double* t1,
+                       const double* t2, const double2* rho, const double* tau, double* out) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  const double* gs[3] = {g0, g1, g2};
+  const double* ts[3] = {t0, t1, t2};
+  int k = 0;
+  for (int d = 0; d < g.dim; ++d) out[(k++) * g.N + j] = gs[d][j];
+  for (int d = 0; d < g.dim; ++d) out[(k++) * g.N + j] = ts[d][j];
+  out[(k++) * g.N + j] = rho[j].x;
+  out[(k++) * g.N + j] = rho[j].y;
+  out[(k++) * g.N + j] = tau[j];
+}
+void launch_pack_coefficients(const Dims& g, const double* const gd[3], const double* const td[3], const double2* rho,
+                              const double* tau, double* out, cudaStream_t st) {
+  count_launches(1), k_pack<<<blocks_for(g.N, 256), 256, 0, st>>>(g, gd[0], gd[1], gd[2], td[0], td[1], td[2], rho, tau, out);
+}
+
+}  // namespace adr

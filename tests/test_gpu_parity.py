@@ -1,0 +1,221 @@
+"""GPU path vs the oracle, element by element, through the C ABI.
+
+Tolerances (float64 arithmetic, unit roundoff 1.1e-16):
+  * coefficients and single operator applications: 1e-12 relative (a few
+    dozen roundings of terms of equal sign; FMA contraction differs);
+  * Galerkin stencils: 1e-12 relative to the largest entry of the level;
+  * one multigrid cycle and fixed-count FGMRES iterates: 1e-10 relative L2
+    (the solver's parity target; rounding differences are amplified by the
+    Krylov recurrences and the nonlinear fixed-count coarse solves);
+  * float32 applications: 1e-5 relative (unit roundoff 6e-8 times the
+    cancellation between the Laplacian and the reaction terms).
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import adr, krylov
+from oracle import multigrid as mg
+from paper_1712_06091_gb300 import workloads as W
+
+from gpu_cases import CASES, make_operator, oracle_cycle_params, oracle_matrix, pattern_offsets, problem, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+NAMES = list(CASES)
+
+
+def _cvec(x, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dtype).cuda()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_coefficients(adrlib, cuda, name):
+    P, _, op = make_operator(name)
+    got = op.coefficients().cpu().numpy()
+    g = adr.Grid(P.n, P.h)
+    D = len(P.n)
+    ref = np.zeros_like(got)
+    for j in range(g.N):
+        tau, gr, t, rho = adr.node_coefficients(g, P.src, P.omega, P.kappa, P.gamma, P.tau1, j)
+        ref[:D, j] = gr
+        ref[D:2 * D, j] = t
+        ref[2 * D, j] = rho.real
+        ref[2 * D + 1, j] = rho.imag
+        ref[2 * D + 2, j] = tau
+    js = g.index(P.src)
+    mask = np.ones(g.N, bool)
+    mask[js] = False       # derivatives at the source are never used (its row is M^-1 H M)
+    for k in range(got.shape[0]):
+        scale = max(np.abs(ref[k, mask]).max(), 1e-300)
+        if k == 2 * D:      # Re rho = w^2 (kappa^2 - |grad tau|^2) cancels: compare on the scale of w^2 kappa^2
+            scale = P.omega ** 2 * np.max(P.kappa) ** 2
+        assert np.abs(got[k, mask] - ref[k, mask]).max() <= 1e-12 * scale, (name, k)
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("scheme", ["2up", "1up", "cen", "prec"])
+def test_apply_f64(adrlib, cuda, name, scheme):
+    P, _, op = make_operator(name)
+    A = oracle_matrix(name, scheme)
+    x = W.random_complex(A.shape[0], 7)
+    y = op.apply(_cvec(x), scheme).cpu().numpy()
+    ref = A @ x
+    err = np.abs(y - ref).max() / np.abs(ref).max()
+    assert err <= 1e-12, (name, scheme, err)
+
+
+@pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17"])
+def test_apply_f32(adrlib, cuda, name):
+    P, _, op = make_operator(name)
+    A = oracle_matrix(name, "2up")
+    x = W.random_complex(A.shape[0], 8)
+    y = op.apply(_cvec(x, torch.complex64), "2up").cpu().numpy()
+    ref = A @ x
+    assert np.abs(y - ref).max() / np.abs(ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("near", [1, 2])
+def test_apply_near_source_radius(adrlib, cuda, near):
+    P, _, op = make_operator("marine2d_65", near_source=near)
+    A = oracle_matrix("marine2d_65", "2up", near)
+    x = W.random_complex(A.shape[0], 9)
+    y = op.apply(_cvec(x), "2up").cpu().numpy()
+    assert np.abs(y - A @ x).max() / np.abs(A @ x).max() <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["const2d_33", "ragged2d_37x21", "marine2d_65", "const3d_17x13x9", "layered3d_17"])
+def test_galerkin_stencils(adrlib, cuda, name):
+    P, params, op = make_operator(name, precision="f64")
+    hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
+    info = op.info()
+    assert [lv["n"] for lv in info["levels"]] == [tuple(lv["n"]) for lv in hier]
+    offs = pattern_offsets(len(P.n))
+    for l in range(1, len(hier)):
+        st = op.level_stencil(l).cpu().numpy()
+        Ac = hier[l]["A"].tocsr()
+        gc = adr.Grid(hier[l]["n"], (1.0,) * len(P.n))
+        dense = np.zeros_like(st)
+        for I in range(gc.N):
+            ci = gc.coords(I)
+            row = dict(zip(Ac[I].indices, Ac[I].data))
+            seen = 0
+            for p, o in enumerate(offs):
+                cj = tuple(ci[d] + o[d] for d in range(len(o)))
+                if gc.inside(cj):
+                    J = gc.index(cj)
+                    dense[p, I] = row.get(J, 0.0)
+                    seen += J in row
+            assert seen == len(row), "oracle entry outside the pattern"
+        scale = np.abs(dense).max()
+        assert np.abs(st - dense).max() <= 1e-12 * scale, (name, l)
+
+
+CYCLES = [
+    dict(),                                                   # K-cycle, MR relaxation, l+1 sweeps
+    dict(cycle="V", levels=3),
+    dict(cycle="V", relax="jacobi", sweeps=1, jacobi_weight=[0.6, 0.5, 0.4, 0.4, 0.4]),
+    dict(levels=1, coarse_iterations=7),
+    dict(kcycle_iterations=3, sweeps=[1, 2, 1], coarse_iterations=5),
+]
+
+
+@pytest.mark.parametrize("name", ["const2d_33", "ragged2d_37x21", "marine2d_65", "layered3d_17", "corner3d_9x11x13"])
+@pytest.mark.parametrize("ci", range(len(CYCLES)))
+def test_cycle_f64(adrlib, cuda, name, ci):
+    P, params, op = make_operator(name, precision="f64", **CYCLES[ci])
+    hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
+    prm = oracle_cycle_params(params)
+    r = W.random_complex(hier[0]["A"].shape[0], 11)
+    z = op.vcycle(_cvec(r)).cpu().numpy()
+    ref = mg.cycle(hier, r, prm)
+    assert rel(z, ref) <= 1e-10, (name, ci, rel(z, ref))
+
+
+@pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17"])
+def test_cycle_f32(adrlib, cuda, name):
+    P, params, op = make_operator(name, precision="f32")
+    hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
+    r = W.random_complex(hier[0]["A"].shape[0], 12)
+    z = op.vcycle(_cvec(r, torch.complex64)).cpu().numpy()
+    ref = mg.cycle(hier, r, oracle_cycle_params(params))
+    assert rel(z, ref) <= 2e-4, rel(z, ref)
+
+
+@pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17", "corner3d_9x11x13"])
+@pytest.mark.parametrize("k,m", [(7, 20), (9, 4)])
+def test_fgmres_iterates(adrlib, cuda, name, k, m):
+    """Same algorithm, fixed iteration count: iterate-for-iterate parity."""
+    P, params, op = make_operator(name, precision="f64", restart=m)
+    A = oracle_matrix(name, "2up")
+    hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
+    prm = oracle_cycle_params(params)
+    q = adr.point_source_rhs(adr.Grid(P.n, P.h), P.src)
+    x_ref, its, res, _ = krylov.fgmres(A, q, lambda v: mg.cycle(hier, v, prm), tol=0.0, restart=m, maxit=k)
+    a, info = op.solve(tol=0.0, maxit=k, raise_on_fail=False)
+    assert info["iterations"] == its == k
+    assert rel(a.cpu().numpy(), x_ref) <= 1e-10
+    assert abs(info["rel_residual"] - res) <= 1e-8 * max(res, 1e-300) + 1e-14
+
+
+@pytest.mark.parametrize("name", ["const2d_33", "ragged2d_37x21", "marine2d_65", "const3d_17x13x9", "layered3d_17"])
+def test_solve_f64_to_direct(adrlib, cuda, name):
+    P, params, op = make_operator(name, precision="f64")
+    A = oracle_matrix(name, "2up")
+    q = adr.point_source_rhs(adr.Grid(P.n, P.h), P.src)
+    xe = spla.spsolve(A.tocsc(), q)
+    a, info = op.solve(tol=1e-12, maxit=400)
+    assert info["rel_residual"] <= 1e-12
+    assert rel(a.cpu().numpy(), xe) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17"])
+def test_solve_mixed_precision(adrlib, cuda, name):
+    """float32 cycle inside the float64 FGMRES: the float64 residual still reaches 1e-8."""
+    P, params, op = make_operator(name, precision="f32")
+    A = oracle_matrix(name, "2up")
+    q = adr.point_source_rhs(adr.Grid(P.n, P.h), P.src)
+    a, info = op.solve(tol=1e-8, maxit=400)
+    a = a.cpu().numpy()
+    true_res = np.linalg.norm(q - A @ a) / np.linalg.norm(q)
+    assert true_res <= 1.0000001e-8
+    assert abs(true_res - info["rel_residual"]) <= 1e-12
+    xe = spla.spsolve(A.tocsc(), q)
+    # solution error bounded by the residual times the conditioning of H_2up
+    assert rel(a, xe) <= 1e-5
+
+
+def test_point_source_and_reconstruct(adrlib, cuda):
+    P, _, op = make_operator("marine2d_65")
+    g = adr.Grid(P.n, P.h)
+    q = op.point_source_rhs().cpu().numpy()
+    assert np.array_equal(q, adr.point_source_rhs(g, P.src))
+    a = W.random_complex(g.N, 3)
+    u = op.reconstruct(_cvec(a)).cpu().numpy()
+    ref = adr.reconstruct(g, P.src, P.omega, P.tau1, a)
+    assert np.abs(u - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_host_pipeline_matches_device(adrlib, cuda):
+    from paper_1712_06091_gb300 import adr as gpu
+    P, params, op = make_operator("marine2d_65")
+    a_dev, info_dev = op.solve(tol=1e-8, maxit=300)
+    u_dev = op.reconstruct(a_dev).cpu().numpy()
+    u, a, info = gpu.solve_host(P.n, P.h, P.src, P.omega, P.kappa, P.tau1, P.gamma, params=params, tol=1e-8,
+                                maxit=300, want_amplitude=True)
+    assert info["iterations"] == info_dev["iterations"]
+    assert np.array_equal(a, a_dev.cpu().numpy())
+    assert np.array_equal(u, u_dev)
+
+
+def test_not_converged_and_zero_rhs(adrlib, cuda):
+    from paper_1712_06091_gb300 import adr as gpu
+    P, params, op = make_operator("const2d_33")
+    a, info = op.solve(tol=1e-14, maxit=2, raise_on_fail=False)
+    assert info["status"] == gpu.L.ADR_ERR_NOT_CONVERGED and info["iterations"] == 2
+    with pytest.raises(gpu.ADRError):
+        op.solve(tol=1e-14, maxit=2)
+    z = torch.zeros(op.N, dtype=torch.complex128, device="cuda")
+    a, info = op.solve(rhs=z, tol=1e-8)
+    assert info["iterations"] == 0 and torch.count_nonzero(a) == 0
