@@ -159,14 +159,21 @@ constexpr int kCross2 = 9;
 constexpr int kCross3 = 13;
 template <int DIM> struct CrossSize { static constexpr int value = 1 + 4 * DIM; };
 
+// Per-source values read by the fine-level kernels from device memory, so a
+// captured CUDA graph stays valid when the operator is rebuilt for another
+// source or frequency.
+struct FineDyn {
+  double omega;
+  int src[3];
+  int64_t src_index;
+};
+
 template <typename T> struct FineOp {
+  const FineDyn* dyn;  // omega and the source (device)
   const T* g[3];     // d_d tau
   const T* t[3];     // d_dd tau
   const C<T>* rho;   // w^2 (kappa^2 - |grad tau|^2) - i w gamma kappa^2
   const C<T>* src_row;    // row of M^{-1} H M at the source (cross form, device)
-  int src[3];
-  int64_t src_index;
-  T omega;
   T h[3];
   T ih2[3];
   T w2, w1;          // weights of the second- and first-order upwind differences
@@ -208,6 +215,14 @@ template <typename T> void launch_fine_residual(const Dims& g, const FineOp<T>& 
 template <typename T> void launch_fine_jacobi(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* xin, C<T>* xout, T w, cudaStream_t st);
 // z = D^{-1} v, or z = diag(A)^{-1} itself when v is null
 template <typename T> void launch_fine_dinv(const Dims& g, const FineOp<T>& f, const C<T>* v, C<T>* z, cudaStream_t st);
+// Fused minimal-residual sweep pieces: w = A z with alpha = (w^H r)/(w^H w)
+// reduced by the last block; r = b - A x with z = D^{-1} r.
+template <typename T> void launch_fine_mr_apply(const Dims& g, const FineOp<T>& f, const C<T>* z, const C<T>* r, C<T>* w,
+                                                double2* partial, unsigned* ticket, double2* alpha, cudaStream_t st);
+template <typename T> void launch_fine_residual_dinv(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* x,
+                                                     const C<T>* dinv, C<T>* r, C<T>* z, cudaStream_t st);
+// Writes the per-source values read by the fine kernels.
+void launch_set_dyn(FineDyn* d, const FineDyn& v, cudaStream_t st);
 // Galerkin product of the fine operator into the stored stencil of level 1.
 template <typename T> void launch_galerkin_fine(const Dims& gf, const Dims& gc, const FineOp<T>& f, C<T>* stencil, C<T>* dinv, cudaStream_t st);
 
@@ -215,6 +230,10 @@ template <typename T> void launch_galerkin_fine(const Dims& gf, const Dims& gc, 
 template <typename T> void launch_stencil_apply(const Dims& g, const C<T>* A, const C<T>* x, C<T>* y, cudaStream_t st);
 template <typename T> void launch_stencil_residual(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x, C<T>* r, cudaStream_t st);
 template <typename T> void launch_stencil_jacobi(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, const C<T>* xin, C<T>* xout, T w, cudaStream_t st);
+template <typename T> void launch_stencil_mr_apply(const Dims& g, const C<T>* A, const C<T>* z, const C<T>* r, C<T>* w,
+                                                   double2* partial, unsigned* ticket, double2* alpha, cudaStream_t st);
+template <typename T> void launch_stencil_residual_dinv(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x,
+                                                        const C<T>* dinv, C<T>* r, C<T>* z, cudaStream_t st);
 template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st);
 
 // Transfers.

@@ -84,15 +84,8 @@ template <typename T> struct Level {
   ArnoldiState ks{};
 };
 
-struct Scratch {
-  double2* partial = nullptr;  // kMaxReduceBlocks x kMaxDots
-  double2* ha = nullptr;       // first Gram-Schmidt pass
-  double2* hb = nullptr;       // second pass
-  double2* nrm2 = nullptr;     // squared norm
-  double2* d2 = nullptr;       // MR dots
-  double2* alpha = nullptr;    // MR weight
-};
-constexpr int kMaxDots = 66;
+constexpr int kMaxDots = kMaxKrylov + 2;
+constexpr int64_t kSmallCoarse = 8192;  // coarsest grids up to this size are solved by one block
 
 static void take_arnoldi(Arena& a, ArnoldiState& s, int m) {
   s.m = m;
@@ -138,7 +131,13 @@ struct Op {
   double2* b = nullptr;  // point-source right-hand side
   double2* r = nullptr;
   ArnoldiState ost{};
-  Scratch sc;
+  KrylovScratch ks{};
+  FineDyn* dyn = nullptr;           // omega and the source, read by the fine kernels
+  // the cycle below the float64 Krylov loop, captured once and replayed
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t cycle_exec = nullptr;
+  long long cycle_kernels = 0;
+  bool use_graph = true;
   void* arena = nullptr;
   size_t arena_bytes = 0;
   double* host_scal = nullptr;  // pinned: [0] estimate, [1] hn, [2] norm^2
@@ -207,12 +206,13 @@ static void plan(Op& op, Arena& a) {
   op.b = a.take<double2>(N);
   op.r = a.take<double2>(N);
   take_arnoldi(a, op.ost, m);
-  op.sc.partial = a.take<double2>((size_t)kMaxReduceBlocks * kMaxDots);
-  op.sc.ha = a.take<double2>(kMaxDots);
-  op.sc.hb = a.take<double2>(kMaxDots);
-  op.sc.nrm2 = a.take<double2>(1);
-  op.sc.d2 = a.take<double2>(2);
-  op.sc.alpha = a.take<double2>(1);
+  op.ks.partial = a.take<double2>((size_t)kMaxReduceBlocks * kMaxDots);
+  op.ks.ticket = a.take<unsigned>(1);
+  op.ks.ha = a.take<double2>(kMaxDots);
+  op.ks.hb = a.take<double2>(kMaxDots);
+  op.ks.nrm2 = a.take<double2>(1);
+  op.ks.alpha = a.take<double2>(1);
+  op.dyn = a.take<FineDyn>(1);
 }
 
 template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool f32) {
@@ -226,12 +226,10 @@ template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool 
     } else {
       f.g[d] = nullptr; f.t[d] = nullptr; f.h[d] = T(1); f.ih2[d] = T(0);
     }
-    f.src[d] = op.src[d];
   }
+  f.dyn = op.dyn;
   f.rho = f32 ? (const C<T>*)(const void*)op.rhof : (const C<T>*)(const void*)op.rho;
   f.src_row = f32 ? (const C<T>*)(const void*)op.srowf : (const C<T>*)(const void*)op.srow;
-  f.src_index = op.src_index;
-  f.omega = (T)op.omega;
   f.near = op.p.near_source;
   set_scheme(f, scheme, op.p.beta);
   return f;
@@ -257,15 +255,21 @@ template <typename T> struct Cycle {
     if (l == 0) launch_fine_jacobi<T>(H.lv[0].g, H.prec, b, xin, xout, w, st);
     else launch_stencil_jacobi<T>(H.lv[l].g, H.lv[l].A, H.lv[l].dinv, b, xin, xout, w, st);
   }
-  void norm2(const C<T>* v, int64_t n, double2* out) {
-    launch_dots<T>(v, 0, 1, v, n, op.sc.partial, out, st);
+  void residual_dinv(int l, const C<T>* b, const C<T>* x, C<T>* r, C<T>* z) {
+    if (l == 0) launch_fine_residual_dinv<T>(H.lv[0].g, H.prec, b, x, H.lv[0].dinv, r, z, st);
+    else launch_stencil_residual_dinv<T>(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, st);
+  }
+  void mr_apply(int l, const C<T>* z, const C<T>* r, C<T>* w) {
+    if (l == 0) launch_fine_mr_apply<T>(H.lv[0].g, H.prec, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
+    else launch_stencil_mr_apply<T>(H.lv[l].g, H.lv[l].A, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
   }
 
   // `sweeps` relaxations on A_l x = b; x_zero says x holds zero on entry.
-  void relax(int l, const C<T>* b, C<T>* x, int sweeps, bool& x_zero) {
+  // Returns true when L.r holds b - A x afterwards.
+  bool relax(int l, const C<T>* b, C<T>* x, int sweeps, bool& x_zero) {
     Level<T>& L = H.lv[l];
     const int64_t n = L.g.N;
-    if (sweeps <= 0) return;
+    if (sweeps <= 0) return false;
     if (op.p.relax == ADR_RELAX_JACOBI) {
       const T w = (T)op.p.jacobi_weight[l];
       C<T>* cur = x;
@@ -276,31 +280,33 @@ template <typename T> struct Cycle {
         C<T>* tmp = cur; cur = oth; oth = tmp;
       }
       if (cur != x) launch_copy<T>(cur, x, n, st);
-      return;
+      return false;
     }
-    // Minimal-residual Jacobi: x += alpha z, z = D^{-1} r, alpha = (Az)^H r / |Az|^2
-    if (x_zero) launch_copy<T>(b, L.r, n, st);
-    else residual(l, b, x, L.r);
-    if (x_zero) launch_zero<T>(x, n, st);
-    x_zero = false;
-    launch_cmul_vec<T>(L.dinv, L.r, L.z, n, st);
+    // Minimal-residual Jacobi: z = D^{-1} r, w = A z, alpha = (w^H r)/(w^H w),
+    // x += alpha z, r -= alpha w (two launches per sweep).
+    const C<T>* rsrc;
+    if (x_zero) {
+      launch_cmul_vec<T>(L.dinv, b, L.z, n, st);
+      rsrc = b;
+    } else {
+      residual_dinv(l, b, x, L.r, L.z);
+      rsrc = L.r;
+    }
     for (int s = 0; s < sweeps; ++s) {
-      apply(l, L.z, L.t);
-      launch_dot2<T>(L.t, L.r, L.t, n, op.sc.partial, op.sc.d2, st);
-      launch_mr_alpha(op.sc.d2, op.sc.alpha, st);
-      launch_mr_update<T>(x, L.z, L.r, L.t, op.sc.alpha, L.dinv, s + 1 < sweeps ? L.z : nullptr, n, st);
+      mr_apply(l, L.z, rsrc, L.t);
+      launch_mr_update2<T>(x, L.z, rsrc, L.r, L.t, op.ks.alpha, L.dinv, s + 1 < sweeps ? L.z : nullptr, x_zero && s == 0,
+                           n, st);
+      rsrc = L.r;
     }
+    x_zero = false;
+    return true;
   }
 
-  // Arnoldi step j on level l: w (in/out, orthogonalised) against V_0..V_j; V_{j+1} = w / |w|.
+  // Arnoldi step j: w (holding A z_j) orthogonalised against V_0..V_j by CGS2,
+  // Hessenberg column and rotation updated; V_{j+1} = w / |w| if store_next.
   void arnoldi(ArnoldiState& ks, C<T>* Vb, int64_t ld, int j, C<T>* w, int64_t n, bool store_next) {
-    launch_dots<T>(Vb, ld, j + 1, w, n, op.sc.partial, op.sc.ha, st);
-    launch_axpy_multi<T>(w, Vb, ld, j + 1, op.sc.ha, -1.0, n, st);
-    launch_dots<T>(Vb, ld, j + 1, w, n, op.sc.partial, op.sc.hb, st);
-    launch_axpy_multi<T>(w, Vb, ld, j + 1, op.sc.hb, -1.0, n, st);
-    norm2(w, n, op.sc.nrm2);
-    launch_arnoldi_column(ks, j, op.sc.ha, op.sc.hb, op.sc.nrm2, st);
-    if (store_next) launch_scale_inv_norm<T>(w, Vb + (int64_t)(j + 1) * ld, op.sc.nrm2, n, st);
+    launch_cgs2<T>(Vb, ld, j + 1, w, n, op.ks, ks, j, st);
+    if (store_next) launch_scale_inv_norm<T>(w, Vb + (int64_t)(j + 1) * ld, op.ks.nrm2, n, st);
   }
 
   // Fixed-count GMRES from zero, right-preconditioned by D^{-1} (coarsest level).
@@ -308,17 +314,19 @@ template <typename T> struct Cycle {
     Level<T>& L = H.lv[l];
     const int64_t n = L.g.N;
     const int k = L.kdim;
-    norm2(b, n, op.sc.nrm2);
-    launch_cycle_start(L.ks, op.sc.nrm2, st);
-    launch_scale_inv_norm<T>(b, L.KV, op.sc.nrm2, n, st);
+    if (l > 0 && n <= kSmallCoarse) {
+      launch_coarse_gmres_cta<T>(L.g, L.A, L.dinv, b, x, L.KV, L.z, k, L.ks, st);
+      return;
+    }
+    launch_norm_start<T>(b, n, op.ks, &L.ks, st);
+    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st);
     for (int j = 0; j < k; ++j) {
       launch_cmul_vec<T>(L.dinv, L.KV + (int64_t)j * n, L.z, n, st);
       apply(l, L.z, L.t);
       arnoldi(L.ks, L.KV, n, j, L.t, n, j + 1 < k);
     }
     launch_backsolve(L.ks, k, st);
-    launch_zero<T>(L.t, n, st);
-    launch_axpy_multi<T>(L.t, L.KV, n, k, L.ks.y, 1.0, n, st);
+    launch_combine<T>(L.t, L.KV, n, k, L.ks, true, n, st);
     launch_cmul_vec<T>(L.dinv, L.t, x, n, st);
   }
 
@@ -327,9 +335,8 @@ template <typename T> struct Cycle {
     Level<T>& L = H.lv[l];
     const int64_t n = L.g.N;
     const int k = L.kdim;
-    norm2(b, n, op.sc.nrm2);
-    launch_cycle_start(L.ks, op.sc.nrm2, st);
-    launch_scale_inv_norm<T>(b, L.KV, op.sc.nrm2, n, st);
+    launch_norm_start<T>(b, n, op.ks, &L.ks, st);
+    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st);
     for (int j = 0; j < k; ++j) {
       C<T>* zj = L.KZ + (int64_t)j * n;
       cycle(l, L.KV + (int64_t)j * n, zj);
@@ -337,8 +344,7 @@ template <typename T> struct Cycle {
       arnoldi(L.ks, L.KV, n, j, L.t, n, j + 1 < k);
     }
     launch_backsolve(L.ks, k, st);
-    launch_zero<T>(x, n, st);
-    launch_axpy_multi<T>(x, L.KZ, n, k, L.ks.y, 1.0, n, st);
+    launch_combine<T>(x, L.KZ, n, k, L.ks, true, n, st);
   }
 
   // x = B_l^{-1} b, zero initial guess (Alg. TwoGrid / Alg. Kcycle).
@@ -348,10 +354,11 @@ template <typename T> struct Cycle {
     Level<T>& Lc = H.lv[l + 1];
     const int64_t n = L.g.N;
     bool x_zero = true;
-    relax(l, b, x, op.p.pre_sweeps[l], x_zero);
-    if (x_zero) launch_restrict<T>(L.g, Lc.g, b, Lc.b, st);
-    else {
-      residual(l, b, x, L.r);
+    const bool rvalid = relax(l, b, x, op.p.pre_sweeps[l], x_zero);
+    if (x_zero) {
+      launch_restrict<T>(L.g, Lc.g, b, Lc.b, st);
+    } else {
+      if (!rvalid) residual(l, b, x, L.r);
       launch_restrict<T>(L.g, Lc.g, L.r, Lc.b, st);
     }
     if (op.p.cycle == ADR_CYCLE_K && l + 1 < H.L - 1) kcycle(l + 1, Lc.b, Lc.x);
@@ -378,6 +385,11 @@ template <typename T> static int build_hierarchy(Op& op, Hier<T>& H) {
 // current source / frequency, written into the operator's arena (no sync).
 static int setup(Op& op, const double* kappa, const double* tau1, const double* gamma) {
   const int64_t N = op.g0.N;
+  FineDyn dyn{};
+  dyn.omega = op.omega;
+  for (int d = 0; d < 3; ++d) dyn.src[d] = op.src[d];
+  dyn.src_index = op.src_index;
+  launch_set_dyn(op.dyn, dyn, op.st);
   FineInputs in{};
   in.kappa = kappa; in.tau1 = tau1; in.gamma = gamma;
   for (int d = 0; d < 3; ++d) { in.src[d] = op.src[d]; in.h[d] = op.h[d]; }
@@ -393,18 +405,53 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
   return op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32);
 }
 
+// Runs the cycle of level 0 from H.lv[0].b into H.lv[0].x: captured into a
+// CUDA graph on first use (every pointer and parameter it touches is fixed
+// for the operator's lifetime, per-source values live in device memory) and
+// replayed on the operator's stream.
+template <typename T> static int run_cycle(Op& op, Hier<T>& H) {
+  Level<T>& L0 = H.lv[0];
+  if (!op.use_graph) {
+    Cycle<T> c{op, H, op.st};
+    c.cycle(0, L0.b, L0.x);
+    return check_launch("cycle");
+  }
+  if (!op.cycle_exec) {
+    const long long before = g_launches.load(std::memory_order_relaxed);
+    ADR_CUDA(cudaStreamBeginCapture(op.cap, cudaStreamCaptureModeThreadLocal));
+    Cycle<T> c{op, H, op.cap};
+    c.cycle(0, L0.b, L0.x);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(op.cap, &graph);
+    if (e != cudaSuccess) return fail(ADR_ERR_CUDA, std::string("cycle capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&op.cycle_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      op.cycle_exec = nullptr;
+      return fail(ADR_ERR_CUDA, std::string("cycle graph instantiation: ") + cudaGetErrorString(e));
+    }
+    op.cycle_kernels = g_launches.load(std::memory_order_relaxed) - before;
+    count_launches((int)-op.cycle_kernels);  // capture launched nothing; replays are counted below
+  }
+  ADR_CUDA(cudaGraphLaunch(op.cycle_exec, op.st));
+  count_launches((int)op.cycle_kernels);
+  return ADR_OK;
+}
+
 // One preconditioner application on float64 vectors (casting for a float32 cycle).
-static void precondition(Op& op, const double2* v, double2* z) {
+static int precondition(Op& op, const double2* v, double2* z) {
   if (op.p.precond_precision == ADR_F64) {
-    Cycle<double> c{op, op.h64, op.st};
-    c.cycle(0, v, z);
+    Level<double>& L0 = op.h64.lv[0];
+    launch_copy<double>(v, L0.b, op.g0.N, op.st);
+    ADR_TRY(run_cycle(op, op.h64));
+    launch_copy<double>(L0.x, z, op.g0.N, op.st);
   } else {
-    Cycle<float> c{op, op.h32, op.st};
     Level<float>& L0 = op.h32.lv[0];
     launch_ccast<double, float>(v, L0.b, op.g0.N, op.st);
-    c.cycle(0, L0.b, L0.x);
+    ADR_TRY(run_cycle(op, op.h32));
     launch_ccast<float, double>(L0.x, z, op.g0.N, op.st);
   }
+  return ADR_OK;
 }
 
 static int read_scalars(Op& op, const double* dev, int count) {
@@ -515,10 +562,20 @@ int adr_operator_create(int dim, const int* n, const double* h, const int* src, 
   Arena real;
   real.base = (char*)op.arena;
   plan(op, real);
+  e = cudaStreamCreateWithFlags(&op.cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(op.ks.ticket, 0, sizeof(unsigned), op.st);
+  if (e != cudaSuccess) {
+    if (op.cap) cudaStreamDestroy(op.cap);
+    cudaFree(op.arena);
+    cudaFreeHost(op.host_scal);
+    delete h_;
+    return fail(ADR_ERR_CUDA, std::string("operator streams: ") + cudaGetErrorString(e));
+  }
 
   int rc = setup(op, kappa, tau1, gamma);
   if (rc != ADR_OK) {
     cudaStreamSynchronize(op.st);
+    cudaStreamDestroy(op.cap);
     cudaFree(op.arena);
     cudaFreeHost(op.host_scal);
     delete h_;
@@ -547,6 +604,8 @@ int adr_operator_destroy(adr_op_t h) {
   if (!h) return ADR_OK;
   Op& op = h->op;
   cudaStreamSynchronize(op.st);
+  if (op.cycle_exec) cudaGraphExecDestroy(op.cycle_exec);
+  if (op.cap) cudaStreamDestroy(op.cap);
   cudaError_t e1 = cudaFree(op.arena);
   cudaError_t e2 = cudaFreeHost(op.host_scal);
   delete h;
@@ -618,12 +677,15 @@ int adr_vcycle(adr_op_t h, const void* r, void* z) {
   if (!h || !r || !z) return fail(ADR_ERR_ARG, "null argument");
   if (r == z) return fail(ADR_ERR_ARG, "z may not alias r");
   Op& op = h->op;
+  const int64_t N = op.g0.N;
   if (op.p.precond_precision == ADR_F64) {
-    Cycle<double> c{op, op.h64, op.st};
-    c.cycle(0, (const double2*)r, (double2*)z);
+    launch_copy<double>((const double2*)r, op.h64.lv[0].b, N, op.st);
+    ADR_TRY(run_cycle(op, op.h64));
+    launch_copy<double>(op.h64.lv[0].x, (double2*)z, N, op.st);
   } else {
-    Cycle<float> c{op, op.h32, op.st};
-    c.cycle(0, (const float2*)r, (float2*)z);
+    launch_copy<float>((const float2*)r, op.h32.lv[0].b, N, op.st);
+    ADR_TRY(run_cycle(op, op.h32));
+    launch_copy<float>(op.h32.lv[0].x, (float2*)z, N, op.st);
   }
   return check_launch("adr_vcycle");
 }
@@ -658,10 +720,9 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
     b = op.b;
   }
   const FineOp<double> A = make_fine<double>(op, ADR_SCHEME_2UP, false);
-  auto norm2 = [&](const double2* v) { launch_dots<double>(v, 0, 1, v, N, op.sc.partial, op.sc.nrm2, st); };
 
-  norm2(b);
-  ADR_TRY(read_scalars(op, (const double*)op.sc.nrm2, 1));
+  launch_norm_start<double>(b, N, op.ks, nullptr, st);
+  ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
   const double bnorm = sqrt(op.host_scal[0]);
   adr_solve_info_t res{};
   if (bnorm == 0.0) {
@@ -675,30 +736,24 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
     launch_zero<double>(a, N, st);
     launch_copy<double>(b, op.r, N, st);
   }
-  norm2(op.r);
-  ADR_TRY(read_scalars(op, (const double*)op.sc.nrm2, 1));
+  launch_norm_start<double>(op.r, N, op.ks, &op.ost, st);
+  ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
   double beta = sqrt(op.host_scal[0]);
   int its = 0, cycles = 0;
   double est = beta / bnorm;
   int status = ADR_OK;
   while (beta > tol * bnorm && its < maxit) {
-    // op.sc.nrm2 holds |r|^2 here
-    launch_cycle_start(op.ost, op.sc.nrm2, st);
-    launch_scale_inv_norm<double>(op.r, op.V, op.sc.nrm2, N, st);
+    // op.ks.nrm2 holds |r|^2 and op.ost a fresh cycle here
+    launch_scale_inv_norm<double>(op.r, op.V, op.ks.nrm2, N, st);
     int k = 0;
     for (int j = 0; j < m; ++j) {
       double2* vj = op.V + (int64_t)j * N;
       double2* zj = op.Z + (int64_t)j * N;
       double2* w = op.V + (int64_t)(j + 1) * N;  // A z_j, orthogonalised and normalised in place
-      precondition(op, vj, zj);
+      ADR_TRY(precondition(op, vj, zj));
       launch_fine_apply<double>(op.g0, A, zj, w, st);
-      launch_dots<double>(op.V, N, j + 1, w, N, op.sc.partial, op.sc.ha, st);
-      launch_axpy_multi<double>(w, op.V, N, j + 1, op.sc.ha, -1.0, N, st);
-      launch_dots<double>(op.V, N, j + 1, w, N, op.sc.partial, op.sc.hb, st);
-      launch_axpy_multi<double>(w, op.V, N, j + 1, op.sc.hb, -1.0, N, st);
-      norm2(w);
-      launch_arnoldi_column(op.ost, j, op.sc.ha, op.sc.hb, op.sc.nrm2, st);
-      launch_scale_inv_norm<double>(w, w, op.sc.nrm2, N, st);
+      launch_cgs2<double>(op.V, N, j + 1, w, N, op.ks, op.ost, j, st);
+      launch_scale_inv_norm<double>(w, w, op.ks.nrm2, N, st);
       ADR_TRY(check_launch("adr_solve iteration"));
       ADR_TRY(read_scalars(op, op.ost.scal, kNumScal));
       ++its;
@@ -711,10 +766,10 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
     }
     if (status == ADR_ERR_NAN) break;
     launch_backsolve(op.ost, k, st);
-    launch_axpy_multi<double>(a, op.Z, N, k, op.ost.y, 1.0, N, st);
+    launch_combine<double>(a, op.Z, N, k, op.ost, false, N, st);
     launch_fine_residual<double>(op.g0, A, b, a, op.r, st);
-    norm2(op.r);
-    ADR_TRY(read_scalars(op, (const double*)op.sc.nrm2, 1));
+    launch_norm_start<double>(op.r, N, op.ks, &op.ost, st);
+    ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
     beta = sqrt(op.host_scal[0]);
     ++cycles;
     if (!std::isfinite(beta)) { status = ADR_ERR_NAN; break; }

@@ -2,6 +2,8 @@
 // (Eq. coarseGridMatrix, A_c = P^T A P), bilinear / trilinear transfers
 // (P and its transpose, Sec. 3.1), relaxation and residuals on those levels.
 #include "adr_common.cuh"
+#include "krylov_dev.cuh"
+#include "reduce.cuh"
 
 namespace adr {
 
@@ -195,5 +197,181 @@ template <typename T> void launch_prolong_add(const Dims& gf, const Dims& gc, co
   template void launch_prolong_add<T>(const Dims&, const Dims&, const C<T>*, C<T>*, cudaStream_t);
 ADR_INSTANTIATE_COARSE(double)
 ADR_INSTANTIATE_COARSE(float)
+
+}  // namespace adr
+
+// ===========================================================================
+// Fused relaxation kernels on stored-stencil levels and the one-block
+// coarsest-grid GMRES
+// ===========================================================================
+namespace adr {
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_stencil_mr_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ z,
+                                                          const C<T>* __restrict__ r, C<T>* __restrict__ w,
+                                                          double2* partial, unsigned* ticket, double2* alpha) {
+  __shared__ double2 sh[32 * 2];
+  C<T> s[2] = {czero<T>(), czero<T>()};
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < g.N; j += (int64_t)gridDim.x * blockDim.x) {
+    int i0, i1, i2;
+    unravel(g, j, i0, i1, i2);
+    const C<T> wj = stencil_dot<DIM, T>(g, A, z, j, i0, i1, i2);
+    w[j] = wj;
+    s[0] = cfma_conj(wj, r[j], s[0]);
+    s[1] = cfma_conj(wj, wj, s[1]);
+  }
+  double2 mine[2], tot[2];
+  block_sum_t<T, 2>(s, sh, mine);
+  if (last_block_total<2>(mine, partial, ticket, tot, sh) && threadIdx.x == 0) {
+    const double den = tot[1].x;
+    *alpha = den > 0.0 ? make_double2(tot[0].x / den, tot[0].y / den) : make_double2(0.0, 0.0);
+  }
+}
+
+template <int DIM, typename T>
+__global__ void k_stencil_residual_dinv(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ b,
+                                        const C<T>* __restrict__ x, const C<T>* __restrict__ dinv, C<T>* __restrict__ r,
+                                        C<T>* __restrict__ z) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int i0, i1, i2;
+  unravel(g, j, i0, i1, i2);
+  const C<T> rj = csub(b[j], stencil_dot<DIM, T>(g, A, x, j, i0, i1, i2));
+  r[j] = rj;
+  z[j] = cmul(dinv[j], rj);
+}
+
+// Sums conj(V_i) w over the block for i < k into hh[i] (all threads see it after return).
+template <typename T>
+__device__ __forceinline__ void cta_dots(const C<T>* V, int64_t n, int k, const C<T>* w, double2* hh, double2* sh) {
+  for (int c = 0; c < k; c += 4) {
+    C<T> acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = czero<T>();
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const C<T> we = w[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * n + e], we, acc[q]);
+    }
+    double2 o[4];
+    block_sum_t<T, 4>(acc, sh, o);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 4 && c + q < k; ++q) hh[c + q] = o[q];
+    __syncthreads();
+  }
+}
+
+// The whole fixed-count Jacobi-preconditioned GMRES of a small coarsest grid
+// in one block: x = D^{-1} V y with V the Arnoldi basis of A D^{-1} and b.
+// V holds (k+1) * n entries of scratch, z n entries.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ dinv,
+                                                           const C<T>* b, C<T>* x, C<T>* V, C<T>* z, int k, ArnoldiState st) {
+  __shared__ double2 sh[32 * 4];
+  __shared__ double2 ha[kMaxKrylov + 1];
+  __shared__ double2 hb[kMaxKrylov + 1];
+  __shared__ double s_scale;
+  const int64_t n = g.N;
+  // beta = |b|, V_0 = b / beta
+  {
+    C<T> s[1] = {czero<T>()};
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s[0] = cfma_conj(b[e], b[e], s[0]);
+    double2 o[1];
+    block_sum_t<T, 1>(s, sh, o);
+    if (threadIdx.x == 0) {
+      const double beta = sqrt(o[0].x);
+      for (int i = 0; i <= st.m; ++i) st.g[i] = make_double2(0.0, 0.0);
+      st.g[0] = make_double2(beta, 0.0);
+      st.scal[kScalBeta] = beta;
+      st.scal[kScalEst] = beta;
+      st.iscal[kIScalStop] = beta > 0.0 ? -1 : 0;
+      s_scale = beta > 0.0 ? 1.0 / beta : 0.0;
+    }
+    __syncthreads();
+    const T inv = (T)s_scale;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) V[e] = cscale(b[e], inv);
+    __syncthreads();
+  }
+  for (int j = 0; j < k; ++j) {
+    const C<T>* vj = V + (int64_t)j * n;
+    C<T>* w = V + (int64_t)(j + 1) * n;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) z[e] = cmul(dinv[e], vj[e]);
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      int i0, i1, i2;
+      unravel(g, e, i0, i1, i2);
+      w[e] = stencil_dot<DIM, T>(g, A, z, e, i0, i1, i2);
+    }
+    __syncthreads();
+    cta_dots<T>(V, n, j + 1, w, ha, sh);
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      C<T> acc = w[e];
+      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], mk<T>((T)(-ha[i].x), (T)(-ha[i].y)), acc);
+      w[e] = acc;
+    }
+    __syncthreads();
+    cta_dots<T>(V, n, j + 1, w, hb, sh);
+    C<T> s[1] = {czero<T>()};
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      C<T> acc = w[e];
+      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], mk<T>((T)(-hb[i].x), (T)(-hb[i].y)), acc);
+      w[e] = acc;
+      s[0] = cfma_conj(acc, acc, s[0]);
+    }
+    double2 o[1];
+    block_sum_t<T, 1>(s, sh, o);
+    if (threadIdx.x == 0) {
+      arnoldi_column_dev(st, j, ha, hb, o[0].x);
+      const double hn = st.scal[kScalHn];
+      s_scale = hn > 0.0 ? 1.0 / hn : 0.0;
+    }
+    __syncthreads();
+    if (j + 1 < k) {
+      const T inv = (T)s_scale;
+      for (int64_t e = threadIdx.x; e < n; e += blockDim.x) w[e] = cscale(w[e], inv);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) backsolve_dev(st, k);
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    C<T> acc = czero<T>();
+    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * n + e], mk<T>((T)st.y[i].x, (T)st.y[i].y), acc);
+    x[e] = cmul(dinv[e], acc);
+  }
+}
+
+static inline unsigned mr_blocks_c(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (unsigned)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+}
+
+template <typename T>
+void launch_stencil_mr_apply(const Dims& g, const C<T>* A, const C<T>* z, const C<T>* r, C<T>* w, double2* partial,
+                             unsigned* ticket, double2* alpha, cudaStream_t st) {
+  const unsigned nb = mr_blocks_c(g.N);
+  if (g.dim == 2) count_launches(1), k_stencil_mr_apply<2, T><<<nb, 256, 0, st>>>(g, A, z, r, w, partial, ticket, alpha);
+  else count_launches(1), k_stencil_mr_apply<3, T><<<nb, 256, 0, st>>>(g, A, z, r, w, partial, ticket, alpha);
+}
+template <typename T>
+void launch_stencil_residual_dinv(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x, const C<T>* dinv, C<T>* r,
+                                  C<T>* z, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_stencil_residual_dinv<2, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, A, b, x, dinv, r, z);
+  else count_launches(1), k_stencil_residual_dinv<3, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, A, b, x, dinv, r, z);
+}
+template <typename T>
+void launch_coarse_gmres_cta(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, C<T>* x, C<T>* V, C<T>* z, int k,
+                             const ArnoldiState& s, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_coarse_gmres_cta<2, T><<<1, 1024, 0, st>>>(g, A, dinv, b, x, V, z, k, s);
+  else count_launches(1), k_coarse_gmres_cta<3, T><<<1, 1024, 0, st>>>(g, A, dinv, b, x, V, z, k, s);
+}
+
+#define ADR_INSTANTIATE_COARSE2(T)                                                                                          \
+  template void launch_stencil_mr_apply<T>(const Dims&, const C<T>*, const C<T>*, const C<T>*, C<T>*, double2*, unsigned*, double2*, cudaStream_t); \
+  template void launch_stencil_residual_dinv<T>(const Dims&, const C<T>*, const C<T>*, const C<T>*, const C<T>*, C<T>*, C<T>*, cudaStream_t); \
+  template void launch_coarse_gmres_cta<T>(const Dims&, const C<T>*, const C<T>*, const C<T>*, C<T>*, C<T>*, C<T>*, int, const ArnoldiState&, cudaStream_t);
+ADR_INSTANTIATE_COARSE2(double)
+ADR_INSTANTIATE_COARSE2(float)
 
 }  // namespace adr

@@ -9,6 +9,7 @@
 // (Sec. 2.2), the Neumann condition of Eq. BCADR (n.grad a = i w (n.grad tau) a)
 // by ghost elimination, and the row of M^{-1} H M at the source (Eq. helmADR2).
 #include "adr_common.cuh"
+#include "reduce.cuh"
 
 namespace adr {
 
@@ -118,7 +119,7 @@ void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
 // Writes the row of node j (coordinates ii) in cross form into c[1 + 4*DIM].
 template <int DIM, typename T>
 __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int64_t j, const int ii[3], C<T>* c) {
-  if (j == f.src_index) {
+  if (j == f.dyn->src_index) {
     c[0] = f.src_row[0];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -129,8 +130,9 @@ __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int6
   }
   bool near = true;
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) near = near && (abs(ii[d] - f.src[d]) <= f.near);
+  for (int d = 0; d < DIM; ++d) near = near && (abs(ii[d] - f.dyn->src[d]) <= f.near);
   const C<T> rho = f.rho[j];
+  const T omega = (T)f.dyn->omega;
   T cre = rho.x, cim = rho.y;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
@@ -140,7 +142,7 @@ __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int6
     const T ih2 = f.ih2[d];
     const int k = ii[d], n = g.n[d];
     T re_m1 = ih2, re_p1 = ih2;
-    T im_m1 = T(-0.5) * f.omega * td, im_p1 = im_m1;
+    T im_m1 = T(-0.5) * omega * td, im_p1 = im_m1;
     cre -= T(2) * ih2;
     // advection difference weights at offsets -2..+2
     T wm2 = 0, wm1 = 0, w0 = 0, wp1 = 0, wp2 = 0;
@@ -170,20 +172,20 @@ __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int6
         }
       }
     }
-    const T adv = T(-2) * f.omega * gd;  // -2 i w (d_d tau) D_d: imaginary factor
+    const T adv = T(-2) * omega * gd;  // -2 i w (d_d tau) D_d: imaginary factor
     im_m1 += adv * wm1;
     im_p1 += adv * wp1;
     cim += adv * w0;
     const T im_m2 = adv * wm2, im_p2 = adv * wp2;
     // Neumann ghost (Eq. BCADR read with the factor a): a_{b+s} = a_{b-s} + s 2 h i w g a_b
     if (k == 0) {
-      const T fac = T(-2) * h * f.omega * gd;  // ghost adds (i fac) a_b per unit coefficient
+      const T fac = T(-2) * h * omega * gd;  // ghost adds (i fac) a_b per unit coefficient
       re_p1 += re_m1; im_p1 += im_m1;
       cre -= im_m1 * fac; cim += re_m1 * fac;
       re_m1 = 0; im_m1 = 0;
     }
     if (k == n - 1) {
-      const T fac = T(2) * h * f.omega * gd;
+      const T fac = T(2) * h * omega * gd;
       re_m1 += re_p1; im_m1 += im_p1;
       cre -= im_p1 * fac; cim += re_p1 * fac;
       re_p1 = 0; im_p1 = 0;
@@ -416,5 +418,85 @@ void launch_pack_coefficients(const Dims& g, const double* const gd[3], const do
                               const double* tau, double* out, cudaStream_t st) {
   count_launches(1), k_pack<<<blocks_for(g.N, 256), 256, 0, st>>>(g, gd[0], gd[1], gd[2], td[0], td[1], td[2], rho, tau, out);
 }
+
+}  // namespace adr
+
+// ===========================================================================
+// Fused relaxation kernels on the fine level
+// ===========================================================================
+namespace adr {
+
+// w = A z and, over all nodes, alpha = (w^H r) / (w^H w) (the one-step
+// minimal-residual weight), computed by the last block to finish.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_fine_mr_apply(Dims g, FineOp<T> f, const C<T>* __restrict__ z,
+                                                       const C<T>* __restrict__ r, C<T>* __restrict__ w,
+                                                       double2* partial, unsigned* ticket, double2* alpha) {
+  __shared__ double2 sh[32 * 2];
+  C<T> s[2] = {czero<T>(), czero<T>()};
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < g.N; j += (int64_t)gridDim.x * blockDim.x) {
+    int ii[3];
+    unravel(g, j, ii[0], ii[1], ii[2]);
+    C<T> c[1 + 4 * DIM];
+    fine_row<DIM, T>(g, f, j, ii, c);
+    const C<T> wj = cross_dot<DIM, T>(g, c, ii, j, z);
+    w[j] = wj;
+    s[0] = cfma_conj(wj, r[j], s[0]);
+    s[1] = cfma_conj(wj, wj, s[1]);
+  }
+  double2 mine[2], tot[2];
+  block_sum_t<T, 2>(s, sh, mine);
+  if (last_block_total<2>(mine, partial, ticket, tot, sh) && threadIdx.x == 0) {
+    const double den = tot[1].x;
+    *alpha = den > 0.0 ? make_double2(tot[0].x / den, tot[0].y / den) : make_double2(0.0, 0.0);
+  }
+}
+
+// r = b - A x ; z = D^{-1} r
+template <int DIM, typename T>
+__global__ void k_fine_residual_dinv(Dims g, FineOp<T> f, const C<T>* __restrict__ b, const C<T>* __restrict__ x,
+                                     const C<T>* __restrict__ dinv, C<T>* __restrict__ r, C<T>* __restrict__ z) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  C<T> c[1 + 4 * DIM];
+  fine_row<DIM, T>(g, f, j, ii, c);
+  const C<T> rj = csub(b[j], cross_dot<DIM, T>(g, c, ii, j, x));
+  r[j] = rj;
+  z[j] = cmul(dinv[j], rj);
+}
+
+__global__ void k_set_dyn(FineDyn* d, FineDyn v) {
+  if (threadIdx.x == 0) *d = v;
+}
+void launch_set_dyn(FineDyn* d, const FineDyn& v, cudaStream_t st) { count_launches(1), k_set_dyn<<<1, 32, 0, st>>>(d, v); }
+
+static inline unsigned mr_blocks(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (unsigned)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+}
+
+template <typename T>
+void launch_fine_mr_apply(const Dims& g, const FineOp<T>& f, const C<T>* z, const C<T>* r, C<T>* w, double2* partial,
+                          unsigned* ticket, double2* alpha, cudaStream_t st) {
+  const unsigned nb = mr_blocks(g.N);
+  if (g.dim == 2) count_launches(1), k_fine_mr_apply<2, T><<<nb, 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
+  else count_launches(1), k_fine_mr_apply<3, T><<<nb, 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
+}
+template <typename T>
+void launch_fine_residual_dinv(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* x, const C<T>* dinv, C<T>* r,
+                               C<T>* z, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_fine_residual_dinv<2, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, b, x, dinv, r, z);
+  else count_launches(1), k_fine_residual_dinv<3, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, b, x, dinv, r, z);
+}
+template void launch_fine_mr_apply<double>(const Dims&, const FineOp<double>&, const double2*, const double2*, double2*,
+                                           double2*, unsigned*, double2*, cudaStream_t);
+template void launch_fine_mr_apply<float>(const Dims&, const FineOp<float>&, const float2*, const float2*, float2*,
+                                          double2*, unsigned*, double2*, cudaStream_t);
+template void launch_fine_residual_dinv<double>(const Dims&, const FineOp<double>&, const double2*, const double2*,
+                                                const double2*, double2*, double2*, cudaStream_t);
+template void launch_fine_residual_dinv<float>(const Dims&, const FineOp<float>&, const float2*, const float2*,
+                                               const float2*, float2*, float2*, cudaStream_t);
 
 }  // namespace adr

@@ -7,6 +7,8 @@
 // (Alg. Kcycle), the fixed-count Jacobi-preconditioned GMRES of the coarsest
 // grid and the minimal-residual Jacobi relaxation (Sec. 3.1).
 #include "krylov.cuh"
+#include "reduce.cuh"
+#include "krylov_dev.cuh"
 
 namespace adr {
 
@@ -160,19 +162,6 @@ template <typename T> void launch_cmul_vec(const C<T>* a, const C<T>* b, C<T>* o
 // ---------------------------------------------------------------------------
 // Small device-side Arnoldi state (one thread)
 // ---------------------------------------------------------------------------
-// Complex Givens rotation with real cosine: [c s; -conj(s) c] [a; b] = [r; 0].
-__device__ void givens(double2 a, double2 b, double& c, double2& s, double2& r) {
-  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
-  if (bb == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); r = a; return; }
-  if (aa == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); r = b; return; }
-  const double nu = sqrt(aa * aa + bb * bb);
-  c = aa / nu;
-  const double2 ph = make_double2(a.x / aa, a.y / aa);
-  const double2 cb = make_double2(b.x / nu, -b.y / nu);
-  s = cmul(ph, cb);
-  r = make_double2(ph.x * nu, ph.y * nu);
-}
-
 __global__ void k_cycle_start(ArnoldiState st, const double2* nrm2) {
   if (threadIdx.x != 0) return;
   const double beta = sqrt(nrm2->x);
@@ -187,52 +176,13 @@ __global__ void k_cycle_start(ArnoldiState st, const double2* nrm2) {
 // squared norm of the orthogonalised vector; rotations and g updated.
 __global__ void k_arnoldi_column(ArnoldiState st, int j, const double2* ha, const double2* hb, const double2* nrm2) {
   if (threadIdx.x != 0) return;
-  const int m1 = st.m + 1;
-  double2* H = st.H + (int64_t)j * m1;
-  if (st.iscal[kIScalStop] >= 0) {  // already broken down: leave the column empty
-    for (int i = 0; i <= j + 1; ++i) H[i] = make_double2(0.0, 0.0);
-    st.scal[kScalHn] = 0.0;
-    return;
-  }
-  for (int i = 0; i <= j; ++i) H[i] = make_double2(ha[i].x + (hb ? hb[i].x : 0.0), ha[i].y + (hb ? hb[i].y : 0.0));
-  const double hn = sqrt(nrm2->x);
-  H[j + 1] = make_double2(hn, 0.0);
-  for (int i = 0; i < j; ++i) {
-    const double2 a = H[i], b = H[i + 1];
-    const double c = st.cs[i];
-    const double2 s = st.sn[i];
-    const double2 cs_ = make_double2(s.x, -s.y);  // conj(s)
-    H[i] = cadd(make_double2(c * a.x, c * a.y), cmul(s, b));
-    H[i + 1] = csub(make_double2(c * b.x, c * b.y), cmul(cs_, a));
-  }
-  double c;
-  double2 s, r;
-  givens(H[j], H[j + 1], c, s, r);
-  st.cs[j] = c;
-  st.sn[j] = s;
-  H[j] = r;
-  H[j + 1] = make_double2(0.0, 0.0);
-  const double2 gj = st.g[j];
-  st.g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
-  st.g[j] = make_double2(c * gj.x, c * gj.y);
-  st.scal[kScalEst] = hypot(st.g[j + 1].x, st.g[j + 1].y);
-  st.scal[kScalHn] = hn;
-  if (hn == 0.0) st.iscal[kIScalStop] = j + 1;
+  arnoldi_column_dev(st, j, ha, hb, nrm2->x);
 }
 
 // y = R^{-1} g for the leading k x k block (k = breakdown index if any).
 __global__ void k_backsolve(ArnoldiState st, int k) {
   if (threadIdx.x != 0) return;
-  const int m1 = st.m + 1;
-  const int stop = st.iscal[kIScalStop];
-  if (stop >= 0 && stop < k) k = stop;
-  for (int i = 0; i < st.m; ++i) st.y[i] = make_double2(0.0, 0.0);
-  for (int i = k - 1; i >= 0; --i) {
-    double2 acc = st.g[i];
-    for (int q = i + 1; q < k; ++q) acc = csub(acc, cmul(st.H[(int64_t)q * m1 + i], st.y[q]));
-    const double2 rii = st.H[(int64_t)i * m1 + i];
-    st.y[i] = cmul(acc, cinv(rii));
-  }
+  backsolve_dev(st, k);
 }
 
 // alpha = (w^H r) / (w^H w) from d[0] = w^H r, d[1] = w^H w (0 if w = 0).
@@ -313,5 +263,202 @@ ADR_INSTANTIATE_KRYLOV(double)
 ADR_INSTANTIATE_KRYLOV(float)
 template void launch_ccast<double, float>(const C<double>*, C<float>*, int64_t, cudaStream_t);
 template void launch_ccast<float, double>(const C<float>*, C<double>*, int64_t, cudaStream_t);
+
+// ===========================================================================
+// Fused Arnoldi / Krylov kernels (one launch per pass, deterministic
+// last-block reductions; see reduce.cuh)
+// ===========================================================================
+
+// Block sums of k values held per thread in chunks; the block's k totals are
+// left in blk[0..k) (shared memory).  acc_fn(i) returns thread's value i.
+// Then the last block reduces partials over blocks into out[0..k).
+__device__ __forceinline__ bool last_block_rt(int k, const double2* blk, double2* partial, unsigned* ticket, double2* out,
+                                              double2* sh) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < k; ++i) partial[(size_t)blockIdx.x * k + i] = blk[i];
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  for (int i = 0; i < k; ++i) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+      const double2 p = __ldcg(&partial[(size_t)b * k + i]);
+      acc.x += p.x;
+      acc.y += p.y;
+    }
+    double2 v[1] = {acc}, o[1];
+    block_sum_k<1>(v, sh, o);
+    if (threadIdx.x == 0) out[i] = o[0];
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  __syncthreads();
+  return true;
+}
+
+// Per-thread sums of conj(V_i[e]) * w[e] for i < k over a grid-stride range,
+// reduced over the block into blk[i].
+template <typename T>
+__device__ __forceinline__ void block_dots(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w, int64_t n,
+                                           double2* blk, double2* sh) {
+  for (int c = 0; c < k; c += 4) {
+    C<T> acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = czero<T>();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+      const C<T> we = w[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * ld + e], we, acc[q]);
+    }
+    double2 o[4];
+    block_sum_t<T, 4>(acc, sh, o);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 4 && c + q < k; ++q) blk[c + q] = o[q];
+    __syncthreads();
+  }
+}
+
+// pass 1: ha = V^H w
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgs_pass1(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w, int64_t n,
+                                                   double2* partial, unsigned* ticket, double2* ha) {
+  __shared__ double2 sh[32 * 4];
+  __shared__ double2 blk[kMaxKrylov + 1];
+  block_dots<T>(V, ld, k, w, n, blk, sh);
+  last_block_rt(k, blk, partial, ticket, ha, sh);
+}
+
+// pass 2: w -= V ha ; hb = V^H w
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgs_pass2(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+                                                   const double2* __restrict__ ha, double2* partial, unsigned* ticket,
+                                                   double2* hb) {
+  __shared__ double2 sh[32 * 4];
+  __shared__ double2 blk[kMaxKrylov + 1];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    C<T> acc = w[e];
+    for (int i = 0; i < k; ++i) {
+      const double2 cd = ha[i];
+      acc = cfma(V[(int64_t)i * ld + e], mk<T>((T)(-cd.x), (T)(-cd.y)), acc);
+    }
+    w[e] = acc;
+  }
+  block_dots<T>(V, ld, k, w, n, blk, sh);   // each thread re-reads only its own elements of w
+  last_block_rt(k, blk, partial, ticket, hb, sh);
+}
+
+// pass 3: w -= V hb ; |w|^2 ; Arnoldi column j and Givens rotation (last block)
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+                                                   const double2* __restrict__ ha, const double2* __restrict__ hb,
+                                                   double2* partial, unsigned* ticket, double2* nrm2, ArnoldiState st, int j) {
+  __shared__ double2 sh[32 * 4];
+  __shared__ double2 blk[1];
+  C<T> s2 = czero<T>();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    C<T> acc = w[e];
+    for (int i = 0; i < k; ++i) {
+      const double2 cd = hb[i];
+      acc = cfma(V[(int64_t)i * ld + e], mk<T>((T)(-cd.x), (T)(-cd.y)), acc);
+    }
+    w[e] = acc;
+    s2 = cfma_conj(acc, acc, s2);
+  }
+  double2 v[1] = {make_double2((double)s2.x, 0.0)}, o[1];
+  block_sum_k<1>(v, sh, o);
+  if (threadIdx.x == 0) blk[0] = o[0];
+  __syncthreads();
+  if (last_block_rt(1, blk, partial, ticket, nrm2, sh) && threadIdx.x == 0) {
+    if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, nrm2->x);
+  }
+}
+
+// |b|^2 and (optionally) the start of an Arnoldi cycle with beta = |b|.
+template <typename T>
+__global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, double2* partial, unsigned* ticket,
+                                                    double2* nrm2, ArnoldiState st, int start) {
+  __shared__ double2 sh[32 * 4];
+  __shared__ double2 blk[1];
+  C<T> s2 = czero<T>();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s2 = cfma_conj(b[e], b[e], s2);
+  double2 v[1] = {make_double2((double)s2.x, 0.0)}, o[1];
+  block_sum_k<1>(v, sh, o);
+  if (threadIdx.x == 0) blk[0] = o[0];
+  __syncthreads();
+  if (last_block_rt(1, blk, partial, ticket, nrm2, sh) && threadIdx.x == 0 && start) {
+    const double beta = sqrt(nrm2->x);
+    for (int i = 0; i <= st.m; ++i) st.g[i] = make_double2(0.0, 0.0);
+    st.g[0] = make_double2(beta, 0.0);
+    st.scal[kScalBeta] = beta;
+    st.scal[kScalEst] = beta;
+    st.iscal[kIScalStop] = beta > 0.0 ? -1 : 0;
+  }
+}
+
+// x = (assign ? 0 : x) + sum_i Z_i y_i  (y from the state, i < k)
+template <typename T>
+__global__ void k_combine(C<T>* x, const C<T>* __restrict__ Z, int64_t ld, int k, ArnoldiState st, int assign, int64_t n) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  C<T> acc = assign ? czero<T>() : x[e];
+  for (int i = 0; i < k; ++i) {
+    const double2 yi = st.y[i];
+    acc = cfma(Z[(int64_t)i * ld + e], mk<T>((T)yi.x, (T)yi.y), acc);
+  }
+  x[e] = acc;
+}
+
+// x = (x_zero ? 0 : x) + alpha z ; r_dst = r_src - alpha w ; znext = dinv .* r_dst
+template <typename T>
+__global__ void k_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst,
+                             const C<T>* __restrict__ w, const double2* __restrict__ alpha, const C<T>* __restrict__ dinv,
+                             C<T>* znext, int x_zero, int64_t n) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const C<T> al = mk<T>((T)alpha->x, (T)alpha->y);
+  x[e] = cfma(al, z[e], x_zero ? czero<T>() : x[e]);
+  const C<T> rn = csub(r_src[e], cmul(al, w[e]));
+  r_dst[e] = rn;
+  if (znext) znext[e] = cmul(dinv[e], rn);
+}
+
+template <typename T>
+void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s, const ArnoldiState& st, int j,
+                 cudaStream_t stream) {
+  const int nb = reduction_blocks(n);
+  count_launches(1), k_cgs_pass1<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.partial, s.ticket, s.ha);
+  count_launches(1), k_cgs_pass2<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.partial, s.ticket, s.hb);
+  count_launches(1), k_cgs_pass3<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.hb, s.partial, s.ticket, s.nrm2, st, j);
+}
+template <typename T>
+void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream) {
+  const int nb = reduction_blocks(n);
+  ArnoldiState dummy{};
+  count_launches(1), k_norm_start<T><<<nb, 256, 0, stream>>>(b, n, s.partial, s.ticket, s.nrm2, st ? *st : dummy, st ? 1 : 0);
+}
+template <typename T>
+void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n, cudaStream_t stream) {
+  count_launches(1), k_combine<T><<<blocks_for(n, 256), 256, 0, stream>>>(x, Z, ld, k, st, assign ? 1 : 0, n);
+}
+template <typename T>
+void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, const C<T>* w, const double2* alpha,
+                       const C<T>* dinv, C<T>* znext, bool x_zero, int64_t n, cudaStream_t stream) {
+  count_launches(1), k_mr_update2<T><<<blocks_for(n, 256), 256, 0, stream>>>(x, z, r_src, r_dst, w, alpha, dinv, znext,
+                                                                               x_zero ? 1 : 0, n);
+}
+
+#define ADR_INSTANTIATE_FUSED(T)                                                                                           \
+  template void launch_cgs2<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, int, cudaStream_t); \
+  template void launch_norm_start<T>(const C<T>*, int64_t, const KrylovScratch&, const ArnoldiState*, cudaStream_t);        \
+  template void launch_combine<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, bool, int64_t, cudaStream_t);     \
+  template void launch_mr_update2<T>(C<T>*, const C<T>*, const C<T>*, C<T>*, const C<T>*, const double2*, const C<T>*, C<T>*, bool, int64_t, cudaStream_t);
+ADR_INSTANTIATE_FUSED(double)
+ADR_INSTANTIATE_FUSED(float)
 
 }  // namespace adr
