@@ -175,7 +175,9 @@ template <typename T> struct FineOp {
   const C<T>* rho;   // w^2 (kappa^2 - |grad tau|^2) - i w gamma kappa^2
   const C<T>* src_row;    // row of M^{-1} H M at the source (cross form, device)
   T h[3];
-  T ih2[3];
+  T ih2[3];          // 1 / h^2
+  T ih[3];           // 1 / h
+  T hih[3];          // 1 / (2 h)
   T w2, w1;          // weights of the second- and first-order upwind differences
   int central;       // 1: central ADR scheme (upwind only on boundary nodes)
   int near;          // Chebyshev radius around the source with central advection
@@ -200,6 +202,7 @@ struct FineInputs {
   int src[3];
   double omega;
   double h[3];
+  double ih[3];   // 1 / h
 };
 
 // Fine coefficients in float64 (g, t, rho, tau) and the source row.
@@ -221,6 +224,11 @@ template <typename T> void launch_fine_mr_apply(const Dims& g, const FineOp<T>& 
                                                 double2* partial, unsigned* ticket, double2* alpha, cudaStream_t st);
 template <typename T> void launch_fine_residual_dinv(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* x,
                                                      const C<T>* dinv, C<T>* r, C<T>* z, cudaStream_t st);
+// Stored float64 cross rows (point-major, (1 + 4 dim) x N) of a fine operator,
+// and the plain stencil apply / residual with them.
+void launch_fine_store_rows(const Dims& g, const FineOp<double>& f, double2* rows, cudaStream_t st);
+void launch_rows_apply(const Dims& g, const double2* rows, const double2* x, double2* y, cudaStream_t st);
+void launch_rows_residual(const Dims& g, const double2* rows, const double2* b, const double2* x, double2* r, cudaStream_t st);
 // Writes the per-source values read by the fine kernels.
 void launch_set_dyn(FineDyn* d, const FineDyn& v, cudaStream_t st);
 // Galerkin product of the fine operator into the stored stencil of level 1.
@@ -239,6 +247,13 @@ template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc
 // Transfers.
 template <typename T> void launch_restrict(const Dims& gf, const Dims& gc, const C<T>* rf, C<T>* rc, cudaStream_t st);
 template <typename T> void launch_prolong_add(const Dims& gf, const Dims& gc, const C<T>* ec, C<T>* xf, cudaStream_t st);
+
+// Largest grid of the fused relaxation kernels (grid-stride beyond): about
+// sixteen 256-thread blocks per SM keeps every SM busy while bounding the
+// number of blocks that meet at the ticket of the last-block reduction (a
+// full one-node-per-thread grid spent more time on that atomic than on the
+// stencil).  Also sizes their partial sums.
+constexpr int kMaxMrBlocks = 2432;
 
 // Counts kernel launches issued by the library (all threads).
 void count_launches(int n);

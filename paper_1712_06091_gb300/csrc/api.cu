@@ -85,7 +85,8 @@ template <typename T> struct Level {
 };
 
 constexpr int kMaxDots = kMaxKrylov + 2;
-constexpr int64_t kSmallCoarse = 8192;  // coarsest grids up to this size are solved by one block
+constexpr int64_t kSmallCoarse = 8192;      // one-block coarsest solve up to this size (no cluster)
+constexpr int64_t kClusterCoarse = 32768;   // cluster coarsest solve up to this size
 
 static void take_arnoldi(Arena& a, ArnoldiState& s, int m) {
   s.m = m;
@@ -130,6 +131,7 @@ struct Op {
   double2* Z = nullptr;
   double2* b = nullptr;  // point-source right-hand side
   double2* r = nullptr;
+  double2* rows2up = nullptr;  // stored float64 rows of H_2up for the outer iteration
   ArnoldiState ost{};
   KrylovScratch ks{};
   FineDyn* dyn = nullptr;           // omega and the source, read by the fine kernels
@@ -138,6 +140,7 @@ struct Op {
   cudaGraphExec_t cycle_exec = nullptr;
   long long cycle_kernels = 0;
   bool use_graph = true;
+  int cluster_size = 0;             // CTAs of the coarsest-grid cluster solver (0: not available)
   void* arena = nullptr;
   size_t arena_bytes = 0;
   double* host_scal = nullptr;  // pinned: [0] estimate, [1] hn, [2] norm^2
@@ -205,8 +208,10 @@ static void plan(Op& op, Arena& a) {
   op.Z = a.take<double2>((size_t)m * N);
   op.b = a.take<double2>(N);
   op.r = a.take<double2>(N);
+  op.rows2up = a.take<double2>((size_t)(1 + 4 * op.dim) * N);
   take_arnoldi(a, op.ost, m);
-  op.ks.partial = a.take<double2>((size_t)kMaxReduceBlocks * kMaxDots);
+  const size_t partial_cgs = (size_t)kMaxReduceBlocks * kMaxDots, partial_mr = (size_t)kMaxMrBlocks * 2;
+  op.ks.partial = a.take<double2>(partial_cgs > partial_mr ? partial_cgs : partial_mr);
   op.ks.ticket = a.take<unsigned>(1);
   op.ks.ha = a.take<double2>(kMaxDots);
   op.ks.hb = a.take<double2>(kMaxDots);
@@ -223,8 +228,10 @@ template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool 
       f.t[d] = f32 ? (const T*)(const void*)op.tf[d] : (const T*)(const void*)op.td[d];
       f.h[d] = (T)op.h[d];
       f.ih2[d] = (T)(1.0 / (op.h[d] * op.h[d]));
+      f.ih[d] = (T)(1.0 / op.h[d]);
+      f.hih[d] = (T)(0.5 / op.h[d]);
     } else {
-      f.g[d] = nullptr; f.t[d] = nullptr; f.h[d] = T(1); f.ih2[d] = T(0);
+      f.g[d] = nullptr; f.t[d] = nullptr; f.h[d] = T(1); f.ih2[d] = T(0); f.ih[d] = T(0); f.hih[d] = T(0);
     }
   }
   f.dyn = op.dyn;
@@ -314,6 +321,10 @@ template <typename T> struct Cycle {
     Level<T>& L = H.lv[l];
     const int64_t n = L.g.N;
     const int k = L.kdim;
+    if (l > 0 && op.cluster_size > 0 && k <= kClusterKMax && n <= kClusterCoarse) {
+      launch_coarse_gmres_cluster<T>(L.g, L.A, L.dinv, b, x, L.KV, L.z, k, L.ks, op.cluster_size, st);
+      return;
+    }
     if (l > 0 && n <= kSmallCoarse) {
       launch_coarse_gmres_cta<T>(L.g, L.A, L.dinv, b, x, L.KV, L.z, k, L.ks, st);
       return;
@@ -392,7 +403,7 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
   launch_set_dyn(op.dyn, dyn, op.st);
   FineInputs in{};
   in.kappa = kappa; in.tau1 = tau1; in.gamma = gamma;
-  for (int d = 0; d < 3; ++d) { in.src[d] = op.src[d]; in.h[d] = op.h[d]; }
+  for (int d = 0; d < 3; ++d) { in.src[d] = op.src[d]; in.h[d] = op.h[d]; in.ih[d] = 1.0 / op.h[d]; }
   in.omega = op.omega;
   launch_coefficients(op.g0, in, op.gd, op.td, op.rho, op.tau, op.srow, op.st);
   for (int d = 0; d < op.dim; ++d) {
@@ -401,6 +412,7 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
   }
   launch_to_f32((const double*)op.rho, op.rhof, 2 * N, op.st);
   launch_to_f32((const double*)op.srow, op.srowf, 2 * kCross3, op.st);
+  launch_fine_store_rows(op.g0, make_fine<double>(op, ADR_SCHEME_2UP, false), op.rows2up, op.st);
   ADR_TRY(check_launch("coefficients"));
   return op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32);
 }
@@ -562,6 +574,7 @@ int adr_operator_create(int dim, const int* n, const double* h, const int* src, 
   Arena real;
   real.base = (char*)op.arena;
   plan(op, real);
+  op.cluster_size = prepare_coarse_cluster(dim, p.precond_precision == ADR_F32);
   e = cudaStreamCreateWithFlags(&op.cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMemsetAsync(op.ks.ticket, 0, sizeof(unsigned), op.st);
   if (e != cudaSuccess) {
@@ -642,7 +655,9 @@ int adr_apply(adr_op_t h, int scheme, int precision, const void* x, void* y) {
   if (!h || !x || !y) return fail(ADR_ERR_ARG, "null argument");
   if (scheme < ADR_SCHEME_2UP || scheme > ADR_SCHEME_PREC) return fail(ADR_ERR_ARG, "unknown scheme");
   Op& op = h->op;
-  if (precision == ADR_F64) {
+  if (precision == ADR_F64 && scheme == ADR_SCHEME_2UP) {
+    launch_rows_apply(op.g0, op.rows2up, (const double2*)x, (double2*)y, op.st);   // the outer iteration's operator
+  } else if (precision == ADR_F64) {
     FineOp<double> f = make_fine<double>(op, scheme, false);
     launch_fine_apply<double>(op.g0, f, (const double2*)x, (double2*)y, op.st);
   } else if (precision == ADR_F32) {
@@ -719,7 +734,6 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
     ADR_TRY(adr_point_source_rhs(h, op.b));
     b = op.b;
   }
-  const FineOp<double> A = make_fine<double>(op, ADR_SCHEME_2UP, false);
 
   launch_norm_start<double>(b, N, op.ks, nullptr, st);
   ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
@@ -731,7 +745,7 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
     return check_launch("adr_solve");
   }
   if (use_x0) {
-    launch_fine_residual<double>(op.g0, A, b, a, op.r, st);
+    launch_rows_residual(op.g0, op.rows2up, b, a, op.r, st);
   } else {
     launch_zero<double>(a, N, st);
     launch_copy<double>(b, op.r, N, st);
@@ -751,7 +765,7 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
       double2* zj = op.Z + (int64_t)j * N;
       double2* w = op.V + (int64_t)(j + 1) * N;  // A z_j, orthogonalised and normalised in place
       ADR_TRY(precondition(op, vj, zj));
-      launch_fine_apply<double>(op.g0, A, zj, w, st);
+      launch_rows_apply(op.g0, op.rows2up, zj, w, st);
       launch_cgs2<double>(op.V, N, j + 1, w, N, op.ks, op.ost, j, st);
       launch_scale_inv_norm<double>(w, w, op.ks.nrm2, N, st);
       ADR_TRY(check_launch("adr_solve iteration"));
@@ -767,7 +781,7 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
     if (status == ADR_ERR_NAN) break;
     launch_backsolve(op.ost, k, st);
     launch_combine<double>(a, op.Z, N, k, op.ost, false, N, st);
-    launch_fine_residual<double>(op.g0, A, b, a, op.r, st);
+    launch_rows_residual(op.g0, op.rows2up, b, a, op.r, st);
     launch_norm_start<double>(op.r, N, op.ks, &op.ost, st);
     ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
     beta = sqrt(op.host_scal[0]);

@@ -2,6 +2,7 @@
 // (Eq. coarseGridMatrix, A_c = P^T A P), bilinear / trilinear transfers
 // (P and its transpose, Sec. 3.1), relaxation and residuals on those levels.
 #include "adr_common.cuh"
+#include "coarse_stencil.cuh"
 #include "krylov_dev.cuh"
 #include "reduce.cuh"
 
@@ -9,22 +10,6 @@ namespace adr {
 
 static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// sum_p A[p][j] x[j + o_p] over the pattern points whose neighbour is inside.
-template <int DIM, typename T>
-__device__ __forceinline__ C<T> stencil_dot(const Dims& g, const C<T>* __restrict__ A, const C<T>* __restrict__ x,
-                                            int64_t j, int i0, int i1, int i2) {
-  constexpr int S = PatternSize<DIM>::value;
-  C<T> acc = czero<T>();
-#pragma unroll 9
-  for (int p = 0; p < S; ++p) {
-    const int8_t* o = pattern_offset<DIM>(p);
-    const int k0 = i0 + o[0], k1 = i1 + o[1], k2 = i2 + o[2];
-    const bool in = (unsigned)k0 < (unsigned)g.n[0] && (unsigned)k1 < (unsigned)g.n[1] &&
-                    (DIM < 3 || (unsigned)k2 < (unsigned)g.n[2]);
-    if (in) acc = cfma(A[(int64_t)p * g.N + j], x[j + o[0] + g.s1 * o[1] + g.s2 * o[2]], acc);
-  }
-  return acc;
-}
 
 template <int DIM, typename T>
 __global__ void k_stencil_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
@@ -271,6 +256,7 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
   __shared__ double2 sh[32 * 4];
   __shared__ double2 ha[kMaxKrylov + 1];
   __shared__ double2 hb[kMaxKrylov + 1];
+  __shared__ C<T> cv[kMaxKrylov + 1];
   __shared__ double s_scale;
   const int64_t n = g.N;
   // beta = |b|, V_0 = b / beta
@@ -305,17 +291,21 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
     }
     __syncthreads();
     cta_dots<T>(V, n, j + 1, w, ha, sh);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) cv[i] = mk<T>((T)(-ha[i].x), (T)(-ha[i].y));
+    __syncthreads();
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       C<T> acc = w[e];
-      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], mk<T>((T)(-ha[i].x), (T)(-ha[i].y)), acc);
+      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
       w[e] = acc;
     }
     __syncthreads();
     cta_dots<T>(V, n, j + 1, w, hb, sh);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) cv[i] = mk<T>((T)(-hb[i].x), (T)(-hb[i].y));
+    __syncthreads();
     C<T> s[1] = {czero<T>()};
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       C<T> acc = w[e];
-      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], mk<T>((T)(-hb[i].x), (T)(-hb[i].y)), acc);
+      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
       w[e] = acc;
       s[0] = cfma_conj(acc, acc, s[0]);
     }
@@ -335,16 +325,18 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
   }
   if (threadIdx.x == 0) backsolve_dev(st, k);
   __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cv[i] = mk<T>((T)st.y[i].x, (T)st.y[i].y);
+  __syncthreads();
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
     C<T> acc = czero<T>();
-    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * n + e], mk<T>((T)st.y[i].x, (T)st.y[i].y), acc);
+    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
     x[e] = cmul(dinv[e], acc);
   }
 }
 
 static inline unsigned mr_blocks_c(int64_t n) {
   int64_t b = (n + 255) / 256;
-  return (unsigned)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+  return (unsigned)(b < kMaxMrBlocks ? (b < 1 ? 1 : b) : kMaxMrBlocks);
 }
 
 template <typename T>

@@ -35,30 +35,31 @@ __global__ void k_coefficients(Dims g, FineInputs in, double* g0, double* g1, do
     r2 += dx[d] * dx[d];
   }
   const double r = sqrt(r2);
+  const double ir = r > 0.0 ? 1.0 / r : 0.0;
   const double T1 = in.tau1[j];
   double* gout[3] = {g0, g1, g2};
   double* tout[3] = {t0, t1, t2};
   double grad2 = 0.0;
   for (int d = 0; d < g.dim; ++d) {
     const int k = ii[d], n = g.n[d];
-    const double h = in.h[d];
+    const double ih = in.ih[d], ih2 = ih * ih;   // reciprocals precomputed: no float64 division per node
     double d1, dd1;
     if (k == 0) {
-      d1 = (tau1_at(g, in.tau1, j, d, k, 1) - tau1_at(g, in.tau1, j, d, k, 0)) / h;
+      d1 = (tau1_at(g, in.tau1, j, d, k, 1) - tau1_at(g, in.tau1, j, d, k, 0)) * ih;
       dd1 = (2.0 * tau1_at(g, in.tau1, j, d, k, 0) - 5.0 * tau1_at(g, in.tau1, j, d, k, 1) +
-             4.0 * tau1_at(g, in.tau1, j, d, k, 2) - tau1_at(g, in.tau1, j, d, k, 3)) / (h * h);
+             4.0 * tau1_at(g, in.tau1, j, d, k, 2) - tau1_at(g, in.tau1, j, d, k, 3)) * ih2;
     } else if (k == n - 1) {
-      d1 = (tau1_at(g, in.tau1, j, d, k, n - 1) - tau1_at(g, in.tau1, j, d, k, n - 2)) / h;
+      d1 = (tau1_at(g, in.tau1, j, d, k, n - 1) - tau1_at(g, in.tau1, j, d, k, n - 2)) * ih;
       dd1 = (2.0 * tau1_at(g, in.tau1, j, d, k, n - 1) - 5.0 * tau1_at(g, in.tau1, j, d, k, n - 2) +
-             4.0 * tau1_at(g, in.tau1, j, d, k, n - 3) - tau1_at(g, in.tau1, j, d, k, n - 4)) / (h * h);
+             4.0 * tau1_at(g, in.tau1, j, d, k, n - 3) - tau1_at(g, in.tau1, j, d, k, n - 4)) * ih2;
     } else {
-      d1 = (tau1_at(g, in.tau1, j, d, k, k + 1) - tau1_at(g, in.tau1, j, d, k, k - 1)) / (2.0 * h);
-      dd1 = (tau1_at(g, in.tau1, j, d, k, k + 1) - 2.0 * T1 + tau1_at(g, in.tau1, j, d, k, k - 1)) / (h * h);
+      d1 = (tau1_at(g, in.tau1, j, d, k, k + 1) - tau1_at(g, in.tau1, j, d, k, k - 1)) * (0.5 * ih);
+      dd1 = (tau1_at(g, in.tau1, j, d, k, k + 1) - 2.0 * T1 + tau1_at(g, in.tau1, j, d, k, k - 1)) * ih2;
     }
     double d0 = 0.0, dd0 = 0.0;
     if (r > 0.0) {
-      d0 = dx[d] / r;
-      dd0 = (1.0 - d0 * d0) / r;
+      d0 = dx[d] * ir;
+      dd0 = (1.0 - d0 * d0) * ir;
     }
     const double gd = __dadd_rn(__dmul_rn(r, d1), __dmul_rn(T1, d0));
     const double td = T1 * dd0 + 2.0 * d0 * d1 + r * dd1;
@@ -146,7 +147,7 @@ __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int6
     cre -= T(2) * ih2;
     // advection difference weights at offsets -2..+2
     T wm2 = 0, wm1 = 0, w0 = 0, wp1 = 0, wp2 = 0;
-    const T half_ih = T(0.5) / h;
+    const T half_ih = f.hih[d];
     if (near || gd == T(0) || (f.central && k > 0 && k < n - 1)) {
       wp1 = half_ih; wm1 = -half_ih;
     } else {
@@ -162,7 +163,7 @@ __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int6
         }
       }
       if (a1 != T(0)) {
-        const T ih = T(1) / h;
+        const T ih = f.ih[d];
         if (gd > T(0)) {
           if (k >= 1) { w0 += a1 * ih; wm1 -= a1 * ih; }
           else { wp1 += a1 * half_ih; wm1 -= a1 * half_ih; }
@@ -202,20 +203,24 @@ template <int DIM> __device__ __forceinline__ int64_t axis_stride(const Dims& g,
   return d == 0 ? 1 : (d == 1 ? g.s1 : g.s2);
 }
 
-// sum_k c_k x_{j + o_k} over the in-grid cross entries
+// sum_k c_k x_{j + o_k} over the cross entries.  Entries whose neighbour is
+// off the grid are exactly zero (ghosts are eliminated into the row), so the
+// load is redirected to node j instead of branching; all loads issue together.
 template <int DIM, typename T>
 __device__ __forceinline__ C<T> cross_dot(const Dims& g, const C<T>* c, const int ii[3], int64_t j, const C<T>* x) {
-  C<T> acc = cmul(c[0], x[j]);
+  C<T> acc0 = cmul(c[0], __ldg(x + j)), acc1 = czero<T>();
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int64_t s = axis_stride<DIM>(g, d);
     const int k = ii[d], n = g.n[d];
-    if (k >= 1) acc = cfma(c[1 + 4 * d + 0], x[j - s], acc);
-    if (k <= n - 2) acc = cfma(c[1 + 4 * d + 1], x[j + s], acc);
-    if (k >= 2) acc = cfma(c[1 + 4 * d + 2], x[j - 2 * s], acc);
-    if (k <= n - 3) acc = cfma(c[1 + 4 * d + 3], x[j + 2 * s], acc);
+    const int64_t jm1 = k >= 1 ? j - s : j, jp1 = k <= n - 2 ? j + s : j;
+    const int64_t jm2 = k >= 2 ? j - 2 * s : j, jp2 = k <= n - 3 ? j + 2 * s : j;
+    acc1 = cfma(c[1 + 4 * d + 0], __ldg(x + jm1), acc1);
+    acc0 = cfma(c[1 + 4 * d + 1], __ldg(x + jp1), acc0);
+    acc1 = cfma(c[1 + 4 * d + 2], __ldg(x + jm2), acc1);
+    acc0 = cfma(c[1 + 4 * d + 3], __ldg(x + jp2), acc0);
   }
-  return acc;
+  return cadd(acc0, acc1);
 }
 
 template <int DIM, typename T>
@@ -474,7 +479,7 @@ void launch_set_dyn(FineDyn* d, const FineDyn& v, cudaStream_t st) { count_launc
 
 static inline unsigned mr_blocks(int64_t n) {
   int64_t b = (n + 255) / 256;
-  return (unsigned)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+  return (unsigned)(b < kMaxMrBlocks ? (b < 1 ? 1 : b) : kMaxMrBlocks);
 }
 
 template <typename T>
@@ -498,5 +503,64 @@ template void launch_fine_residual_dinv<double>(const Dims&, const FineOp<double
                                                 const double2*, double2*, double2*, cudaStream_t);
 template void launch_fine_residual_dinv<float>(const Dims&, const FineOp<float>&, const float2*, const float2*,
                                                const float2*, float2*, float2*, cudaStream_t);
+
+}  // namespace adr
+
+// ===========================================================================
+// Stored cross rows: the fine operator of the float64 outer iteration, written
+// once per setup so that each outer apply costs a plain 9/13-point complex
+// stencil (about 40 float64 FMAs per node instead of rebuilding the row).
+// ===========================================================================
+namespace adr {
+
+template <int DIM, typename T>
+__global__ void k_fine_store_rows(Dims g, FineOp<T> f, C<T>* __restrict__ rows) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  C<T> c[1 + 4 * DIM];
+  fine_row<DIM, T>(g, f, j, ii, c);
+#pragma unroll
+  for (int q = 0; q < 1 + 4 * DIM; ++q) rows[(int64_t)q * g.N + j] = c[q];
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ C<T> rows_dot(const Dims& g, const C<T>* __restrict__ rows, int64_t j, const C<T>* __restrict__ x) {
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  C<T> c[1 + 4 * DIM];
+#pragma unroll
+  for (int q = 0; q < 1 + 4 * DIM; ++q) c[q] = __ldg(rows + (int64_t)q * g.N + j);
+  return cross_dot<DIM, T>(g, c, ii, j, x);
+}
+
+template <int DIM, typename T>
+__global__ void k_rows_apply(Dims g, const C<T>* __restrict__ rows, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  y[j] = rows_dot<DIM, T>(g, rows, j, x);
+}
+
+template <int DIM, typename T>
+__global__ void k_rows_residual(Dims g, const C<T>* __restrict__ rows, const C<T>* __restrict__ b,
+                                const C<T>* __restrict__ x, C<T>* __restrict__ r) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  r[j] = csub(b[j], rows_dot<DIM, T>(g, rows, j, x));
+}
+
+void launch_fine_store_rows(const Dims& g, const FineOp<double>& f, double2* rows, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_fine_store_rows<2, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
+  else count_launches(1), k_fine_store_rows<3, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
+}
+void launch_rows_apply(const Dims& g, const double2* rows, const double2* x, double2* y, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_rows_apply<2, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, x, y);
+  else count_launches(1), k_rows_apply<3, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, x, y);
+}
+void launch_rows_residual(const Dims& g, const double2* rows, const double2* b, const double2* x, double2* r, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_rows_residual<2, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, b, x, r);
+  else count_launches(1), k_rows_residual<3, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, b, x, r);
+}
 
 }  // namespace adr

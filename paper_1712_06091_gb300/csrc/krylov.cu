@@ -118,13 +118,14 @@ void launch_axpy_multi(C<T>* w, const C<T>* V, int64_t ld, int k, const double2*
   count_launches(1), k_axpy_multi<T><<<blocks_for(n, 256), 256, 0, st>>>(w, V, ld, k, coef, sign, n);
 }
 
-// out = w / sqrt(nrm2->x), or zero if the norm vanishes.
+// out = w / |w| with the reciprocal norm precomputed in nrm2->y by the kernel
+// that reduced nrm2->x (zero if the norm vanishes): no per-thread float64
+// square root or division.
 template <typename T>
 __global__ void k_scale_inv_norm(const C<T>* w, C<T>* out, const double2* __restrict__ nrm2, int64_t n) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const double s = sqrt(nrm2->x);
-  const T inv = s > 0.0 ? (T)(1.0 / s) : T(0);
+  const T inv = (T)nrm2->y;
   out[e] = cscale(w[e], inv);
 }
 template <typename T>
@@ -340,12 +341,12 @@ __global__ void __launch_bounds__(256) k_cgs_pass2(const C<T>* __restrict__ V, i
                                                    double2* hb) {
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[kMaxKrylov + 1];
+  __shared__ C<T> coef[kMaxKrylov + 1];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-ha[i].x), (T)(-ha[i].y));
+  __syncthreads();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     C<T> acc = w[e];
-    for (int i = 0; i < k; ++i) {
-      const double2 cd = ha[i];
-      acc = cfma(V[(int64_t)i * ld + e], mk<T>((T)(-cd.x), (T)(-cd.y)), acc);
-    }
+    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
     w[e] = acc;
   }
   block_dots<T>(V, ld, k, w, n, blk, sh);   // each thread re-reads only its own elements of w
@@ -359,22 +360,24 @@ __global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, i
                                                    double2* partial, unsigned* ticket, double2* nrm2, ArnoldiState st, int j) {
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[1];
-  C<T> s2 = czero<T>();
+  __shared__ C<T> coef[kMaxKrylov + 1];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-hb[i].x), (T)(-hb[i].y));
+  __syncthreads();
+  C<T> s2[1] = {czero<T>()};
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     C<T> acc = w[e];
-    for (int i = 0; i < k; ++i) {
-      const double2 cd = hb[i];
-      acc = cfma(V[(int64_t)i * ld + e], mk<T>((T)(-cd.x), (T)(-cd.y)), acc);
-    }
+    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
     w[e] = acc;
-    s2 = cfma_conj(acc, acc, s2);
+    s2[0] = cfma_conj(acc, acc, s2[0]);
   }
-  double2 v[1] = {make_double2((double)s2.x, 0.0)}, o[1];
-  block_sum_k<1>(v, sh, o);
+  double2 o[1];
+  block_sum_t<T, 1>(s2, sh, o);
   if (threadIdx.x == 0) blk[0] = o[0];
   __syncthreads();
   if (last_block_rt(1, blk, partial, ticket, nrm2, sh) && threadIdx.x == 0) {
-    if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, nrm2->x);
+    const double s2t = nrm2->x;
+    nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
+    if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, s2t);
   }
 }
 
@@ -384,15 +387,17 @@ __global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, do
                                                     double2* nrm2, ArnoldiState st, int start) {
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[1];
-  C<T> s2 = czero<T>();
+  C<T> s2[1] = {czero<T>()};
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    s2 = cfma_conj(b[e], b[e], s2);
-  double2 v[1] = {make_double2((double)s2.x, 0.0)}, o[1];
-  block_sum_k<1>(v, sh, o);
+    s2[0] = cfma_conj(b[e], b[e], s2[0]);
+  double2 o[1];
+  block_sum_t<T, 1>(s2, sh, o);
   if (threadIdx.x == 0) blk[0] = o[0];
   __syncthreads();
-  if (last_block_rt(1, blk, partial, ticket, nrm2, sh) && threadIdx.x == 0 && start) {
+  if (last_block_rt(1, blk, partial, ticket, nrm2, sh) && threadIdx.x == 0) {
     const double beta = sqrt(nrm2->x);
+    nrm2->y = beta > 0.0 ? 1.0 / beta : 0.0;
+    if (!start) return;
     for (int i = 0; i <= st.m; ++i) st.g[i] = make_double2(0.0, 0.0);
     st.g[0] = make_double2(beta, 0.0);
     st.scal[kScalBeta] = beta;
@@ -404,13 +409,13 @@ __global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, do
 // x = (assign ? 0 : x) + sum_i Z_i y_i  (y from the state, i < k)
 template <typename T>
 __global__ void k_combine(C<T>* x, const C<T>* __restrict__ Z, int64_t ld, int k, ArnoldiState st, int assign, int64_t n) {
+  __shared__ C<T> coef[kMaxKrylov];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)st.y[i].x, (T)st.y[i].y);
+  __syncthreads();
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
   C<T> acc = assign ? czero<T>() : x[e];
-  for (int i = 0; i < k; ++i) {
-    const double2 yi = st.y[i];
-    acc = cfma(Z[(int64_t)i * ld + e], mk<T>((T)yi.x, (T)yi.y), acc);
-  }
+  for (int i = 0; i < k; ++i) acc = cfma(Z[(int64_t)i * ld + e], coef[i], acc);
   x[e] = acc;
 }
 

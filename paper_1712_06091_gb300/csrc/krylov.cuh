@@ -64,6 +64,15 @@ template <typename T>
 void launch_mr_update(C<T>* x, const C<T>* z, C<T>* r, const C<T>* w, const double2* alpha, const C<T>* dinv, C<T>* znext,
                       int64_t n, cudaStream_t st);
 
+// The same solve on one thread-block cluster (cluster = 16 or 8 CTAs), for
+// Krylov dimensions up to kClusterKMax.  prepare_coarse_cluster returns the
+// cluster size the device can schedule (0 if none); call it outside capture.
+constexpr int kClusterKMax = 32;
+int prepare_coarse_cluster(int dim, bool f32);
+template <typename T>
+void launch_coarse_gmres_cluster(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, C<T>* x, C<T>* V, C<T>* z,
+                                 int k, const ArnoldiState& s, int cluster, cudaStream_t st);
+
 // Whole fixed-count Jacobi-preconditioned GMRES of a small stored-stencil
 // level in one block of 1024 threads (V: (k+1) n scratch, z: n scratch).
 template <typename T>
