@@ -242,6 +242,7 @@ template <typename T> void launch_stencil_mr_apply(const Dims& g, const C<T>* A,
                                                    double2* partial, unsigned* ticket, double2* alpha, cudaStream_t st);
 template <typename T> void launch_stencil_residual_dinv(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x,
                                                         const C<T>* dinv, C<T>* r, C<T>* z, cudaStream_t st);
+template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, cudaStream_t st);
 template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st);
 
 // Transfers.

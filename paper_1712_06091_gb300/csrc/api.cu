@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "krylov.cuh"
+#include "coarse_stencil.cuh"
 
 namespace adr {
 
@@ -170,7 +171,7 @@ template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
   for (int l = 0; l < H.L; ++l) {
     Level<T>& L = H.lv[l];
     const size_t N = (size_t)L.g.N;
-    L.A = l > 0 ? a.take<C<T>>((size_t)S * N) : nullptr;
+    L.A = l > 0 ? a.take<C<T>>((size_t)stencil_entries((int64_t)N, S)) : nullptr;
     L.dinv = a.take<C<T>>(N);
     L.b = a.take<C<T>>(N);
     L.x = a.take<C<T>>(N);
@@ -675,16 +676,11 @@ int adr_level_stencil(adr_op_t h, int level, void* out) {
   const int L = op.p.precond_precision == ADR_F64 ? op.h64.L : op.h32.L;
   if (level < 1 || level >= L) return fail(ADR_ERR_ARG, "level must be in [1, levels)");
   const int S = op.dim == 2 ? kPattern2 : kPattern3;
-  size_t bytes;
-  const void* src;
-  if (op.p.precond_precision == ADR_F64) {
-    bytes = sizeof(double2) * (size_t)S * op.h64.lv[level].g.N;
-    src = op.h64.lv[level].A;
-  } else {
-    bytes = sizeof(float2) * (size_t)S * op.h32.lv[level].g.N;
-    src = op.h32.lv[level].A;
-  }
-  ADR_CUDA(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, op.st));
+  if (op.p.precond_precision == ADR_F64)
+    launch_stencil_export<double>(op.h64.lv[level].A, (double2*)out, op.h64.lv[level].g.N, S, op.st);
+  else
+    launch_stencil_export<float>(op.h32.lv[level].A, (float2*)out, op.h32.lv[level].g.N, S, op.st);
+  ADR_TRY(check_launch("adr_level_stencil"));
   return ADR_OK;
 }
 

@@ -12,7 +12,7 @@ static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n
 
 
 template <int DIM, typename T>
-__global__ void k_stencil_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
   int i0, i1, i2;
@@ -72,7 +72,7 @@ __global__ void k_galerkin_stored(Dims gf, Dims gc, const C<T>* __restrict__ Af,
           bool in = true;
           for (int d = 0; d < DIM; ++d) in = in && k[d] >= 0 && k[d] < gf.n[d];
           if (!in) continue;
-          const C<T> wa = cscale(Af[(int64_t)p * gf.N + fj], wi);
+          const C<T> wa = cscale(Af[stencil_index(p, fj, S)], wi);
           int pj[3][2];
           T pw[3][2];
           int pc[3];
@@ -89,7 +89,7 @@ __global__ void k_galerkin_stored(Dims gf, Dims gc, const C<T>* __restrict__ Af,
               }
         }
       }
-  for (int p = 0; p < S; ++p) out[(int64_t)p * gc.N + I] = acc[p];
+  for (int p = 0; p < S; ++p) out[stencil_index(p, I, S)] = acc[p];
   dinv[I] = cinv(acc[(S - 1) / 2]);
 }
 
@@ -142,6 +142,21 @@ __global__ void k_prolong_add(Dims gf, Dims gc, const C<T>* __restrict__ ec, C<T
   xf[j] = cadd(xf[j], acc);
 }
 
+// Point-major copy (entry p of node j at p * N + j) of a tiled stencil.
+template <typename T>
+__global__ void k_stencil_export(const C<T>* __restrict__ A, C<T>* __restrict__ out, int64_t N, int S) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= N * S) return;
+  const int p = (int)(e / N);
+  const int64_t j = e - (int64_t)p * N;
+  out[e] = A[stencil_index(p, j, S)];
+}
+template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, cudaStream_t st) {
+  count_launches(1), k_stencil_export<T><<<blocks_for(N * S, 256), 256, 0, st>>>(A, out, N, S);
+}
+template void launch_stencil_export<double>(const double2*, double2*, int64_t, int, cudaStream_t);
+template void launch_stencil_export<float>(const float2*, float2*, int64_t, int, cudaStream_t);
+
 template <typename T> void launch_stencil_apply(const Dims& g, const C<T>* A, const C<T>* x, C<T>* y, cudaStream_t st) {
   const int th = 256;
   if (g.dim == 2) count_launches(1), k_stencil_apply<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, A, x, y);
@@ -192,7 +207,7 @@ ADR_INSTANTIATE_COARSE(float)
 namespace adr {
 
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256) k_stencil_mr_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ z,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_mr_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ z,
                                                           const C<T>* __restrict__ r, C<T>* __restrict__ w,
                                                           double2* partial, unsigned* ticket, double2* alpha) {
   __shared__ double2 sh[32 * 2];
@@ -214,7 +229,7 @@ __global__ void __launch_bounds__(256) k_stencil_mr_apply(Dims g, const C<T>* __
 }
 
 template <int DIM, typename T>
-__global__ void k_stencil_residual_dinv(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ b,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_residual_dinv(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ b,
                                         const C<T>* __restrict__ x, const C<T>* __restrict__ dinv, C<T>* __restrict__ r,
                                         C<T>* __restrict__ z) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

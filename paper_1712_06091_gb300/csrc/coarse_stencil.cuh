@@ -27,6 +27,16 @@ __device__ __forceinline__ unsigned axis_mask(int i, int n) {
   return m;
 }
 
+// Layout of a stored stencil: nodes are grouped in tiles of 32 (one warp);
+// a tile keeps its S points' coefficients together, point-major inside the
+// tile, so a warp streams one contiguous 32*S-entry segment (locality in the
+// DRAM pages instead of S scattered streams).  Entry (p, j) lives at
+// ((j / 32) * S + p) * 32 + j % 32; arrays hold S * round_up(N, 32) entries.
+__host__ __device__ __forceinline__ int64_t stencil_index(int p, int64_t j, int S) {
+  return (((j >> 5) * S + p) << 5) + (j & 31);
+}
+__host__ __device__ __forceinline__ int64_t stencil_entries(int64_t N, int S) { return ((N + 31) >> 5) * 32 * S; }
+
 // sum_p A[p][j] x[j + o_p], unrolled over the pattern with compile-time
 // offsets and no branch: a neighbour off the grid is replaced by node j
 // itself, whose product with the (exactly zero) Galerkin coefficient of that
@@ -37,7 +47,8 @@ __device__ __forceinline__ C<T> stencil_dot_seq(const C<T>* __restrict__ A, cons
                                                 int64_t N, int64_t s1, int64_t s2, unsigned m0, unsigned m1, unsigned m2,
                                                 std::integer_sequence<int, P...>) {
   C<T> acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
-  ((acc[P & 3] = cfma(__ldg(A + (int64_t)P * N + j),
+  const C<T>* Aj = A + stencil_index(0, j, (int)sizeof...(P));
+  ((acc[P & 3] = cfma(__ldg(Aj + P * 32),
                       __ldg(x + ((((m0 >> (Off<DIM, P>::o0 + 2)) & (m1 >> (Off<DIM, P>::o1 + 2)) &
                                    (m2 >> (Off<DIM, P>::o2 + 2))) & 1u)
                                      ? j + Off<DIM, P>::o0 + Off<DIM, P>::o1 * s1 + Off<DIM, P>::o2 * s2

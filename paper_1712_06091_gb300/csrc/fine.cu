@@ -9,6 +9,7 @@
 // (Sec. 2.2), the Neumann condition of Eq. BCADR (n.grad a = i w (n.grad tau) a)
 // by ghost elimination, and the row of M^{-1} H M at the source (Eq. helmADR2).
 #include "adr_common.cuh"
+#include "coarse_stencil.cuh"
 #include "reduce.cuh"
 
 namespace adr {
@@ -342,7 +343,7 @@ __global__ void k_galerkin_fine(Dims gf, Dims gc, FineOp<T> f, C<T>* __restrict_
     }
   };
   galerkin_accumulate<DIM, T>(gf, gc, I, Ii, row_of, acc);
-  for (int p = 0; p < S; ++p) out[(int64_t)p * gc.N + I] = acc[p];
+  for (int p = 0; p < S; ++p) out[stencil_index(p, I, S)] = acc[p];
   dinv[I] = cinv(acc[(S - 1) / 2]);
 }
 
@@ -434,7 +435,7 @@ namespace adr {
 // w = A z and, over all nodes, alpha = (w^H r) / (w^H w) (the one-step
 // minimal-residual weight), computed by the last block to finish.
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256) k_fine_mr_apply(Dims g, FineOp<T> f, const C<T>* __restrict__ z,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_fine_mr_apply(Dims g, FineOp<T> f, const C<T>* __restrict__ z,
                                                        const C<T>* __restrict__ r, C<T>* __restrict__ w,
                                                        double2* partial, unsigned* ticket, double2* alpha) {
   __shared__ double2 sh[32 * 2];
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(256) k_fine_mr_apply(Dims g, FineOp<T> f, cons
 
 // r = b - A x ; z = D^{-1} r
 template <int DIM, typename T>
-__global__ void k_fine_residual_dinv(Dims g, FineOp<T> f, const C<T>* __restrict__ b, const C<T>* __restrict__ x,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_fine_residual_dinv(Dims g, FineOp<T> f, const C<T>* __restrict__ b, const C<T>* __restrict__ x,
                                      const C<T>* __restrict__ dinv, C<T>* __restrict__ r, C<T>* __restrict__ z) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
