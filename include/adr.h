@@ -209,6 +209,22 @@ int adr_solve_host(int dim, const int* n, const double* h, const int* src, doubl
 int adr_traveltime(int dim, const int* n, const double* h, const int* src, const double* kappa, double* tau1,
                    int max_sweeps, void* stream, int* sweeps_done);
 
+/* Kernel classes that adr_profile_kernel can time. */
+#define ADR_PROF_NONE 0
+#define ADR_PROF_LEVEL1_RELAX 1   /* minimal-residual apply on level 1 (stored stencil) */
+#define ADR_PROF_FINE_RELAX 2     /* minimal-residual apply on the finest level */
+#define ADR_PROF_OUTER_APPLY 3    /* float64 H_2up apply of the outer iteration */
+#define ADR_PROF_COARSEST 4       /* coarsest-grid solve */
+
+/* Instrumentation: brackets every launch of one kernel class of op with CUDA
+ * events on the stream it runs on (inside the captured cycle as well) and
+ * accumulates their durations at the synchronisation points of adr_solve.
+ * Changing the class discards the captured cycle (recaptured on next use).
+ * adr_profile_read returns the launches timed and their total milliseconds
+ * since the class was set.  Errors: ADR_ERR_ARG, ADR_ERR_CUDA. */
+int adr_profile_kernel(adr_op_t op, int kernel_class);
+int adr_profile_read(adr_op_t op, long long* launches, double* total_ms);
+
 /* Number of CUDA kernels the library has launched since it was loaded (all
  * threads, all operators); an instrumentation counter, never reset. */
 long long adr_kernel_launches(void);

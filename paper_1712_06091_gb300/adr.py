@@ -125,6 +125,17 @@ class Operator:
         self.src = tuple(int(v) for v in src)
         self.omega = float(omega)
 
+    def profile(self, kernel_class="none"):
+        """adr_profile_kernel: time every launch of one kernel class with CUDA events."""
+        L.check(self._lib.adr_profile_kernel(self._h, L.PROFILE_CLASSES[kernel_class]))
+
+    def profile_read(self):
+        """(launches timed, total milliseconds) since profile() was called."""
+        n = ctypes.c_longlong(0)
+        ms = ctypes.c_double(0.0)
+        L.check(self._lib.adr_profile_read(self._h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
     # -- queries ----------------------------------------------------------
     def info(self) -> dict:
         i = L.OpInfo()
@@ -215,15 +226,19 @@ def traveltime(n, h, src, kappa, max_sweeps=None, device="cuda", stream=None):
 
 
 def solve_host(n, h, src, omega, kappa, tau1, gamma, params=None, tol=1e-8, maxit=500, stream=None,
-               want_amplitude=False):
-    """adr_solve_host: host numpy arrays in, host complex128 u (and a) out."""
+               want_amplitude=False, out=None):
+    """adr_solve_host: host numpy arrays in, host complex128 u (and a) out.
+
+    `out` may be a preallocated (e.g. pinned) complex128 host array for u."""
     lib = L.load()
     dim = len(n)
     N = int(np.prod(n))
     k = np.ascontiguousarray(kappa, dtype=np.float64).reshape(-1)
     t = np.ascontiguousarray(tau1, dtype=np.float64).reshape(-1)
     g = np.ascontiguousarray(gamma, dtype=np.float64).reshape(-1)
-    u = np.empty(N, dtype=np.complex128)
+    u = np.empty(N, dtype=np.complex128) if out is None else out
+    if u.dtype != np.complex128 or u.size != N or not u.flags.c_contiguous:
+        raise ValueError("out must be a contiguous complex128 array of N entries")
     a = np.empty(N, dtype=np.complex128) if want_amplitude else None
     p = params if params is not None else default_params()
     nn = (ctypes.c_int * 3)(*n, *([1] * (3 - dim)))

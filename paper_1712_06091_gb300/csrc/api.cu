@@ -142,10 +142,58 @@ struct Op {
   long long cycle_kernels = 0;
   bool use_graph = true;
   int cluster_size = 0;             // CTAs of the coarsest-grid cluster solver (0: not available)
+  // instrumentation (adr_profile_kernel): event pairs 2k, 2k+1 of prof_pool
+  int prof_class = ADR_PROF_NONE;
+  std::vector<cudaEvent_t> prof_pool;
+  int prof_graph_pairs = 0;         // pairs recorded inside the captured cycle
+  int prof_stream_pairs = 0;        // pairs recorded on the stream since the last collection
+  bool prof_graph_fresh = false;    // the cycle was replayed since the last collection
+  bool capturing = false;
+  long long prof_count = 0;
+  double prof_ms = 0.0;
   void* arena = nullptr;
   size_t arena_bytes = 0;
   double* host_scal = nullptr;  // pinned: [0] estimate, [1] hn, [2] norm^2
 };
+
+constexpr int kProfPairs = 256;
+
+// Starts timing one launch of class cls on stream s; returns the pair index or -1.
+static int prof_begin(Op& op, int cls, cudaStream_t s) {
+  if (op.prof_class != cls || op.prof_pool.empty()) return -1;
+  int k;
+  if (op.capturing) {
+    if (op.prof_graph_pairs >= kProfPairs / 2) return -1;
+    k = op.prof_graph_pairs++;
+  } else {
+    if (kProfPairs / 2 + op.prof_stream_pairs >= kProfPairs) return -1;
+    k = kProfPairs / 2 + op.prof_stream_pairs++;
+  }
+  // Inside stream capture a plain record only marks a dependency; the external
+  // flag turns it into an event-record node of the graph.
+  cudaEventRecordWithFlags(op.prof_pool[2 * k], s, op.capturing ? cudaEventRecordExternal : 0);
+  return k;
+}
+static void prof_end(Op& op, int k, cudaStream_t s) {
+  if (k >= 0) cudaEventRecordWithFlags(op.prof_pool[2 * k + 1], s, op.capturing ? cudaEventRecordExternal : 0);
+}
+// Adds the completed pairs to the totals (call after a stream synchronisation).
+static void prof_collect(Op& op) {
+  if (op.prof_class == ADR_PROF_NONE || op.prof_pool.empty()) return;
+  auto add = [&](int k) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, op.prof_pool[2 * k], op.prof_pool[2 * k + 1]) == cudaSuccess) {
+      op.prof_ms += ms;
+      op.prof_count += 1;
+    }
+  };
+  if (op.prof_graph_fresh)
+    for (int k = 0; k < op.prof_graph_pairs; ++k) add(k);
+  for (int k = 0; k < op.prof_stream_pairs; ++k) add(kProfPairs / 2 + k);
+  op.prof_graph_fresh = false;
+  op.prof_stream_pairs = 0;
+  cudaGetLastError();
+}
 
 static bool can_coarsen(const Dims& g) {
   for (int d = 0; d < g.dim; ++d)
@@ -268,8 +316,10 @@ template <typename T> struct Cycle {
     else launch_stencil_residual_dinv<T>(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, st);
   }
   void mr_apply(int l, const C<T>* z, const C<T>* r, C<T>* w) {
+    const int pk = prof_begin(op, l == 0 ? ADR_PROF_FINE_RELAX : (l == 1 ? ADR_PROF_LEVEL1_RELAX : -1), st);
     if (l == 0) launch_fine_mr_apply<T>(H.lv[0].g, H.prec, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
     else launch_stencil_mr_apply<T>(H.lv[l].g, H.lv[l].A, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
+    prof_end(op, pk, st);
   }
 
   // `sweeps` relaxations on A_l x = b; x_zero says x holds zero on entry.
@@ -319,6 +369,11 @@ template <typename T> struct Cycle {
 
   // Fixed-count GMRES from zero, right-preconditioned by D^{-1} (coarsest level).
   void coarse_solve(int l, const C<T>* b, C<T>* x) {
+    const int pk = prof_begin(op, ADR_PROF_COARSEST, st);
+    coarse_solve_impl(l, b, x);
+    prof_end(op, pk, st);
+  }
+  void coarse_solve_impl(int l, const C<T>* b, C<T>* x) {
     Level<T>& L = H.lv[l];
     const int64_t n = L.g.N;
     const int k = L.kdim;
@@ -432,8 +487,11 @@ template <typename T> static int run_cycle(Op& op, Hier<T>& H) {
   if (!op.cycle_exec) {
     const long long before = g_launches.load(std::memory_order_relaxed);
     ADR_CUDA(cudaStreamBeginCapture(op.cap, cudaStreamCaptureModeThreadLocal));
+    op.prof_graph_pairs = 0;
+    op.capturing = true;
     Cycle<T> c{op, H, op.cap};
     c.cycle(0, L0.b, L0.x);
+    op.capturing = false;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(op.cap, &graph);
     if (e != cudaSuccess) return fail(ADR_ERR_CUDA, std::string("cycle capture: ") + cudaGetErrorString(e));
@@ -448,6 +506,7 @@ template <typename T> static int run_cycle(Op& op, Hier<T>& H) {
   }
   ADR_CUDA(cudaGraphLaunch(op.cycle_exec, op.st));
   count_launches((int)op.cycle_kernels);
+  op.prof_graph_fresh = true;
   return ADR_OK;
 }
 
@@ -470,6 +529,7 @@ static int precondition(Op& op, const double2* v, double2* z) {
 static int read_scalars(Op& op, const double* dev, int count) {
   ADR_CUDA(cudaMemcpyAsync(op.host_scal, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, op.st));
   ADR_CUDA(cudaStreamSynchronize(op.st));
+  prof_collect(op);
   return ADR_OK;
 }
 
@@ -614,12 +674,45 @@ int adr_operator_update(adr_op_t h, const int* src, double omega, const double* 
 
 long long adr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int adr_profile_kernel(adr_op_t h, int kernel_class) {
+  if (!h) return fail(ADR_ERR_ARG, "null argument");
+  if (kernel_class < ADR_PROF_NONE || kernel_class > ADR_PROF_COARSEST) return fail(ADR_ERR_ARG, "unknown kernel class");
+  Op& op = h->op;
+  ADR_CUDA(cudaStreamSynchronize(op.st));
+  if (kernel_class != ADR_PROF_NONE && op.prof_pool.empty()) {
+    op.prof_pool.resize(2 * kProfPairs, nullptr);
+    for (auto& ev : op.prof_pool) ADR_CUDA(cudaEventCreate(&ev));
+  }
+  if (kernel_class != op.prof_class && op.cycle_exec) {  // the event nodes live in the captured cycle
+    cudaGraphExecDestroy(op.cycle_exec);
+    op.cycle_exec = nullptr;
+    op.prof_graph_pairs = 0;
+  }
+  op.prof_class = kernel_class;
+  op.prof_stream_pairs = 0;
+  op.prof_graph_fresh = false;
+  op.prof_count = 0;
+  op.prof_ms = 0.0;
+  return ADR_OK;
+}
+
+int adr_profile_read(adr_op_t h, long long* launches, double* total_ms) {
+  if (!h || !launches || !total_ms) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  ADR_CUDA(cudaStreamSynchronize(op.st));
+  prof_collect(op);
+  *launches = op.prof_count;
+  *total_ms = op.prof_ms;
+  return ADR_OK;
+}
+
 int adr_operator_destroy(adr_op_t h) {
   if (!h) return ADR_OK;
   Op& op = h->op;
   cudaStreamSynchronize(op.st);
   if (op.cycle_exec) cudaGraphExecDestroy(op.cycle_exec);
   if (op.cap) cudaStreamDestroy(op.cap);
+  for (cudaEvent_t ev : op.prof_pool) cudaEventDestroy(ev);
   cudaError_t e1 = cudaFree(op.arena);
   cudaError_t e2 = cudaFreeHost(op.host_scal);
   delete h;
@@ -761,7 +854,11 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
       double2* zj = op.Z + (int64_t)j * N;
       double2* w = op.V + (int64_t)(j + 1) * N;  // A z_j, orthogonalised and normalised in place
       ADR_TRY(precondition(op, vj, zj));
-      launch_rows_apply(op.g0, op.rows2up, zj, w, st);
+      {
+        const int pk = prof_begin(op, ADR_PROF_OUTER_APPLY, st);
+        launch_rows_apply(op.g0, op.rows2up, zj, w, st);
+        prof_end(op, pk, st);
+      }
       launch_cgs2<double>(op.V, N, j + 1, w, N, op.ks, op.ost, j, st);
       launch_scale_inv_norm<double>(w, w, op.ks.nrm2, N, st);
       ADR_TRY(check_launch("adr_solve iteration"));
