@@ -209,6 +209,34 @@ int adr_solve_host(int dim, const int* n, const double* h, const int* src, doubl
 int adr_traveltime(int dim, const int* n, const double* h, const int* src, const double* kappa, double* tau1,
                    int max_sweeps, void* stream, int* sweeps_done);
 
+/* adr_traveltime without any allocation.  The paper has no counterpart: this
+ * is a deployment variant of the same computation, with the same arguments,
+ * result and error codes as adr_traveltime.
+ *
+ * It is for callers that must not allocate during the call: a process whose
+ * device memory is held by a caching allocator (where cudaMalloc can fail
+ * although the caller's pool has room), or one that keeps other streams busy
+ * (cudaFree waits for the whole device; pinning host memory is slow).  No
+ * cudaMalloc, cudaFree, cudaMallocHost or allocating library routine runs in
+ * this call.  The per-sweep convergence flags live in a fixed device array of
+ * ADR_TRAVELTIME_STATIC_MAX_SWEEPS ints (32 KiB) inside the library; the call
+ * zeroes the first max_sweeps of them on `stream` before its first sweep, so
+ * nothing needs to be zero beforehand.  The host reads the flags into stack
+ * memory every 16 sweeps (a synchronisation of `stream`), so the call can not
+ * be captured into a CUDA graph.
+ *
+ * - max_sweeps above ADR_TRAVELTIME_STATIC_MAX_SWEEPS is rejected with
+ *   ADR_ERR_ARG before any device work.
+ * - The first call on a device looks up the array's device address on the
+ *   current device (which may load the library's module there); it must not
+ *   run while any stream of the process is being captured.
+ * - The array is shared by every call on a device: calls that overlap in time
+ *   on one device (from other threads or streams) race on it and must be
+ *   serialised by the caller. */
+#define ADR_TRAVELTIME_STATIC_MAX_SWEEPS 8192
+int adr_traveltime_static(int dim, const int* n, const double* h, const int* src, const double* kappa, double* tau1,
+                          int max_sweeps, void* stream, int* sweeps_done);
+
 /* Kernel classes that adr_profile_kernel can time. */
 #define ADR_PROF_NONE 0
 #define ADR_PROF_LEVEL1_RELAX 1   /* minimal-residual apply on level 1 (stored stencil) */

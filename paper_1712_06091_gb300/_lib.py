@@ -24,12 +24,14 @@ SCHEMES = {"2up": 0, "1up": 1, "cen": 2, "prec": 3}
 CYCLES = {"V": 0, "K": 1}
 RELAX = {"jacobi": 0, "mr": 1}
 MAX_LEVELS = 8
+TRAVELTIME_STATIC_MAX_SWEEPS = 8192
 
 # The exported entry points, in the order include/adr.h declares them.
 EXPORTS = (
     "adr_params_default", "adr_operator_create", "adr_operator_update", "adr_operator_destroy", "adr_operator_info",
     "adr_coefficients", "adr_apply", "adr_level_stencil", "adr_vcycle", "adr_point_source_rhs",
-    "adr_solve", "adr_reconstruct", "adr_solve_host", "adr_traveltime", "adr_profile_kernel", "adr_profile_read",
+    "adr_solve", "adr_reconstruct", "adr_solve_host", "adr_traveltime", "adr_traveltime_static", "adr_profile_kernel",
+    "adr_profile_read",
     "adr_kernel_launches", "adr_last_error", "adr_version",
 )
 PROFILE_CLASSES = {"none": 0, "level1_relax": 1, "fine_relax": 2, "outer_apply": 3, "coarsest": 4}
@@ -101,6 +103,7 @@ def load():
         "adr_solve_host": [i, ip, dp, ip, d, vp, vp, vp, ctypes.POINTER(Params), d, i, vp, vp, vp,
                            ctypes.POINTER(SolveInfo)],
         "adr_traveltime": [i, ip, dp, ip, vp, vp, i, vp, ip],
+        "adr_traveltime_static": [i, ip, dp, ip, vp, vp, i, vp, ip],
         "adr_profile_kernel": [vp, i],
         "adr_profile_read": [vp, ctypes.POINTER(ctypes.c_longlong), dp],
     }

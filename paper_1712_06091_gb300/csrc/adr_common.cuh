@@ -259,6 +259,9 @@ constexpr int kMaxMrBlocks = 2432;
 // Counts kernel launches issued by the library (all threads).
 void count_launches(int n);
 
+// Records msg as the calling thread's adr_last_error text; returns code.
+int set_last_error(int code, const char* msg);
+
 // Vector kernels.
 template <typename T> void launch_cmul_vec(const C<T>* a, const C<T>* b, C<T>* out, int64_t n, cudaStream_t st);  // out = a .* b
 template <typename Ts, typename Td> void launch_ccast(const C<Ts>* src, C<Td>* dst, int64_t n, cudaStream_t st);

@@ -33,6 +33,7 @@ static int fail(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
 }
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
 
 #define ADR_CUDA(call)                                                                            \
   do {                                                                                            \

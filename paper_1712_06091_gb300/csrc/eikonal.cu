@@ -151,3 +151,98 @@ extern "C" int adr_traveltime(int dim, const int* n, const double* h, const int*
   if (rc == ADR_OK && done >= max_sweeps) rc = ADR_ERR_NOT_CONVERGED;
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// adr_traveltime_static: the same relaxation without any allocation.
+//
+// Callers that cannot allocate: a process whose device memory is held by a
+// caching allocator (a cudaMalloc can then fail although the caller's pool has
+// room), and callers keeping other streams busy, because cudaFree waits for
+// the whole device and cudaMallocHost pins pages at a cost comparable to the
+// solve of a small grid.  Here the convergence flags live in a fixed device
+// array, one int per sweep: sweep k of a call sets flag k when it lowers any
+// node.  The call zeroes the flags it will use before the first sweep, so
+// the array may hold anything from an earlier call.  Every call on a device
+// uses the same array: calls that overlap in time on one device (other
+// threads, other streams) race on it and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace adr {
+
+constexpr int kStaticMaxSweeps = 8192;   // 32 KiB of flags; ADR_TRAVELTIME_STATIC_MAX_SWEEPS
+static __device__ __align__(256) int g_sweep_flags[kStaticMaxSweeps];
+
+constexpr int kStaticMaxDevices = 64;
+static std::mutex g_sweep_flags_mu;
+static int* g_sweep_flags_ptr[kStaticMaxDevices] = {};
+
+// Device address of g_sweep_flags on the current device, looked up once per
+// device (the lookup may load the module on that device, so the first call
+// on a device must not happen inside a stream capture).
+static int sweep_flags_on_current_device(int** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_last_error(ADR_ERR_CUDA, (std::string("cudaGetDevice: ") + cudaGetErrorString(e)).c_str());
+  if (dev < 0 || dev >= kStaticMaxDevices) return set_last_error(ADR_ERR_ARG, "device index above 63");
+  std::lock_guard<std::mutex> lock(g_sweep_flags_mu);
+  if (!g_sweep_flags_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_sweep_flags);
+    if (e != cudaSuccess || !p)
+      return set_last_error(ADR_ERR_CUDA, (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
+    g_sweep_flags_ptr[dev] = static_cast<int*>(p);
+  }
+  *out = g_sweep_flags_ptr[dev];
+  return ADR_OK;
+}
+
+}  // namespace adr
+
+extern "C" int adr_traveltime_static(int dim, const int* n, const double* h, const int* src, const double* kappa,
+                                     double* tau1, int max_sweeps, void* stream, int* sweeps_done) {
+  if ((dim != 2 && dim != 3) || !n || !h || !src || !kappa || !tau1 || max_sweeps < 1)
+    return set_last_error(ADR_ERR_ARG, "invalid argument");
+  if (max_sweeps > kStaticMaxSweeps)
+    return set_last_error(ADR_ERR_ARG, "max_sweeps exceeds the static flag array (8192 sweeps)");
+  for (int d = 0; d < dim; ++d)
+    if (n[d] < 2 || !(h[d] > 0.0) || src[d] < 0 || src[d] >= n[d]) return set_last_error(ADR_ERR_ARG, "invalid grid or source");
+  int* flags = nullptr;
+  const int rc0 = sweep_flags_on_current_device(&flags);
+  if (rc0 != ADR_OK) return rc0;
+  cudaStream_t st = (cudaStream_t)stream;
+  Dims g = make_dims(dim, n);
+  EikParams P{};
+  for (int d = 0; d < 3; ++d) {
+    P.src[d] = d < dim ? src[d] : 0;
+    P.h[d] = d < dim ? h[d] : 1.0;
+  }
+  P.js = P.src[0] + g.s1 * P.src[1] + g.s2 * P.src[2];
+  if (cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)max_sweeps, st) != cudaSuccess)
+    return set_last_error(ADR_ERR_CUDA, "cudaMemsetAsync of the sweep flags failed");
+  count_launches(1), k_eik_init<<<blocks_for(g.N, 256), 256, 0, st>>>(tau1, g.N, P.js, kappa);
+  constexpr int check_every = 16;
+  int host_flags[check_every];   // pageable stack memory: no pinned allocation
+  int done = 0;
+  while (done < max_sweeps) {
+    const int first = done;
+    for (int k = 0; k < check_every && done < max_sweeps; ++k, ++done) {
+      if (dim == 2) count_launches(1), k_eik_sweep<2><<<blocks_for(g.N, 256), 256, 0, st>>>(g, P, kappa, tau1, flags + done);
+      else count_launches(1), k_eik_sweep<3><<<blocks_for(g.N, 256), 256, 0, st>>>(g, P, kappa, tau1, flags + done);
+    }
+    const int batch = done - first;
+    if (cudaMemcpyAsync(host_flags, flags + first, sizeof(int) * (size_t)batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      if (sweeps_done) *sweeps_done = done;
+      return set_last_error(ADR_ERR_CUDA, "reading the sweep flags failed");
+    }
+    int any = 0;
+    for (int k = 0; k < batch; ++k) any |= host_flags[k];
+    if (!any) break;
+  }
+  if (sweeps_done) *sweeps_done = done;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_last_error(ADR_ERR_CUDA, cudaGetErrorString(e));
+  if (done >= max_sweeps) return set_last_error(ADR_ERR_NOT_CONVERGED, "max_sweeps reached while tau1 still changed");
+  return ADR_OK;
+}
