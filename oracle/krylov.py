@@ -13,6 +13,10 @@ residual.  Readings (also in the design notes):
       or the iteration budget is spent.
   K3  A cycle ends after `restart` iterations, on convergence of the
       estimate, on an exact breakdown, or when the budget is spent.
+  K4  With reorth_eta < 1 the second Gram-Schmidt pass of K1 runs only when
+      the first pass cancelled |w| below reorth_eta |w| (the test of Daniel,
+      Gragg, Kaufman and Stewart, 1976, compared on squared norms); a single
+      classical pass otherwise.  reorth_eta >= 1 (or None) is K1 unchanged.
 """
 from __future__ import annotations
 
@@ -21,10 +25,24 @@ import numpy as np
 from .multigrid import back_substitution, cgs2, givens
 
 
-def fgmres(A, b, precond, x0=None, tol=1e-8, restart=20, maxit=500):
+def cgs_selective(V, w, eta):
+    """Classical Gram-Schmidt against the columns of V, repeated only when the
+    first pass leaves less than eta |w| (reading K4).  Returns (h, w)."""
+    s2 = np.vdot(w, w).real
+    h = V.conj().T @ w
+    w = w - V @ h
+    if np.vdot(w, w).real >= eta * eta * s2:
+        return h, w
+    h2 = V.conj().T @ w
+    w = w - V @ h2
+    return h + h2, w
+
+
+def fgmres(A, b, precond, x0=None, tol=1e-8, restart=20, maxit=500, reorth_eta=None):
     """Solve A x = b.  Returns (x, iterations, final relative residual, history).
 
     `history` holds the estimate |g_{j+1}|/|b| after every iteration.
+    reorth_eta: None or >= 1 for CGS2 (K1), else the selective test of K4.
     """
     n = b.shape[0]
     x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
@@ -48,7 +66,10 @@ def fgmres(A, b, precond, x0=None, tol=1e-8, restart=20, maxit=500):
         for j in range(restart):
             Z[:, j] = precond(V[:, j])
             w = A @ Z[:, j]
-            hcol, w = cgs2(V[:, : j + 1], w)
+            if reorth_eta is None or reorth_eta >= 1.0:
+                hcol, w = cgs2(V[:, : j + 1], w)
+            else:
+                hcol, w = cgs_selective(V[:, : j + 1], w, reorth_eta)
             H[: j + 1, j] = hcol
             H[j + 1, j] = np.linalg.norm(w)
             for i in range(j):

@@ -112,6 +112,46 @@ def test_fgmres_matches_direct_solve_and_is_monotone():
     assert abs(np.linalg.norm(q - A @ x) / np.linalg.norm(q) - rel) < 1e-14
 
 
+def test_selective_gram_schmidt_reorthogonalises_only_on_cancellation():
+    rng = np.random.default_rng(5)
+    n, k = 400, 12
+    V, _ = np.linalg.qr(rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k)))
+    # mild cancellation: one pass, exact decomposition w = V h + w'
+    w = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    h, w1 = krylov.cgs_selective(V, w, 0.1)
+    assert np.linalg.norm(w - (V @ h + w1)) <= 1e-14 * np.linalg.norm(w)
+    h_one = V.conj().T @ w
+    assert np.array_equal(h, h_one)                      # no second pass taken
+    assert np.linalg.norm(V.conj().T @ w1) <= 1e-14 * np.linalg.norm(w1)
+    # severe cancellation (|w'| = 1e-8 |w|): one pass leaves V-components of
+    # relative size ~eps/1e-8; the test triggers the second pass, which removes them
+    c = rng.standard_normal(k) + 1j * rng.standard_normal(k)
+    u = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    u -= V @ (V.conj().T @ u)
+    w = V @ c + 1e-8 * np.linalg.norm(c) * u / np.linalg.norm(u)
+    _, w_single = krylov.cgs_selective(V, w, 0.0)
+    h, w_sel = krylov.cgs_selective(V, w, 0.1)
+    loss = lambda x: np.linalg.norm(V.conj().T @ x) / np.linalg.norm(x)
+    assert loss(w_single) > 1e-12
+    assert loss(w_sel) < 1e-14
+    assert np.linalg.norm(h - c) <= 1e-12 * np.linalg.norm(c)
+
+
+def test_fgmres_selective_reorthogonalisation_matches_cgs2():
+    P = W.constant_medium((33, 33))
+    g = adr.Grid(P.n, P.h)
+    A = adr.assemble_adr(g, P.src, P.omega, P.kappa, P.gamma, P.tau1, "2up")
+    Ap = adr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, P.tau1)
+    hier = mg.build_hierarchy(Ap, P.n, 3)
+    q = adr.point_source_rhs(g, P.src)
+    prm = mg.CycleParams()
+    pc = lambda v: mg.cycle(hier, v, prm)
+    x2, its2, rel2, _ = krylov.fgmres(A, q, pc, tol=1e-12, restart=8, maxit=200)
+    xs, itss, rels, _ = krylov.fgmres(A, q, pc, tol=1e-12, restart=8, maxit=200, reorth_eta=0.1)
+    assert rels <= 1e-12 and abs(itss - its2) <= 1
+    assert np.linalg.norm(xs - x2) <= 1e-10 * np.linalg.norm(x2)
+
+
 def test_kcycle_fgmres_inner_is_fixed_count():
     g, P, A, b = _small_system(n=(17, 17))
     Ap = adr.assemble_preconditioner(adr.Grid(P.n, P.h), P.src, P.omega, P.kappa, P.gamma, P.tau1)
