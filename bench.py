@@ -224,7 +224,8 @@ def oracle_sample(pd, tol):
                           weights=pd["jacobi_weight"], coarse_iterations=pd["coarse_iterations"],
                           kcycle_iterations=pd["kcycle_iterations"])
     q = oadr.point_source_rhs(g, P.src)
-    a, its, res, _ = krylov.fgmres(A, q, lambda v: omg.cycle(hier, v, prm), tol=tol, restart=pd["restart"], maxit=400)
+    a, its, res, _ = krylov.fgmres(A, q, lambda v: omg.cycle(hier, v, prm), tol=tol, restart=pd["restart"], maxit=400,
+                                   reorth_eta=pd["reorth_eta"])
     oadr.reconstruct(g, P.src, P.omega, tau1, a)
     return time.perf_counter() - t0, g.N, its
 

@@ -88,6 +88,10 @@ typedef struct adr_params {
   int near_source;                     /* rows within this Chebyshev distance of the
                                           source use central advection (Sec. 2.2 says
                                           "distance of one node"; 1..4, default 1) */
+  double reorth_eta;                   /* outer Gram-Schmidt: the second classical pass
+                                          runs only when the first left less than
+                                          reorth_eta |w| (Daniel-Gragg-Kaufman-Stewart
+                                          test); >= 1: always (CGS2).  Default 0.1 */
 } adr_params_t;
 
 typedef struct adr_level_info {

@@ -51,6 +51,7 @@ class Params(ctypes.Structure):
         ("restart", ctypes.c_int),
         ("precond_precision", ctypes.c_int),
         ("near_source", ctypes.c_int),
+        ("reorth_eta", ctypes.c_double),
     ]
 
 

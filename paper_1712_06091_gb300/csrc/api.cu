@@ -544,6 +544,7 @@ static int validate_params(const adr_params_t& p) {
   if (p.restart < 1 || p.restart > 64) return fail(ADR_ERR_ARG, "restart must be in [1, 64]");
   if (p.precond_precision != ADR_F64 && p.precond_precision != ADR_F32) return fail(ADR_ERR_ARG, "unknown precision");
   if (p.near_source < 1 || p.near_source > 4) return fail(ADR_ERR_ARG, "near_source must be in [1, 4]");
+  if (!(p.reorth_eta >= 0.0 && p.reorth_eta <= 1e6)) return fail(ADR_ERR_ARG, "reorth_eta must be in [0, 1e6]");
   for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
     if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
       return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");
@@ -582,6 +583,7 @@ int adr_params_default(adr_params_t* p) {
   p->restart = 20;
   p->precond_precision = ADR_F32;
   p->near_source = 1;
+  p->reorth_eta = 0.1;
   return ADR_OK;
 }
 
@@ -860,7 +862,7 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
         launch_rows_apply(op.g0, op.rows2up, zj, w, st);
         prof_end(op, pk, st);
       }
-      launch_cgs2<double>(op.V, N, j + 1, w, N, op.ks, op.ost, j, st);
+      launch_cgs_selective<double>(op.V, N, j + 1, w, N, op.ks, op.ost, j, op.p.reorth_eta, st);
       launch_scale_inv_norm<double>(w, w, op.ks.nrm2, N, st);
       ADR_TRY(check_launch("adr_solve iteration"));
       ADR_TRY(read_scalars(op, op.ost.scal, kNumScal));

@@ -353,15 +353,15 @@ __global__ void __launch_bounds__(256) k_cgs_pass2(const C<T>* __restrict__ V, i
   last_block_rt(k, blk, partial, ticket, hb, sh);
 }
 
-// pass 3: w -= V hb ; |w|^2 ; Arnoldi column j and Givens rotation (last block)
+// w -= V c ; |w|^2 reduced over the grid.  Returns true in the last block
+// (total in nrm2->x, valid in thread 0).
 template <typename T>
-__global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
-                                                   const double2* __restrict__ ha, const double2* __restrict__ hb,
-                                                   double2* partial, unsigned* ticket, double2* nrm2, ArnoldiState st, int j) {
+__device__ __forceinline__ bool update_norm(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+                                            const double2* c, double2* partial, unsigned* ticket, double2* nrm2) {
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[1];
   __shared__ C<T> coef[kMaxKrylov + 1];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-hb[i].x), (T)(-hb[i].y));
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-c[i].x), (T)(-c[i].y));
   __syncthreads();
   C<T> s2[1] = {czero<T>()};
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -374,7 +374,92 @@ __global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, i
   block_sum_t<T, 1>(s2, sh, o);
   if (threadIdx.x == 0) blk[0] = o[0];
   __syncthreads();
-  if (last_block_rt(1, blk, partial, ticket, nrm2, sh) && threadIdx.x == 0) {
+  return last_block_rt(1, blk, partial, ticket, nrm2, sh);
+}
+
+// pass 3: w -= V hb ; |w|^2 ; Arnoldi column j and Givens rotation (last block)
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+                                                   const double2* __restrict__ ha, const double2* __restrict__ hb,
+                                                   double2* partial, unsigned* ticket, double2* nrm2, ArnoldiState st, int j) {
+  if (update_norm<T>(V, ld, k, w, n, hb, partial, ticket, nrm2) && threadIdx.x == 0) {
+    const double s2t = nrm2->x;
+    nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
+    if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, s2t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram-Schmidt with a conditional second pass (selective re-orthogonalisation):
+//   A: ha = V^H w and |w|^2 (kept in ha[k].x)
+//   B: w -= V ha, t = |w'|^2; if t >= eta^2 |w|^2 the column is final
+//      (hb = 0, Arnoldi column), else ha[k].y = 1 requests the second pass
+//   C: (only if requested) hb = V^H w'
+//   D: (only if requested) w' -= V hb, |w''|^2, Arnoldi column from ha + hb
+// C and D exit at once when the flag is clear, so the launch sequence is
+// fixed (graph-capturable) while the second pass costs nothing when skipped.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_sgs_dots_norm(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w,
+                                                       int64_t n, double2* partial, unsigned* ticket, double2* ha) {
+  __shared__ double2 sh[32 * 5];
+  __shared__ double2 blk[kMaxKrylov + 2];
+  for (int c = 0; c < k; c += 4) {
+    C<T> acc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = czero<T>();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+      const C<T> we = w[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * ld + e], we, acc[q]);
+      if (c == 0) acc[4] = cfma_conj(we, we, acc[4]);
+    }
+    double2 o[5];
+    block_sum_t<T, 5>(acc, sh, o);
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < 4 && c + q < k; ++q) blk[c + q] = o[q];
+      if (c == 0) blk[k] = o[4];
+    }
+    __syncthreads();
+  }
+  last_block_rt(k + 1, blk, partial, ticket, ha, sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sgs_update_test(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+                                                         double2* ha, double2* hb, double2* partial, unsigned* ticket,
+                                                         double2* nrm2, ArnoldiState st, int j, double eta2) {
+  if (update_norm<T>(V, ld, k, w, n, ha, partial, ticket, nrm2) && threadIdx.x == 0) {
+    const double t = nrm2->x;
+    if (t >= eta2 * ha[k].x) {
+      ha[k].y = 0.0;
+      for (int i = 0; i < k; ++i) hb[i] = make_double2(0.0, 0.0);
+      nrm2->y = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+      if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, t);
+    } else {
+      ha[k].y = 1.0;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sgs_reorth_dots(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w,
+                                                         int64_t n, const double2* ha, double2* partial, unsigned* ticket,
+                                                         double2* hb) {
+  if (ha[k].y == 0.0) return;   // uniform over the grid
+  __shared__ double2 sh[32 * 4];
+  __shared__ double2 blk[kMaxKrylov + 1];
+  block_dots<T>(V, ld, k, w, n, blk, sh);
+  last_block_rt(k, blk, partial, ticket, hb, sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sgs_reorth_update(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+                                                           const double2* ha, const double2* hb, double2* partial,
+                                                           unsigned* ticket, double2* nrm2, ArnoldiState st, int j) {
+  if (ha[k].y == 0.0) return;   // uniform over the grid
+  if (update_norm<T>(V, ld, k, w, n, hb, partial, ticket, nrm2) && threadIdx.x == 0) {
     const double s2t = nrm2->x;
     nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
     if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, s2t);
@@ -442,6 +527,21 @@ void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const Kry
   count_launches(1), k_cgs_pass3<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.hb, s.partial, s.ticket, s.nrm2, st, j);
 }
 template <typename T>
+void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
+                          const ArnoldiState& st, int j, double eta, cudaStream_t stream) {
+  if (!(eta < 1.0)) {
+    launch_cgs2<T>(V, ld, k, w, n, s, st, j, stream);
+    return;
+  }
+  const int nb = reduction_blocks(n);
+  count_launches(1), k_sgs_dots_norm<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.partial, s.ticket, s.ha);
+  count_launches(1), k_sgs_update_test<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.hb, s.partial, s.ticket, s.nrm2,
+                                                                    st, j, eta * eta);
+  count_launches(1), k_sgs_reorth_dots<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.partial, s.ticket, s.hb);
+  count_launches(1), k_sgs_reorth_update<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.hb, s.partial, s.ticket,
+                                                                      s.nrm2, st, j);
+}
+template <typename T>
 void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream) {
   const int nb = reduction_blocks(n);
   ArnoldiState dummy{};
@@ -460,6 +560,8 @@ void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, c
 
 #define ADR_INSTANTIATE_FUSED(T)                                                                                           \
   template void launch_cgs2<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, int, cudaStream_t); \
+  template void launch_cgs_selective<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, int, \
+                                        double, cudaStream_t);                                                              \
   template void launch_norm_start<T>(const C<T>*, int64_t, const KrylovScratch&, const ArnoldiState*, cudaStream_t);        \
   template void launch_combine<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, bool, int64_t, cudaStream_t);     \
   template void launch_mr_update2<T>(C<T>*, const C<T>*, const C<T>*, C<T>*, const C<T>*, const double2*, const C<T>*, C<T>*, bool, int64_t, cudaStream_t);

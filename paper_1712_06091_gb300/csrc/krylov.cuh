@@ -39,6 +39,11 @@ struct KrylovScratch {
 template <typename T>
 void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s, const ArnoldiState& st, int j,
                  cudaStream_t stream);
+// Gram-Schmidt step j with the second pass only when the first one cancelled
+// |w| below eta |w| (four launches; eta >= 1 is launch_cgs2).
+template <typename T>
+void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
+                          const ArnoldiState& st, int j, double eta, cudaStream_t stream);
 // |b|^2 into s.nrm2; with st, also starts an Arnoldi cycle with beta = |b|.
 template <typename T>
 void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream);

@@ -145,14 +145,17 @@ def test_cycle_f32(adrlib, cuda, name):
 
 @pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17", "corner3d_9x11x13"])
 @pytest.mark.parametrize("k,m", [(7, 20), (9, 4)])
-def test_fgmres_iterates(adrlib, cuda, name, k, m):
-    """Same algorithm, fixed iteration count: iterate-for-iterate parity."""
-    P, params, op = make_operator(name, precision="f64", restart=m)
+@pytest.mark.parametrize("eta", [0.1, 2.0, 0.0])
+def test_fgmres_iterates(adrlib, cuda, name, k, m, eta):
+    """Same algorithm, fixed iteration count: iterate-for-iterate parity (selective,
+    always and never re-orthogonalised Gram-Schmidt)."""
+    P, params, op = make_operator(name, precision="f64", restart=m, reorth_eta=eta)
     A = oracle_matrix(name, "2up")
     hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
     prm = oracle_cycle_params(params)
     q = adr.point_source_rhs(adr.Grid(P.n, P.h), P.src)
-    x_ref, its, res, _ = krylov.fgmres(A, q, lambda v: mg.cycle(hier, v, prm), tol=0.0, restart=m, maxit=k)
+    x_ref, its, res, _ = krylov.fgmres(A, q, lambda v: mg.cycle(hier, v, prm), tol=0.0, restart=m, maxit=k,
+                                       reorth_eta=eta)
     a, info = op.solve(tol=0.0, maxit=k, raise_on_fail=False)
     assert info["iterations"] == its == k
     assert rel(a.cpu().numpy(), x_ref) <= 1e-10
