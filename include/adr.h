@@ -92,6 +92,10 @@ typedef struct adr_params {
                                           runs only when the first left less than
                                           reorth_eta |w| (Daniel-Gragg-Kaufman-Stewart
                                           test); >= 1: always (CGS2).  Default 0.1 */
+  int adjoint;                         /* 1: also build the conjugate-transposed
+                                          operator and its hierarchy (adr_adjoint_solve,
+                                          adr_apply_adjoint, adr_vcycle_adjoint); about
+                                          doubles the operator's memory.  Default 0 */
 } adr_params_t;
 
 typedef struct adr_level_info {
@@ -199,6 +203,51 @@ int adr_solve_host(int dim, const int* n, const double* h, const int* src, doubl
                    const double* kappa, const double* tau1, const double* gamma,
                    const adr_params_t* params, double tol, int maxit, void* stream,
                    double* u_host, double* a_host, adr_solve_info_t* info);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint state and slowness gradient.  The paper has no adjoint; this is the
+ * standard adjoint-state gradient of a receiver misfit through its operator:
+ * with u = M a, M = diag(exp(-i w tau)) (Eq. new_u), receivers R, data d and
+ * J = 1/2 |R u - d|^2, the travel time held fixed,
+ *     H_2up^H lambda = M^H R^T (R u - d),
+ *     dJ/dkappa_j = -Re( conj(lambda_j) (2 w^2 kappa_j - 2 i w gamma_j kappa_j) a_j ),
+ * because kappa enters H_2up only through its reaction diagonal
+ * w^2 kappa^2 - i w gamma kappa^2 (Eq. ADR).  The entry points below need an
+ * operator created with params.adjoint = 1 (else ADR_ERR_STATE), except
+ * adr_receivers and adr_kappa_gradient.
+ * ------------------------------------------------------------------------- */
+
+/* Solves H_2up^H lambda = rhs (device complex128[N], not aliasing lambda) by
+ * the same flexible GMRES as adr_solve, preconditioned by the cycle on the
+ * conjugate-transposed hierarchy (coarse operators P^T A^H P).  use_x0, tol,
+ * maxit, info and the error codes as in adr_solve. */
+int adr_adjoint_solve(adr_op_t op, const void* rhs, void* lambda, int use_x0, double tol, int maxit,
+                      adr_solve_info_t* info);
+
+/* y = H_2up^H x, complex128[N] (the conjugate transpose of the float64
+ * operator that adr_apply(op, ADR_SCHEME_2UP, ADR_F64, ...) applies). */
+int adr_apply_adjoint(adr_op_t op, const void* x, void* y);
+
+/* One application of the cycle on the conjugate-transposed hierarchy:
+ * z = B_H^{-1} r in the precision of the cycle (as adr_vcycle). */
+int adr_vcycle_adjoint(adr_op_t op, const void* r, void* z);
+
+/* Receiver sampling: rec (device int64[nrec]) node indices, d (device
+ * complex128[nrec]) data, u (device complex128[N]) the wavefield.  Writes, for
+ * the pointers that are not NULL: res (device complex128[nrec]) = u[rec] - d;
+ * rhs (device complex128[N]) = M^H R^T res (zero elsewhere; repeated receivers
+ * add up); *misfit (host) = 1/2 |res|^2 (synchronises the stream).  A receiver
+ * index outside [0, N) contributes nothing and, when misfit is requested,
+ * makes the call return ADR_ERR_ARG. */
+int adr_receivers(adr_op_t op, int nrec, const int64_t* rec, const void* d, const void* u, void* res, void* rhs,
+                  double* misfit);
+
+/* grad (device float64[N]) -= Re(conj(lambda) (2 w^2 kappa - 2 i w gamma kappa) a)
+ * elementwise: adds this source's term of dJ/dkappa.  kappa, gamma: device
+ * float64[N] (those the operator was last built with); a, lambda: device
+ * complex128[N] (amplitude and adjoint state). */
+int adr_kappa_gradient(adr_op_t op, const double* kappa, const double* gamma, const void* a, const void* lambda,
+                       double* grad);
 
 /* Travel-time factor for the point source at node src (input preparation,
  * not part of the solve): tau1 (device float64[N], output) with

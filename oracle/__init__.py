@@ -22,6 +22,8 @@ travel time and amplitude":
                  Jacobi-preconditioned GMRES coarsest solve (Sec. 3.1).
 * `krylov`    -- flexible GMRES with classical Gram-Schmidt applied twice.
 * `eikonal`   -- factored-eikonal fast marching (Eq. factoredEikonal).
+* `adjoint`   -- receiver misfit and its slowness gradient by the adjoint
+                 state of the assembled system (not in the paper).
 
 Every function is FP64 and single-threaded; scipy.sparse supplies the sparse
 matrix products and direct solves used as library steps.

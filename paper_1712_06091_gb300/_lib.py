@@ -30,7 +30,8 @@ TRAVELTIME_STATIC_MAX_SWEEPS = 8192
 EXPORTS = (
     "adr_params_default", "adr_operator_create", "adr_operator_update", "adr_operator_destroy", "adr_operator_info",
     "adr_coefficients", "adr_apply", "adr_level_stencil", "adr_vcycle", "adr_point_source_rhs",
-    "adr_solve", "adr_reconstruct", "adr_solve_host", "adr_traveltime", "adr_traveltime_static", "adr_profile_kernel",
+    "adr_solve", "adr_reconstruct", "adr_solve_host", "adr_adjoint_solve", "adr_apply_adjoint", "adr_vcycle_adjoint",
+    "adr_receivers", "adr_kappa_gradient", "adr_traveltime", "adr_traveltime_static", "adr_profile_kernel",
     "adr_profile_read",
     "adr_kernel_launches", "adr_last_error", "adr_version",
 )
@@ -52,6 +53,7 @@ class Params(ctypes.Structure):
         ("precond_precision", ctypes.c_int),
         ("near_source", ctypes.c_int),
         ("reorth_eta", ctypes.c_double),
+        ("adjoint", ctypes.c_int),
     ]
 
 
@@ -103,6 +105,11 @@ def load():
         "adr_reconstruct": [vp, vp, vp],
         "adr_solve_host": [i, ip, dp, ip, d, vp, vp, vp, ctypes.POINTER(Params), d, i, vp, vp, vp,
                            ctypes.POINTER(SolveInfo)],
+        "adr_adjoint_solve": [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo)],
+        "adr_apply_adjoint": [vp, vp, vp],
+        "adr_vcycle_adjoint": [vp, vp, vp],
+        "adr_receivers": [vp, i, vp, vp, vp, vp, vp, dp],
+        "adr_kappa_gradient": [vp, vp, vp, vp, vp, vp],
         "adr_traveltime": [i, ip, dp, ip, vp, vp, i, vp, ip],
         "adr_traveltime_static": [i, ip, dp, ip, vp, vp, i, vp, ip],
         "adr_profile_kernel": [vp, i],

@@ -195,6 +195,60 @@ class Operator:
         return a, {"iterations": info.iterations, "restarts": info.restarts, "rel_residual": info.rel_residual,
                    "rel_estimate": info.rel_estimate, "status": info.status}
 
+    # -- adjoint (operator created with params.adjoint = 1) ---------------
+    def apply_adjoint(self, x):
+        """adr_apply_adjoint: H_2up^H x (complex128)."""
+        x = self._vec(x.reshape(-1), torch.complex128)
+        y = torch.empty_like(x)
+        L.check(self._lib.adr_apply_adjoint(self._h, _ptr(x), _ptr(y)))
+        return y
+
+    def vcycle_adjoint(self, r):
+        """adr_vcycle_adjoint: one cycle on the conjugate-transposed hierarchy."""
+        r = self._vec(r.reshape(-1), self.cycle_dtype)
+        z = torch.empty_like(r)
+        L.check(self._lib.adr_vcycle_adjoint(self._h, _ptr(r), _ptr(z)))
+        return z
+
+    def adjoint_solve(self, rhs, x0=None, tol=1e-8, maxit=500, out=None, raise_on_fail=True):
+        """adr_adjoint_solve: (lambda, info) with H_2up^H lambda = rhs."""
+        lam = out if out is not None else torch.empty(self.N, dtype=torch.complex128, device=self.device)
+        self._vec(lam, torch.complex128)
+        if x0 is not None:
+            lam.copy_(x0.reshape(-1))
+        rhs = self._vec(rhs.reshape(-1), torch.complex128)
+        info = L.SolveInfo()
+        rc = self._lib.adr_adjoint_solve(self._h, _ptr(rhs), _ptr(lam), 1 if x0 is not None else 0, float(tol),
+                                         int(maxit), ctypes.byref(info))
+        L.check(rc, () if raise_on_fail else (L.ADR_ERR_NOT_CONVERGED,))
+        return lam, {"iterations": info.iterations, "restarts": info.restarts, "rel_residual": info.rel_residual,
+                     "rel_estimate": info.rel_estimate, "status": info.status}
+
+    def receivers(self, rec, d, u):
+        """adr_receivers: (misfit 1/2 |u[rec] - d|^2, residuals, adjoint source M^H R^T res)."""
+        rec = torch.as_tensor(rec, dtype=torch.int64, device=self.device).reshape(-1).contiguous()
+        d = torch.as_tensor(d, dtype=torch.complex128, device=self.device).reshape(-1).contiguous()
+        if d.numel() != rec.numel():
+            raise ValueError("one datum per receiver")
+        u = self._vec(u.reshape(-1), torch.complex128)
+        res = torch.empty(rec.numel(), dtype=torch.complex128, device=self.device)
+        rhs = torch.empty(self.N, dtype=torch.complex128, device=self.device)
+        J = ctypes.c_double(0.0)
+        L.check(self._lib.adr_receivers(self._h, int(rec.numel()), _ptr(rec), _ptr(d), _ptr(u), _ptr(res), _ptr(rhs),
+                                        ctypes.byref(J)))
+        return J.value, res, rhs
+
+    def kappa_gradient(self, kappa, gamma, a, lam, grad):
+        """adr_kappa_gradient: grad -= Re(conj(lam) dH/dkappa a) in place (float64, N)."""
+        k = _dev_real(kappa, self.N, self.device)
+        g = _dev_real(gamma, self.N, self.device)
+        a = self._vec(a.reshape(-1), torch.complex128)
+        lam = self._vec(lam.reshape(-1), torch.complex128)
+        if grad.dtype != torch.float64 or grad.numel() != self.N or not grad.is_contiguous() or grad.device != self.device:
+            raise ValueError("grad must be a contiguous float64 tensor of N entries on the operator's device")
+        L.check(self._lib.adr_kappa_gradient(self._h, _ptr(k), _ptr(g), _ptr(a), _ptr(lam), _ptr(grad)))
+        return grad
+
     def reconstruct(self, a):
         a = self._vec(a.reshape(-1), torch.complex128)
         u = torch.empty_like(a)
@@ -255,3 +309,61 @@ def solve_host(n, h, src, omega, kappa, tau1, gamma, params=None, tol=1e-8, maxi
     res = {"iterations": info.iterations, "restarts": info.restarts, "rel_residual": info.rel_residual,
            "status": info.status}
     return (u, a, res) if want_amplitude else (u, res)
+
+
+def misfit_gradient(n, h, omega, kappa, gamma, sources, tau1s, receivers, data, params=None, tol=1e-10, maxit=500,
+                    device="cuda"):
+    """Receiver misfit J(kappa) = sum_s 1/2 |R u_s - d_s|^2 and dJ/dkappa (tau1 held fixed).
+
+    Per source: adr_operator_update, adr_solve, adr_reconstruct, adr_receivers,
+    adr_adjoint_solve, adr_kappa_gradient; one operator (params.adjoint = 1) is
+    reused over the sources.  Returns (J, grad) with grad a float64 tensor.
+    """
+    device = torch.device(device)
+    if device.type == "cuda" and device.index is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    p = params if params is not None else default_params()
+    p.adjoint = 1
+    N = int(np.prod(n))
+    k = _dev_real(kappa, N, device)
+    g = _dev_real(gamma, N, device)
+    grad = torch.zeros(N, dtype=torch.float64, device=device)
+    a = torch.empty(N, dtype=torch.complex128, device=device)
+    lam = torch.empty(N, dtype=torch.complex128, device=device)
+    J = 0.0
+    op = None
+    try:
+        for src, t1, d in zip(sources, tau1s, data):
+            if op is None:
+                op = Operator(n, h, src, omega, k, t1, g, params=p, device=device)
+            else:
+                op.update(src, omega, k, t1, g)
+            op.solve(tol=tol, maxit=maxit, out=a)
+            u = op.reconstruct(a)
+            Js, _, rhs = op.receivers(receivers, d, u)
+            op.adjoint_solve(rhs, tol=tol, maxit=maxit, out=lam)
+            op.kappa_gradient(k, g, a, lam, grad)
+            J += Js
+    finally:
+        if op is not None:
+            op.close()
+    return J, grad
+
+
+class KappaMisfit(torch.autograd.Function):
+    """J(kappa) as a differentiable scalar: forward runs the solves and the
+    adjoint solves of misfit_gradient, backward scales the stored gradient.
+
+        J = KappaMisfit.apply(kappa, problem)   # problem: dict of the other arguments
+    """
+
+    @staticmethod
+    def forward(ctx, kappa, problem):
+        J, grad = misfit_gradient(kappa=kappa.detach(), device=kappa.device, **problem)
+        ctx.save_for_backward(grad.to(kappa.dtype))
+        return torch.tensor(J, dtype=kappa.dtype, device=kappa.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (grad,) = ctx.saved_tensors
+        return gJ * grad, None

@@ -181,6 +181,8 @@ template <typename T> struct FineOp {
   T w2, w1;          // weights of the second- and first-order upwind differences
   int central;       // 1: central ADR scheme (upwind only on boundary nodes)
   int near;          // Chebyshev radius around the source with central advection
+  const C<T>* rows;  // if set: stored cross rows (entry q of node j at q * N + j) used
+                     // instead of building the row (the conjugate-transposed operator)
 };
 
 // Scheme -> upwind weights.
@@ -227,6 +229,9 @@ template <typename T> void launch_fine_residual_dinv(const Dims& g, const FineOp
 // Stored float64 cross rows (point-major, (1 + 4 dim) x N) of a fine operator,
 // and the plain stencil apply / residual with them.
 void launch_fine_store_rows(const Dims& g, const FineOp<double>& f, double2* rows, cudaStream_t st);
+void launch_fine_store_rows(const Dims& g, const FineOp<float>& f, float2* rows, cudaStream_t st);
+// rowsT = conjugate transpose of the stored cross rows (same layout).
+template <typename T> void launch_rows_adjoint(const Dims& g, const C<T>* rows, C<T>* rowsT, cudaStream_t st);
 void launch_rows_apply(const Dims& g, const double2* rows, const double2* x, double2* y, cudaStream_t st);
 void launch_rows_residual(const Dims& g, const double2* rows, const double2* b, const double2* x, double2* r, cudaStream_t st);
 // Writes the per-source values read by the fine kernels.
@@ -267,6 +272,12 @@ template <typename T> void launch_cmul_vec(const C<T>* a, const C<T>* b, C<T>* o
 template <typename Ts, typename Td> void launch_ccast(const C<Ts>* src, C<Td>* dst, int64_t n, cudaStream_t st);
 
 void launch_rhs_point(double2* q, int64_t N, int64_t src_index, double value, cudaStream_t st);
+// Receiver residuals res = R u - d, rhs += M^H R^T res, out = (sum |res|^2, bad indices).
+void launch_receivers(int64_t N, int nrec, const int64_t* rec, const double2* d, const double2* u, const double* tau,
+                      double omega, double2* res, double2* rhs, double2* out, cudaStream_t st);
+// grad -= Re(conj(lambda) (2 w^2 kappa - 2 i w gamma kappa) a), elementwise.
+void launch_kappa_gradient(int64_t N, double omega, const double* kappa, const double* gamma, const double2* a,
+                           const double2* lambda, double* grad, cudaStream_t st);
 void launch_reconstruct(const double2* a, const double* tau, double omega, double2* u, int64_t N, cudaStream_t st);
 void launch_pack_coefficients(const Dims& g, const double* const gd[3], const double* const td[3], const double2* rho,
                               const double* tau, double* out, cudaStream_t st);

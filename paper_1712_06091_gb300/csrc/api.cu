@@ -141,6 +141,16 @@ struct Op {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t cycle_exec = nullptr;
   long long cycle_kernels = 0;
+  // conjugate-transposed operator (params.adjoint): H_2up^H rows for the outer
+  // iteration and a hierarchy on A^H sharing the forward one's work vectors
+  double2* rows2upT = nullptr;
+  void* rows0 = nullptr;            // stored rows of the cycle's fine operator (setup scratch)
+  void* rows0T = nullptr;           // their conjugate transpose
+  Hier<double> a64;
+  Hier<float> a32;
+  cudaGraphExec_t cycle_exec_adj = nullptr;
+  long long cycle_kernels_adj = 0;
+  bool prof_off = false;            // the adjoint cycle is never timed
   bool use_graph = true;
   int cluster_size = 0;             // CTAs of the coarsest-grid cluster solver (0: not available)
   // instrumentation (adr_profile_kernel): event pairs 2k, 2k+1 of prof_pool
@@ -161,7 +171,7 @@ constexpr int kProfPairs = 256;
 
 // Starts timing one launch of class cls on stream s; returns the pair index or -1.
 static int prof_begin(Op& op, int cls, cudaStream_t s) {
-  if (op.prof_class != cls || op.prof_pool.empty()) return -1;
+  if (op.prof_class != cls || op.prof_pool.empty() || op.prof_off) return -1;
   int k;
   if (op.capturing) {
     if (op.prof_graph_pairs >= kProfPairs / 2) return -1;
@@ -238,6 +248,19 @@ template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
   }
 }
 
+// The adjoint hierarchy: its own operators (stencils and inverse diagonals)
+// on the forward hierarchy's grids and work vectors.
+template <typename T> static void plan_adjoint(const Hier<T>& H, Hier<T>& HT, Arena& a, int dim) {
+  const int S = dim == 2 ? kPattern2 : kPattern3;
+  HT.L = H.L;
+  for (int l = 0; l < H.L; ++l) {
+    HT.lv[l] = H.lv[l];
+    const size_t N = (size_t)H.lv[l].g.N;
+    HT.lv[l].A = l > 0 ? a.take<C<T>>((size_t)stencil_entries((int64_t)N, S)) : nullptr;
+    HT.lv[l].dinv = a.take<C<T>>(N);
+  }
+}
+
 static void plan(Op& op, Arena& a) {
   const size_t N = (size_t)op.g0.N;
   for (int d = 0; d < op.dim; ++d) {
@@ -268,6 +291,15 @@ static void plan(Op& op, Arena& a) {
   op.ks.nrm2 = a.take<double2>(1);
   op.ks.alpha = a.take<double2>(1);
   op.dyn = a.take<FineDyn>(1);
+  if (op.p.adjoint) {
+    const size_t cross = (size_t)(1 + 4 * op.dim) * N;
+    const size_t cbytes = op.p.precond_precision == ADR_F64 ? sizeof(double2) : sizeof(float2);
+    op.rows2upT = a.take<double2>(cross);
+    op.rows0 = a.take<char>(cross * cbytes);
+    op.rows0T = a.take<char>(cross * cbytes);
+    if (op.p.precond_precision == ADR_F64) plan_adjoint(op.h64, op.a64, a, op.dim);
+    else plan_adjoint(op.h32, op.a32, a, op.dim);
+  }
 }
 
 template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool f32) {
@@ -449,6 +481,22 @@ template <typename T> static int build_hierarchy(Op& op, Hier<T>& H) {
   return check_launch("hierarchy setup");
 }
 
+// Hierarchy on A^H: the cycle's fine operator stored as rows, conjugate-
+// transposed, and the Galerkin products P^T A^H P of its levels (the same
+// kernels as the forward hierarchy, reading the stored rows).
+template <typename T> static int build_adjoint(Op& op, Hier<T>& H, Hier<T>& HT) {
+  launch_fine_store_rows(H.lv[0].g, H.prec, (C<T>*)op.rows0, op.st);
+  launch_rows_adjoint<T>(H.lv[0].g, (const C<T>*)op.rows0, (C<T>*)op.rows0T, op.st);
+  HT.prec = H.prec;
+  HT.prec.rows = (const C<T>*)op.rows0T;
+  launch_fine_dinv<T>(HT.lv[0].g, HT.prec, nullptr, HT.lv[0].dinv, op.st);
+  for (int l = 1; l < HT.L; ++l) {
+    if (l == 1) launch_galerkin_fine<T>(HT.lv[0].g, HT.lv[1].g, HT.prec, HT.lv[1].A, HT.lv[1].dinv, op.st);
+    else launch_galerkin_stored<T>(HT.lv[l - 1].g, HT.lv[l].g, HT.lv[l - 1].A, HT.lv[l].A, HT.lv[l].dinv, op.st);
+  }
+  return check_launch("adjoint hierarchy setup");
+}
+
 // Coefficients, their float32 copies and the Galerkin hierarchy for the
 // current source / frequency, written into the operator's arena (no sync).
 static int setup(Op& op, const double* kappa, const double* tau1, const double* gamma) {
@@ -471,58 +519,68 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
   launch_to_f32((const double*)op.srow, op.srowf, 2 * kCross3, op.st);
   launch_fine_store_rows(op.g0, make_fine<double>(op, ADR_SCHEME_2UP, false), op.rows2up, op.st);
   ADR_TRY(check_launch("coefficients"));
-  return op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32);
+  ADR_TRY(op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32));
+  if (!op.p.adjoint) return ADR_OK;
+  launch_rows_adjoint<double>(op.g0, op.rows2up, op.rows2upT, op.st);
+  return op.p.precond_precision == ADR_F64 ? build_adjoint(op, op.h64, op.a64) : build_adjoint(op, op.h32, op.a32);
 }
 
 // Runs the cycle of level 0 from H.lv[0].b into H.lv[0].x: captured into a
 // CUDA graph on first use (every pointer and parameter it touches is fixed
 // for the operator's lifetime, per-source values live in device memory) and
 // replayed on the operator's stream.
-template <typename T> static int run_cycle(Op& op, Hier<T>& H) {
+template <typename T> static int run_cycle(Op& op, Hier<T>& H, bool adj = false) {
   Level<T>& L0 = H.lv[0];
+  op.prof_off = adj;
   if (!op.use_graph) {
     Cycle<T> c{op, H, op.st};
     c.cycle(0, L0.b, L0.x);
+    op.prof_off = false;
     return check_launch("cycle");
   }
-  if (!op.cycle_exec) {
+  cudaGraphExec_t& exec = adj ? op.cycle_exec_adj : op.cycle_exec;
+  long long& kernels = adj ? op.cycle_kernels_adj : op.cycle_kernels;
+  if (!exec) {
     const long long before = g_launches.load(std::memory_order_relaxed);
     ADR_CUDA(cudaStreamBeginCapture(op.cap, cudaStreamCaptureModeThreadLocal));
-    op.prof_graph_pairs = 0;
+    if (!adj) op.prof_graph_pairs = 0;
     op.capturing = true;
     Cycle<T> c{op, H, op.cap};
     c.cycle(0, L0.b, L0.x);
     op.capturing = false;
+    op.prof_off = false;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(op.cap, &graph);
     if (e != cudaSuccess) return fail(ADR_ERR_CUDA, std::string("cycle capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&op.cycle_exec, graph, 0);
+    e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      op.cycle_exec = nullptr;
+      exec = nullptr;
       return fail(ADR_ERR_CUDA, std::string("cycle graph instantiation: ") + cudaGetErrorString(e));
     }
-    op.cycle_kernels = g_launches.load(std::memory_order_relaxed) - before;
-    count_launches((int)-op.cycle_kernels);  // capture launched nothing; replays are counted below
+    kernels = g_launches.load(std::memory_order_relaxed) - before;
+    count_launches((int)-kernels);  // capture launched nothing; replays are counted below
   }
-  ADR_CUDA(cudaGraphLaunch(op.cycle_exec, op.st));
-  count_launches((int)op.cycle_kernels);
-  op.prof_graph_fresh = true;
+  op.prof_off = false;
+  ADR_CUDA(cudaGraphLaunch(exec, op.st));
+  count_launches((int)kernels);
+  if (!adj) op.prof_graph_fresh = true;
   return ADR_OK;
 }
 
-// One preconditioner application on float64 vectors (casting for a float32 cycle).
-static int precondition(Op& op, const double2* v, double2* z) {
+// One preconditioner application on float64 vectors (casting for a float32
+// cycle); adj selects the cycle on A^H.
+static int precondition(Op& op, const double2* v, double2* z, bool adj = false) {
   if (op.p.precond_precision == ADR_F64) {
-    Level<double>& L0 = op.h64.lv[0];
-    launch_copy<double>(v, L0.b, op.g0.N, op.st);
-    ADR_TRY(run_cycle(op, op.h64));
-    launch_copy<double>(L0.x, z, op.g0.N, op.st);
+    Hier<double>& H = adj ? op.a64 : op.h64;
+    launch_copy<double>(v, H.lv[0].b, op.g0.N, op.st);
+    ADR_TRY(run_cycle(op, H, adj));
+    launch_copy<double>(H.lv[0].x, z, op.g0.N, op.st);
   } else {
-    Level<float>& L0 = op.h32.lv[0];
-    launch_ccast<double, float>(v, L0.b, op.g0.N, op.st);
-    ADR_TRY(run_cycle(op, op.h32));
-    launch_ccast<float, double>(L0.x, z, op.g0.N, op.st);
+    Hier<float>& H = adj ? op.a32 : op.h32;
+    launch_ccast<double, float>(v, H.lv[0].b, op.g0.N, op.st);
+    ADR_TRY(run_cycle(op, H, adj));
+    launch_ccast<float, double>(H.lv[0].x, z, op.g0.N, op.st);
   }
   return ADR_OK;
 }
@@ -545,6 +603,7 @@ static int validate_params(const adr_params_t& p) {
   if (p.precond_precision != ADR_F64 && p.precond_precision != ADR_F32) return fail(ADR_ERR_ARG, "unknown precision");
   if (p.near_source < 1 || p.near_source > 4) return fail(ADR_ERR_ARG, "near_source must be in [1, 4]");
   if (!(p.reorth_eta >= 0.0 && p.reorth_eta <= 1e6)) return fail(ADR_ERR_ARG, "reorth_eta must be in [0, 1e6]");
+  if (p.adjoint != 0 && p.adjoint != 1) return fail(ADR_ERR_ARG, "adjoint must be 0 or 1");
   for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
     if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
       return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");
@@ -714,6 +773,7 @@ int adr_operator_destroy(adr_op_t h) {
   Op& op = h->op;
   cudaStreamSynchronize(op.st);
   if (op.cycle_exec) cudaGraphExecDestroy(op.cycle_exec);
+  if (op.cycle_exec_adj) cudaGraphExecDestroy(op.cycle_exec_adj);
   if (op.cap) cudaStreamDestroy(op.cap);
   for (cudaEvent_t ev : op.prof_pool) cudaEventDestroy(ev);
   cudaError_t e1 = cudaFree(op.arena);
@@ -813,19 +873,13 @@ int adr_reconstruct(adr_op_t h, const void* a, void* u) {
   return check_launch("adr_reconstruct");
 }
 
-int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double tol, int maxit, adr_solve_info_t* info) {
-  if (!h || !a_out) return fail(ADR_ERR_ARG, "null argument");
-  if (!(tol >= 0.0) || maxit < 0) return fail(ADR_ERR_ARG, "tol must be >= 0 and maxit >= 0");
-  Op& op = h->op;
+// Flexible GMRES(m) on H_2up (adj: on H_2up^H with the cycle on A^H),
+// right-preconditioned, float64 (Sec. 3.1; readings K1-K4).
+static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, double tol, int maxit, adr_solve_info_t* info) {
   cudaStream_t st = op.st;
   const int64_t N = op.g0.N;
   const int m = op.p.restart;
-  double2* a = (double2*)a_out;
-  const double2* b = (const double2*)rhs_in;
-  if (!b) {
-    ADR_TRY(adr_point_source_rhs(h, op.b));
-    b = op.b;
-  }
+  const double2* rows = adj ? op.rows2upT : op.rows2up;
 
   launch_norm_start<double>(b, N, op.ks, nullptr, st);
   ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
@@ -837,7 +891,7 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
     return check_launch("adr_solve");
   }
   if (use_x0) {
-    launch_rows_residual(op.g0, op.rows2up, b, a, op.r, st);
+    launch_rows_residual(op.g0, rows, b, a, op.r, st);
   } else {
     launch_zero<double>(a, N, st);
     launch_copy<double>(b, op.r, N, st);
@@ -856,10 +910,10 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
       double2* vj = op.V + (int64_t)j * N;
       double2* zj = op.Z + (int64_t)j * N;
       double2* w = op.V + (int64_t)(j + 1) * N;  // A z_j, orthogonalised and normalised in place
-      ADR_TRY(precondition(op, vj, zj));
+      ADR_TRY(precondition(op, vj, zj, adj));
       {
-        const int pk = prof_begin(op, ADR_PROF_OUTER_APPLY, st);
-        launch_rows_apply(op.g0, op.rows2up, zj, w, st);
+        const int pk = adj ? -1 : prof_begin(op, ADR_PROF_OUTER_APPLY, st);
+        launch_rows_apply(op.g0, rows, zj, w, st);
         prof_end(op, pk, st);
       }
       launch_cgs_selective<double>(op.V, N, j + 1, w, N, op.ks, op.ost, j, op.p.reorth_eta, st);
@@ -877,7 +931,7 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
     if (status == ADR_ERR_NAN) break;
     launch_backsolve(op.ost, k, st);
     launch_combine<double>(a, op.Z, N, k, op.ost, false, N, st);
-    launch_rows_residual(op.g0, op.rows2up, b, a, op.r, st);
+    launch_rows_residual(op.g0, rows, b, a, op.r, st);
     launch_norm_start<double>(op.r, N, op.ks, &op.ost, st);
     ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
     beta = sqrt(op.host_scal[0]);
@@ -895,6 +949,82 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
   if (status == ADR_ERR_NAN) return fail(ADR_ERR_NAN, "NaN or Inf in the Krylov iteration");
   if (status == ADR_ERR_NOT_CONVERGED) return fail(ADR_ERR_NOT_CONVERGED, "iteration budget spent above the tolerance");
   return ADR_OK;
+}
+
+int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double tol, int maxit, adr_solve_info_t* info) {
+  if (!h || !a_out) return fail(ADR_ERR_ARG, "null argument");
+  if (!(tol >= 0.0) || maxit < 0) return fail(ADR_ERR_ARG, "tol must be >= 0 and maxit >= 0");
+  Op& op = h->op;
+  const double2* b = (const double2*)rhs_in;
+  if (!b) {
+    ADR_TRY(adr_point_source_rhs(h, op.b));
+    b = op.b;
+  }
+  return fgmres(op, false, b, (double2*)a_out, use_x0, tol, maxit, info);
+}
+
+int adr_adjoint_solve(adr_op_t h, const void* rhs, void* lambda, int use_x0, double tol, int maxit,
+                      adr_solve_info_t* info) {
+  if (!h || !rhs || !lambda) return fail(ADR_ERR_ARG, "null argument");
+  if (!(tol >= 0.0) || maxit < 0) return fail(ADR_ERR_ARG, "tol must be >= 0 and maxit >= 0");
+  if (rhs == lambda) return fail(ADR_ERR_ARG, "lambda may not alias rhs");
+  Op& op = h->op;
+  if (!op.p.adjoint) return fail(ADR_ERR_STATE, "operator created without params.adjoint");
+  return fgmres(op, true, (const double2*)rhs, (double2*)lambda, use_x0, tol, maxit, info);
+}
+
+int adr_apply_adjoint(adr_op_t h, const void* x, void* y) {
+  if (!h || !x || !y) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  if (!op.p.adjoint) return fail(ADR_ERR_STATE, "operator created without params.adjoint");
+  launch_rows_apply(op.g0, op.rows2upT, (const double2*)x, (double2*)y, op.st);
+  return check_launch("adr_apply_adjoint");
+}
+
+int adr_vcycle_adjoint(adr_op_t h, const void* r, void* z) {
+  if (!h || !r || !z) return fail(ADR_ERR_ARG, "null argument");
+  if (r == z) return fail(ADR_ERR_ARG, "z may not alias r");
+  Op& op = h->op;
+  if (!op.p.adjoint) return fail(ADR_ERR_STATE, "operator created without params.adjoint");
+  const int64_t N = op.g0.N;
+  if (op.p.precond_precision == ADR_F64) {
+    launch_copy<double>((const double2*)r, op.a64.lv[0].b, N, op.st);
+    ADR_TRY(run_cycle(op, op.a64, true));
+    launch_copy<double>(op.a64.lv[0].x, (double2*)z, N, op.st);
+  } else {
+    launch_copy<float>((const float2*)r, op.a32.lv[0].b, N, op.st);
+    ADR_TRY(run_cycle(op, op.a32, true));
+    launch_copy<float>(op.a32.lv[0].x, (float2*)z, N, op.st);
+  }
+  return check_launch("adr_vcycle_adjoint");
+}
+
+int adr_receivers(adr_op_t h, int nrec, const int64_t* rec, const void* d, const void* u, void* res, void* rhs,
+                  double* misfit) {
+  if (!h || nrec < 0 || (nrec > 0 && (!rec || !d || !u))) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  if (rhs) launch_zero<double>((double2*)rhs, op.g0.N, op.st);
+  if (nrec == 0) {
+    if (misfit) *misfit = 0.0;
+    return check_launch("adr_receivers");
+  }
+  launch_receivers(op.g0.N, nrec, rec, (const double2*)d, (const double2*)u, op.tau, op.omega, (double2*)res,
+                   (double2*)rhs, op.ks.nrm2, op.st);
+  ADR_TRY(check_launch("adr_receivers"));
+  if (misfit) {
+    ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2));
+    if (op.host_scal[1] != 0.0) return fail(ADR_ERR_ARG, "receiver index outside the grid");
+    *misfit = 0.5 * op.host_scal[0];
+  }
+  return ADR_OK;
+}
+
+int adr_kappa_gradient(adr_op_t h, const double* kappa, const double* gamma, const void* a, const void* lambda,
+                       double* grad) {
+  if (!h || !kappa || !gamma || !a || !lambda || !grad) return fail(ADR_ERR_ARG, "null argument");
+  Op& op = h->op;
+  launch_kappa_gradient(op.g0.N, op.omega, kappa, gamma, (const double2*)a, (const double2*)lambda, grad, op.st);
+  return check_launch("adr_kappa_gradient");
 }
 
 int adr_solve_host(int dim, const int* n, const double* h, const int* src, double omega, const double* kappa,

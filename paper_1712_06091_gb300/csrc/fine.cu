@@ -121,6 +121,11 @@ void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
 // Writes the row of node j (coordinates ii) in cross form into c[1 + 4*DIM].
 template <int DIM, typename T>
 __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int64_t j, const int ii[3], C<T>* c) {
+  if (f.rows) {
+#pragma unroll
+    for (int q = 0; q < 1 + 4 * DIM; ++q) c[q] = __ldg(f.rows + (int64_t)q * g.N + j);
+    return;
+  }
   if (j == f.dyn->src_index) {
     c[0] = f.src_row[0];
 #pragma unroll
@@ -555,6 +560,46 @@ void launch_fine_store_rows(const Dims& g, const FineOp<double>& f, double2* row
   if (g.dim == 2) count_launches(1), k_fine_store_rows<2, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
   else count_launches(1), k_fine_store_rows<3, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
 }
+void launch_fine_store_rows(const Dims& g, const FineOp<float>& f, float2* rows, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_fine_store_rows<2, float><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
+  else count_launches(1), k_fine_store_rows<3, float><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
+}
+
+// Conjugate transpose of stored cross rows: row i of A^H holds, at the slot
+// of offset o, conj(A[i + o][i]), the entry of row i + o at offset -o (zero
+// when i + o is off the grid, where A has no row).
+template <int DIM, typename T>
+__global__ void k_rows_adjoint(Dims g, const C<T>* __restrict__ rows, C<T>* __restrict__ rowsT) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  int ii[3];
+  unravel(g, i, ii[0], ii[1], ii[2]);
+  const C<T> c0 = rows[i];
+  rowsT[i] = mk<T>(c0.x, -c0.y);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int64_t stride = d == 0 ? 1 : (d == 1 ? g.s1 : g.s2);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int o = (s & 2) ? ((s & 1) ? 2 : -2) : ((s & 1) ? 1 : -1);   // slots -1, +1, -2, +2
+      const int q = 1 + 4 * d + s, qbar = 1 + 4 * d + (s ^ 1);
+      C<T> v = czero<T>();
+      const int k = ii[d] + o;
+      if (k >= 0 && k < g.n[d]) {
+        const C<T> a = rows[(int64_t)qbar * g.N + i + o * stride];
+        v = mk<T>(a.x, -a.y);
+      }
+      rowsT[(int64_t)q * g.N + i] = v;
+    }
+  }
+}
+template <typename T>
+void launch_rows_adjoint(const Dims& g, const C<T>* rows, C<T>* rowsT, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_rows_adjoint<2, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, rowsT);
+  else count_launches(1), k_rows_adjoint<3, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, rowsT);
+}
+template void launch_rows_adjoint<double>(const Dims&, const double2*, double2*, cudaStream_t);
+template void launch_rows_adjoint<float>(const Dims&, const float2*, float2*, cudaStream_t);
 void launch_rows_apply(const Dims& g, const double2* rows, const double2* x, double2* y, cudaStream_t st) {
   if (g.dim == 2) count_launches(1), k_rows_apply<2, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, x, y);
   else count_launches(1), k_rows_apply<3, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, x, y);
