@@ -109,6 +109,7 @@ typedef struct adr_op_info {
   int levels;
   adr_level_info_t level[ADR_MAX_LEVELS];
   int64_t arena_bytes;     /* device bytes owned by the operator */
+  int problems;            /* problems of a batched operator (1 otherwise) */
 } adr_op_info_t;
 
 typedef struct adr_solve_info {
@@ -150,6 +151,30 @@ int adr_operator_create(int dim, const int* n, const double* h, const int* src, 
 int adr_operator_update(adr_op_t op, const int* src, double omega, const double* kappa, const double* tau1,
                         const double* gamma);
 
+/* A batch of `problems` independent point-source problems on one grid (the
+ * same dim, n, h and params), each with its own source, frequency, slowness,
+ * travel time and absorbing profile; the paper has no batched form.  Every
+ * operation of the operator then runs all problems at once: each kernel
+ * launch covers every problem's nodes (one launch per step of the cycle and
+ * of the Krylov iteration), and the problems' flexible GMRES iterations
+ * advance in lockstep, a problem that meets its tolerance being frozen.
+ *   src: int[3 * problems] (3 entries per problem, unused axes 0);
+ *   omega: double[problems] (host arrays);
+ *   kappa, tau1, gamma: device float64[problems * N], problem-major.
+ * Vectors of the other entry points become problem-major arrays of
+ * problems * N entries; adr_solve fills `problems` info entries;
+ * adr_coefficients / adr_level_stencil write one block per problem.  The
+ * adjoint (params.adjoint) is built for single problems only (ADR_ERR_ARG).
+ * problems in [1, 65535]. */
+int adr_batch_create(int dim, const int* n, const double* h, int problems, const int* src, const double* omega,
+                     const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
+                     void* stream, adr_op_t* out);
+
+/* adr_operator_update for a batch (arrays as in adr_batch_create); the
+ * single-problem adr_operator_update refuses batches (ADR_ERR_STATE). */
+int adr_batch_update(adr_op_t op, const int* src, const double* omega, const double* kappa, const double* tau1,
+                     const double* gamma);
+
 /* Releases the operator and its device arena (after synchronising its stream). */
 int adr_operator_destroy(adr_op_t op);
 
@@ -187,7 +212,8 @@ int adr_point_source_rhs(adr_op_t op, void* q);
  *   Stops when |rhs - H_2up a| / |rhs| <= tol (checked on the Givens estimate
  *   inside a cycle and explicitly at the end of each cycle) or after maxit
  *   iterations (then ADR_ERR_NOT_CONVERGED, a still holds the iterate).
- *   info may be NULL. */
+ *   info may be NULL; for a batch it receives one entry per problem, and the
+ *   return code is ADR_ERR_NOT_CONVERGED if any problem missed the tolerance. */
 int adr_solve(adr_op_t op, const void* rhs, void* a, int use_x0, double tol, int maxit,
               adr_solve_info_t* info);
 

@@ -28,7 +28,8 @@ TRAVELTIME_STATIC_MAX_SWEEPS = 8192
 
 # The exported entry points, in the order include/adr.h declares them.
 EXPORTS = (
-    "adr_params_default", "adr_operator_create", "adr_operator_update", "adr_operator_destroy", "adr_operator_info",
+    "adr_params_default", "adr_operator_create", "adr_operator_update", "adr_batch_create", "adr_batch_update",
+    "adr_operator_destroy", "adr_operator_info",
     "adr_coefficients", "adr_apply", "adr_level_stencil", "adr_vcycle", "adr_point_source_rhs",
     "adr_solve", "adr_reconstruct", "adr_solve_host", "adr_adjoint_solve", "adr_apply_adjoint", "adr_vcycle_adjoint",
     "adr_receivers", "adr_kappa_gradient", "adr_traveltime", "adr_traveltime_static", "adr_profile_kernel",
@@ -63,7 +64,7 @@ class LevelInfo(ctypes.Structure):
 
 class OpInfo(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("levels", ctypes.c_int), ("level", LevelInfo * MAX_LEVELS),
-                ("arena_bytes", ctypes.c_int64)]
+                ("arena_bytes", ctypes.c_int64), ("problems", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -94,6 +95,8 @@ def load():
         "adr_params_default": [ctypes.POINTER(Params)],
         "adr_operator_create": [i, ip, dp, ip, d, vp, vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
         "adr_operator_update": [vp, ip, d, vp, vp, vp],
+        "adr_batch_create": [i, ip, dp, i, ip, dp, vp, vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
+        "adr_batch_update": [vp, ip, dp, vp, vp, vp],
         "adr_operator_destroy": [vp],
         "adr_operator_info": [vp, ctypes.POINTER(OpInfo)],
         "adr_coefficients": [vp, vp],

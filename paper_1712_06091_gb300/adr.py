@@ -142,7 +142,7 @@ class Operator:
         L.check(self._lib.adr_operator_info(self._h, ctypes.byref(i)))
         levels = [{"n": tuple(i.level[l].n[: self.dim]), "nodes": i.level[l].nodes,
                    "stencil_points": i.level[l].stencil_points} for l in range(i.levels)]
-        return {"dim": i.dim, "levels": levels, "arena_bytes": i.arena_bytes}
+        return {"dim": i.dim, "levels": levels, "arena_bytes": i.arena_bytes, "problems": i.problems}
 
     def coefficients(self) -> torch.Tensor:
         """(2*dim + 3, N) float64: d tau per axis, d^2 tau per axis, Re rho, Im rho, tau."""
@@ -367,3 +367,90 @@ class KappaMisfit(torch.autograd.Function):
     def backward(ctx, gJ):
         (grad,) = ctx.saved_tensors
         return gJ * grad, None
+
+
+class BatchOperator(Operator):
+    """adr_batch_create: `problems` point-source problems on one grid, run together.
+
+    Inputs and vectors are problem-major: kappa, tau1, gamma of shape
+    (problems, N) (or flat problems * N); solve() returns a (problems * N)
+    complex128 tensor and one info dict per problem.  `nodes` is N, `N` the
+    total length of a batch vector.
+    """
+
+    def __init__(self, n, h, srcs, omegas, kappa, tau1, gamma, params=None, device="cuda", stream=None):
+        self._lib = L.load()
+        self.dim = len(n)
+        self.n = tuple(int(v) for v in n)
+        self.h = tuple(float(v) for v in h)
+        self.problems = len(srcs)
+        if len(omegas) != self.problems:
+            raise ValueError("one frequency per source")
+        self.srcs = [tuple(int(v) for v in s) for s in srcs]
+        self.omegas = [float(w) for w in omegas]
+        self.nodes = int(np.prod(self.n))
+        self.N = self.nodes * self.problems
+        self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.params = params if params is not None else default_params()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        k = _dev_real(kappa, self.N, self.device)
+        t = _dev_real(tau1, self.N, self.device)
+        g = _dev_real(gamma, self.N, self.device)
+        nn = (ctypes.c_int * 3)(*self.n, *([1] * (3 - self.dim)))
+        hh = (ctypes.c_double * 3)(*self.h, *([1.0] * (3 - self.dim)))
+        ss, ww = self._src_omega(self.srcs, self.omegas)
+        handle = ctypes.c_void_p()
+        L.check(self._lib.adr_batch_create(self.dim, nn, hh, self.problems, ss, ww, _ptr(k), _ptr(t), _ptr(g),
+                                           ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream),
+                                           ctypes.byref(handle)))
+        self._h = handle
+        self.cycle_dtype = torch.complex128 if self.params.precond_precision == L.ADR_F64 else torch.complex64
+        self.src = self.srcs[0]
+        self.omega = self.omegas[0]
+
+    def _src_omega(self, srcs, omegas):
+        if len(srcs) != self.problems or len(omegas) != self.problems:
+            raise ValueError(f"expected {self.problems} sources and frequencies")
+        ss = (ctypes.c_int * (3 * self.problems))()
+        for p, s in enumerate(srcs):
+            for d in range(self.dim):
+                ss[3 * p + d] = int(s[d])
+        ww = (ctypes.c_double * self.problems)(*[float(w) for w in omegas])
+        return ss, ww
+
+    def update(self, srcs, omegas, kappa, tau1, gamma):
+        """adr_batch_update: new sources / frequencies / media, same grid and arena."""
+        k = _dev_real(kappa, self.N, self.device)
+        t = _dev_real(tau1, self.N, self.device)
+        g = _dev_real(gamma, self.N, self.device)
+        ss, ww = self._src_omega(srcs, omegas)
+        L.check(self._lib.adr_batch_update(self._h, ss, ww, _ptr(k), _ptr(t), _ptr(g)))
+        self.srcs = [tuple(int(v) for v in s) for s in srcs]
+        self.omegas = [float(w) for w in omegas]
+
+    def coefficients(self) -> torch.Tensor:
+        out = torch.empty((self.problems, 2 * self.dim + 3, self.nodes), dtype=torch.float64, device=self.device)
+        L.check(self._lib.adr_coefficients(self._h, _ptr(out)))
+        return out
+
+    def level_stencil(self, level) -> torch.Tensor:
+        info = self.info()["levels"][level]
+        out = torch.empty((self.problems, info["stencil_points"], info["nodes"]), dtype=self.cycle_dtype,
+                          device=self.device)
+        L.check(self._lib.adr_level_stencil(self._h, int(level), _ptr(out)))
+        return out
+
+    def solve(self, rhs=None, x0=None, tol=1e-8, maxit=500, out=None, raise_on_fail=True):
+        """(a, [info dict per problem]).  rhs=None solves for the point sources."""
+        a = out if out is not None else torch.empty(self.N, dtype=torch.complex128, device=self.device)
+        self._vec(a, torch.complex128)
+        if x0 is not None:
+            a.copy_(x0.reshape(-1))
+        rp = ctypes.c_void_p(0) if rhs is None else _ptr(self._vec(rhs.reshape(-1), torch.complex128))
+        infos = (L.SolveInfo * self.problems)()
+        rc = self._lib.adr_solve(self._h, rp, _ptr(a), 1 if x0 is not None else 0, float(tol), int(maxit), infos)
+        L.check(rc, () if raise_on_fail else (L.ADR_ERR_NOT_CONVERGED,))
+        return a, [{"iterations": i.iterations, "restarts": i.restarts, "rel_residual": i.rel_residual,
+                    "rel_estimate": i.rel_estimate, "status": i.status} for i in infos]

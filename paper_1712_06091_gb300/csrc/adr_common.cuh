@@ -75,6 +75,7 @@ struct Dims {
   int n[3];
   int64_t N;
   int64_t s1, s2;  // strides of axes 1 and 2
+  int B;           // problems sharing this grid in a batched launch (grid.y)
 };
 
 inline Dims make_dims(int dim, const int* n) {
@@ -86,8 +87,26 @@ inline Dims make_dims(int dim, const int* n) {
   g.s1 = g.n[0];
   g.s2 = (int64_t)g.n[0] * g.n[1];
   g.N = g.s2 * g.n[2];
+  g.B = 1;
   return g;
 }
+
+// Batched launches: problem blockIdx.y, whose slice of every per-problem
+// array starts `stride` entries after the previous problem's.
+template <typename... P>
+__device__ __forceinline__ void batch_shift(int64_t stride, P&... p) {
+  const int64_t o = (int64_t)blockIdx.y * stride;
+  ((p += o), ...);
+}
+// The same for pointers that may be null (they stay null).
+template <typename... P>
+__device__ __forceinline__ void batch_shift_opt(int64_t stride, P&... p) {
+  const int64_t o = (int64_t)blockIdx.y * stride;
+  ((p = (p != nullptr) ? p + o : p), ...);
+}
+
+// Per-problem partial sums of the last-block reductions.
+constexpr int64_t kPartialStride = 20480;
 
 __device__ __forceinline__ void unravel(const Dims& g, int64_t j, int& i0, int& i1, int& i2) {
   i0 = (int)(j % g.n[0]);
@@ -185,6 +204,7 @@ template <typename T> struct FineOp {
                      // instead of building the row (the conjugate-transposed operator)
 };
 
+
 // Scheme -> upwind weights.
 template <typename T> inline void set_scheme(FineOp<T>& f, int scheme, double beta) {
   f.central = 0;
@@ -247,7 +267,7 @@ template <typename T> void launch_stencil_mr_apply(const Dims& g, const C<T>* A,
                                                    double2* partial, unsigned* ticket, double2* alpha, cudaStream_t st);
 template <typename T> void launch_stencil_residual_dinv(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x,
                                                         const C<T>* dinv, C<T>* r, C<T>* z, cudaStream_t st);
-template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, cudaStream_t st);
+template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, int B, cudaStream_t st);
 template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st);
 
 // Transfers.
@@ -271,14 +291,17 @@ int set_last_error(int code, const char* msg);
 template <typename T> void launch_cmul_vec(const C<T>* a, const C<T>* b, C<T>* out, int64_t n, cudaStream_t st);  // out = a .* b
 template <typename Ts, typename Td> void launch_ccast(const C<Ts>* src, C<Td>* dst, int64_t n, cudaStream_t st);
 
-void launch_rhs_point(double2* q, int64_t N, int64_t src_index, double value, cudaStream_t st);
+// q = value at each problem's source node (dyn[p].src_index), zero elsewhere.
+void launch_rhs_point(double2* q, int64_t N, const FineDyn* dyn, double value, int B, cudaStream_t st);
 // Receiver residuals res = R u - d, rhs += M^H R^T res, out = (sum |res|^2, bad indices).
 void launch_receivers(int64_t N, int nrec, const int64_t* rec, const double2* d, const double2* u, const double* tau,
                       double omega, double2* res, double2* rhs, double2* out, cudaStream_t st);
 // grad -= Re(conj(lambda) (2 w^2 kappa - 2 i w gamma kappa) a), elementwise.
 void launch_kappa_gradient(int64_t N, double omega, const double* kappa, const double* gamma, const double2* a,
                            const double2* lambda, double* grad, cudaStream_t st);
-void launch_reconstruct(const double2* a, const double* tau, double omega, double2* u, int64_t N, cudaStream_t st);
+// u = a exp(-i w tau) with each problem's w from dyn.
+void launch_reconstruct(const double2* a, const double* tau, const FineDyn* dyn, double2* u, int64_t N, int B,
+                        cudaStream_t st);
 void launch_pack_coefficients(const Dims& g, const double* const gd[3], const double* const td[3], const double2* rho,
                               const double* tau, double* out, cudaStream_t st);
 

@@ -10,6 +10,7 @@
 //    level (Sec. 3.1, Sec. 4.2).
 //  * adr_solve: right-preconditioned flexible GMRES(m) in float64 on H_2up,
 //    classical Gram-Schmidt applied twice, Givens rotations on the device.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -86,19 +87,19 @@ template <typename T> struct Level {
   ArnoldiState ks{};
 };
 
-constexpr int kMaxDots = kMaxKrylov + 2;
 constexpr int64_t kSmallCoarse = 8192;      // one-block coarsest solve up to this size (no cluster)
 constexpr int64_t kClusterCoarse = 32768;   // cluster coarsest solve up to this size
 
-static void take_arnoldi(Arena& a, ArnoldiState& s, int m) {
+// B Arnoldi states packed problem-major (see arnoldi_at).
+static void take_arnoldi(Arena& a, ArnoldiState& s, int m, int B) {
   s.m = m;
-  s.H = a.take<double2>((size_t)(m + 1) * m);
-  s.cs = a.take<double>(m);
-  s.sn = a.take<double2>(m);
-  s.g = a.take<double2>(m + 1);
-  s.y = a.take<double2>(m);
-  s.scal = a.take<double>(kNumScal);
-  s.iscal = a.take<int>(kNumIScal);
+  s.H = a.take<double2>((size_t)(m + 1) * m * B);
+  s.cs = a.take<double>((size_t)m * B);
+  s.sn = a.take<double2>((size_t)m * B);
+  s.g = a.take<double2>((size_t)(m + 1) * B);
+  s.y = a.take<double2>((size_t)m * B);
+  s.scal = a.take<double>((size_t)kNumScal * B);
+  s.iscal = a.take<int>((size_t)kNumIScal * B);
 }
 
 template <typename T> struct Hier {
@@ -109,13 +110,16 @@ template <typename T> struct Hier {
 
 struct Op {
   int dim = 0;
+  int B = 1;                        // problems of the batch (same grid; own source, frequency, medium)
   Dims g0{};
   adr_params_t p{};
   cudaStream_t st = nullptr;
-  double omega = 0;
+  double omega = 0;                 // problem 0 (the only one when B = 1)
   double h[3] = {0, 0, 0};
   int src[3] = {0, 0, 0};
   int64_t src_index = 0;
+  std::vector<double> omegas;       // per problem
+  std::vector<int> srcs;            // 3 per problem
   // fine coefficients
   double* gd[3] = {nullptr, nullptr, nullptr};
   double* td[3] = {nullptr, nullptr, nullptr};
@@ -164,7 +168,8 @@ struct Op {
   double prof_ms = 0.0;
   void* arena = nullptr;
   size_t arena_bytes = 0;
-  double* host_scal = nullptr;  // pinned: [0] estimate, [1] hn, [2] norm^2
+  double* host_scal = nullptr;  // pinned: the per-problem scalars read by the solve
+  size_t host_scal_count = 0;
 };
 
 constexpr int kProfPairs = 256;
@@ -222,28 +227,30 @@ template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
       int nc[3];
       for (int d = 0; d < 3; ++d) nc[d] = (H.lv[l - 1].g.n[d] - 1) / 2 + 1;
       g = make_dims(op.dim, nc);
+      g.B = op.B;
     }
     H.L = l + 1;
     H.lv[l].g = g;
   }
   const int S = op.dim == 2 ? kPattern2 : kPattern3;
+  const size_t B = (size_t)op.B;
   for (int l = 0; l < H.L; ++l) {
     Level<T>& L = H.lv[l];
     const size_t N = (size_t)L.g.N;
-    L.A = l > 0 ? a.take<C<T>>((size_t)stencil_entries((int64_t)N, S)) : nullptr;
-    L.dinv = a.take<C<T>>(N);
-    L.b = a.take<C<T>>(N);
-    L.x = a.take<C<T>>(N);
-    L.r = a.take<C<T>>(N);
-    L.t = a.take<C<T>>(N);
-    L.z = a.take<C<T>>(N);
+    L.A = l > 0 ? a.take<C<T>>((size_t)stencil_entries((int64_t)N, S) * B) : nullptr;
+    L.dinv = a.take<C<T>>(N * B);
+    L.b = a.take<C<T>>(N * B);
+    L.x = a.take<C<T>>(N * B);
+    L.r = a.take<C<T>>(N * B);
+    L.t = a.take<C<T>>(N * B);
+    L.z = a.take<C<T>>(N * B);
     L.kdim = 0;
     if (l == H.L - 1) L.kdim = p.coarse_iterations;
     else if (p.cycle == ADR_CYCLE_K && l > 0) L.kdim = p.kcycle_iterations;
     if (L.kdim > 0) {
-      L.KV = a.take<C<T>>((size_t)(L.kdim + 1) * N);
-      L.KZ = (l == H.L - 1) ? nullptr : a.take<C<T>>((size_t)L.kdim * N);
-      take_arnoldi(a, L.ks, L.kdim);
+      L.KV = a.take<C<T>>((size_t)(L.kdim + 1) * N * B);
+      L.KZ = (l == H.L - 1) ? nullptr : a.take<C<T>>((size_t)L.kdim * N * B);
+      take_arnoldi(a, L.ks, L.kdim, op.B);
     }
   }
 }
@@ -262,35 +269,36 @@ template <typename T> static void plan_adjoint(const Hier<T>& H, Hier<T>& HT, Ar
 }
 
 static void plan(Op& op, Arena& a) {
+  const size_t B = (size_t)op.B;
   const size_t N = (size_t)op.g0.N;
+  const size_t NB = N * B;
   for (int d = 0; d < op.dim; ++d) {
-    op.gd[d] = a.take<double>(N);
-    op.td[d] = a.take<double>(N);
-    op.gf[d] = a.take<float>(N);
-    op.tf[d] = a.take<float>(N);
+    op.gd[d] = a.take<double>(NB);
+    op.td[d] = a.take<double>(NB);
+    op.gf[d] = a.take<float>(NB);
+    op.tf[d] = a.take<float>(NB);
   }
-  op.rho = a.take<double2>(N);
-  op.rhof = a.take<float>(2 * N);
-  op.tau = a.take<double>(N);
-  op.srow = a.take<double2>(kCross3);
-  op.srowf = a.take<float>(2 * kCross3);
+  op.rho = a.take<double2>(NB);
+  op.rhof = a.take<float>(2 * NB);
+  op.tau = a.take<double>(NB);
+  op.srow = a.take<double2>(kCross3 * B);
+  op.srowf = a.take<float>(2 * kCross3 * B);
   if (op.p.precond_precision == ADR_F64) plan_hierarchy(op, op.h64, a);
   else plan_hierarchy(op, op.h32, a);
   const int m = op.p.restart;
-  op.V = a.take<double2>((size_t)(m + 1) * N);
-  op.Z = a.take<double2>((size_t)m * N);
-  op.b = a.take<double2>(N);
-  op.r = a.take<double2>(N);
-  op.rows2up = a.take<double2>((size_t)(1 + 4 * op.dim) * N);
-  take_arnoldi(a, op.ost, m);
-  const size_t partial_cgs = (size_t)kMaxReduceBlocks * kMaxDots, partial_mr = (size_t)kMaxMrBlocks * 2;
-  op.ks.partial = a.take<double2>(partial_cgs > partial_mr ? partial_cgs : partial_mr);
-  op.ks.ticket = a.take<unsigned>(1);
-  op.ks.ha = a.take<double2>(kMaxDots);
-  op.ks.hb = a.take<double2>(kMaxDots);
-  op.ks.nrm2 = a.take<double2>(1);
-  op.ks.alpha = a.take<double2>(1);
-  op.dyn = a.take<FineDyn>(1);
+  op.V = a.take<double2>((size_t)(m + 1) * NB);
+  op.Z = a.take<double2>((size_t)m * NB);
+  op.b = a.take<double2>(NB);
+  op.r = a.take<double2>(NB);
+  op.rows2up = a.take<double2>((size_t)(1 + 4 * op.dim) * NB);
+  take_arnoldi(a, op.ost, m, op.B);
+  op.ks.partial = a.take<double2>((size_t)kPartialStride * B);
+  op.ks.ticket = a.take<unsigned>(B);
+  op.ks.ha = a.take<double2>((size_t)kMaxDots * B);
+  op.ks.hb = a.take<double2>((size_t)kMaxDots * B);
+  op.ks.nrm2 = a.take<double2>(B);
+  op.ks.alpha = a.take<double2>(B);
+  op.dyn = a.take<FineDyn>(B);
   if (op.p.adjoint) {
     const size_t cross = (size_t)(1 + 4 * op.dim) * N;
     const size_t cbytes = op.p.precond_precision == ADR_F64 ? sizeof(double2) : sizeof(float2);
@@ -370,14 +378,14 @@ template <typename T> struct Cycle {
         x_zero = false;
         C<T>* tmp = cur; cur = oth; oth = tmp;
       }
-      if (cur != x) launch_copy<T>(cur, x, n, st);
+      if (cur != x) launch_copy<T>(cur, x, n * L.g.B, st);
       return false;
     }
     // Minimal-residual Jacobi: z = D^{-1} r, w = A z, alpha = (w^H r)/(w^H w),
     // x += alpha z, r -= alpha w (two launches per sweep).
     const C<T>* rsrc;
     if (x_zero) {
-      launch_cmul_vec<T>(L.dinv, b, L.z, n, st);
+      launch_cmul_vec<T>(L.dinv, b, L.z, n * L.g.B, st);
       rsrc = b;
     } else {
       residual_dinv(l, b, x, L.r, L.z);
@@ -386,7 +394,7 @@ template <typename T> struct Cycle {
     for (int s = 0; s < sweeps; ++s) {
       mr_apply(l, L.z, rsrc, L.t);
       launch_mr_update2<T>(x, L.z, rsrc, L.r, L.t, op.ks.alpha, L.dinv, s + 1 < sweeps ? L.z : nullptr, x_zero && s == 0,
-                           n, st);
+                           n, st, L.g.B);
       rsrc = L.r;
     }
     x_zero = false;
@@ -395,9 +403,10 @@ template <typename T> struct Cycle {
 
   // Arnoldi step j: w (holding A z_j) orthogonalised against V_0..V_j by CGS2,
   // Hessenberg column and rotation updated; V_{j+1} = w / |w| if store_next.
-  void arnoldi(ArnoldiState& ks, C<T>* Vb, int64_t ld, int j, C<T>* w, int64_t n, bool store_next) {
-    launch_cgs2<T>(Vb, ld, j + 1, w, n, op.ks, ks, j, st);
-    if (store_next) launch_scale_inv_norm<T>(w, Vb + (int64_t)(j + 1) * ld, op.ks.nrm2, n, st);
+  // Vb holds the basis at stride ld = B n (vector-major over the batch).
+  void arnoldi(ArnoldiState& ks, C<T>* Vb, int64_t ld, int j, C<T>* w, int64_t n, int B, bool store_next) {
+    launch_cgs2<T>(Vb, ld, j + 1, w, n, op.ks, ks, j, st, B);
+    if (store_next) launch_scale_inv_norm<T>(w, Vb + (int64_t)(j + 1) * ld, op.ks.nrm2, n, st, B);
   }
 
   // Fixed-count GMRES from zero, right-preconditioned by D^{-1} (coarsest level).
@@ -418,16 +427,18 @@ template <typename T> struct Cycle {
       launch_coarse_gmres_cta<T>(L.g, L.A, L.dinv, b, x, L.KV, L.z, k, L.ks, st);
       return;
     }
-    launch_norm_start<T>(b, n, op.ks, &L.ks, st);
-    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st);
+    const int B = L.g.B;
+    const int64_t ld = n * B;
+    launch_norm_start<T>(b, n, op.ks, &L.ks, st, B);
+    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st, B);
     for (int j = 0; j < k; ++j) {
-      launch_cmul_vec<T>(L.dinv, L.KV + (int64_t)j * n, L.z, n, st);
+      launch_cmul_vec<T>(L.dinv, L.KV + (int64_t)j * ld, L.z, ld, st);
       apply(l, L.z, L.t);
-      arnoldi(L.ks, L.KV, n, j, L.t, n, j + 1 < k);
+      arnoldi(L.ks, L.KV, ld, j, L.t, n, B, j + 1 < k);
     }
-    launch_backsolve(L.ks, k, st);
-    launch_combine<T>(L.t, L.KV, n, k, L.ks, true, n, st);
-    launch_cmul_vec<T>(L.dinv, L.t, x, n, st);
+    launch_backsolve(L.ks, k, st, B);
+    launch_combine<T>(L.t, L.KV, ld, k, L.ks, true, n, st, B);
+    launch_cmul_vec<T>(L.dinv, L.t, x, ld, st);
   }
 
   // Inner flexible GMRES of the K-cycle on level l, from zero, fixed count.
@@ -435,16 +446,18 @@ template <typename T> struct Cycle {
     Level<T>& L = H.lv[l];
     const int64_t n = L.g.N;
     const int k = L.kdim;
-    launch_norm_start<T>(b, n, op.ks, &L.ks, st);
-    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st);
+    const int B = L.g.B;
+    const int64_t ld = n * B;
+    launch_norm_start<T>(b, n, op.ks, &L.ks, st, B);
+    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st, B);
     for (int j = 0; j < k; ++j) {
-      C<T>* zj = L.KZ + (int64_t)j * n;
-      cycle(l, L.KV + (int64_t)j * n, zj);
+      C<T>* zj = L.KZ + (int64_t)j * ld;
+      cycle(l, L.KV + (int64_t)j * ld, zj);
       apply(l, zj, L.t);
-      arnoldi(L.ks, L.KV, n, j, L.t, n, j + 1 < k);
+      arnoldi(L.ks, L.KV, ld, j, L.t, n, B, j + 1 < k);
     }
-    launch_backsolve(L.ks, k, st);
-    launch_combine<T>(x, L.KZ, n, k, L.ks, true, n, st);
+    launch_backsolve(L.ks, k, st, B);
+    launch_combine<T>(x, L.KZ, ld, k, L.ks, true, n, st, B);
   }
 
   // x = B_l^{-1} b, zero initial guess (Alg. TwoGrid / Alg. Kcycle).
@@ -463,7 +476,7 @@ template <typename T> struct Cycle {
     }
     if (op.p.cycle == ADR_CYCLE_K && l + 1 < H.L - 1) kcycle(l + 1, Lc.b, Lc.x);
     else cycle(l + 1, Lc.b, Lc.x);
-    if (x_zero) { launch_zero<T>(x, n, st); x_zero = false; }
+    if (x_zero) { launch_zero<T>(x, n * L.g.B, st); x_zero = false; }
     launch_prolong_add<T>(L.g, Lc.g, Lc.x, x, st);
     relax(l, b, x, op.p.post_sweeps[l], x_zero);
   }
@@ -501,22 +514,31 @@ template <typename T> static int build_adjoint(Op& op, Hier<T>& H, Hier<T>& HT) 
 // current source / frequency, written into the operator's arena (no sync).
 static int setup(Op& op, const double* kappa, const double* tau1, const double* gamma) {
   const int64_t N = op.g0.N;
-  FineDyn dyn{};
-  dyn.omega = op.omega;
-  for (int d = 0; d < 3; ++d) dyn.src[d] = op.src[d];
-  dyn.src_index = op.src_index;
-  launch_set_dyn(op.dyn, dyn, op.st);
-  FineInputs in{};
-  in.kappa = kappa; in.tau1 = tau1; in.gamma = gamma;
-  for (int d = 0; d < 3; ++d) { in.src[d] = op.src[d]; in.h[d] = op.h[d]; in.ih[d] = 1.0 / op.h[d]; }
-  in.omega = op.omega;
-  launch_coefficients(op.g0, in, op.gd, op.td, op.rho, op.tau, op.srow, op.st);
-  for (int d = 0; d < op.dim; ++d) {
-    launch_to_f32(op.gd[d], op.gf[d], N, op.st);
-    launch_to_f32(op.td[d], op.tf[d], N, op.st);
+  const int64_t NB = N * op.B;
+  Dims g1 = op.g0;
+  g1.B = 1;
+  for (int pb = 0; pb < op.B; ++pb) {   // per-problem coefficients (setup, not the cycle)
+    FineDyn dyn{};
+    dyn.omega = op.omegas[pb];
+    for (int d = 0; d < 3; ++d) dyn.src[d] = op.srcs[3 * pb + d];
+    dyn.src_index = dyn.src[0] + op.g0.s1 * dyn.src[1] + op.g0.s2 * dyn.src[2];
+    launch_set_dyn(op.dyn + pb, dyn, op.st);
+    FineInputs in{};
+    const int64_t o = (int64_t)pb * N;
+    in.kappa = kappa + o; in.tau1 = tau1 + o; in.gamma = gamma + o;
+    for (int d = 0; d < 3; ++d) { in.src[d] = dyn.src[d]; in.h[d] = op.h[d]; in.ih[d] = 1.0 / op.h[d]; }
+    in.omega = dyn.omega;
+    double* gd[3] = {nullptr, nullptr, nullptr};
+    double* td[3] = {nullptr, nullptr, nullptr};
+    for (int d = 0; d < op.dim; ++d) { gd[d] = op.gd[d] + o; td[d] = op.td[d] + o; }
+    launch_coefficients(g1, in, gd, td, op.rho + o, op.tau + o, op.srow + (int64_t)pb * kCross3, op.st);
   }
-  launch_to_f32((const double*)op.rho, op.rhof, 2 * N, op.st);
-  launch_to_f32((const double*)op.srow, op.srowf, 2 * kCross3, op.st);
+  for (int d = 0; d < op.dim; ++d) {
+    launch_to_f32(op.gd[d], op.gf[d], NB, op.st);
+    launch_to_f32(op.td[d], op.tf[d], NB, op.st);
+  }
+  launch_to_f32((const double*)op.rho, op.rhof, 2 * NB, op.st);
+  launch_to_f32((const double*)op.srow, op.srowf, 2 * kCross3 * op.B, op.st);
   launch_fine_store_rows(op.g0, make_fine<double>(op, ADR_SCHEME_2UP, false), op.rows2up, op.st);
   ADR_TRY(check_launch("coefficients"));
   ADR_TRY(op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32));
@@ -573,19 +595,20 @@ template <typename T> static int run_cycle(Op& op, Hier<T>& H, bool adj = false)
 static int precondition(Op& op, const double2* v, double2* z, bool adj = false) {
   if (op.p.precond_precision == ADR_F64) {
     Hier<double>& H = adj ? op.a64 : op.h64;
-    launch_copy<double>(v, H.lv[0].b, op.g0.N, op.st);
+    launch_copy<double>(v, H.lv[0].b, op.g0.N * op.B, op.st);
     ADR_TRY(run_cycle(op, H, adj));
-    launch_copy<double>(H.lv[0].x, z, op.g0.N, op.st);
+    launch_copy<double>(H.lv[0].x, z, op.g0.N * op.B, op.st);
   } else {
     Hier<float>& H = adj ? op.a32 : op.h32;
-    launch_ccast<double, float>(v, H.lv[0].b, op.g0.N, op.st);
+    launch_ccast<double, float>(v, H.lv[0].b, op.g0.N * op.B, op.st);
     ADR_TRY(run_cycle(op, H, adj));
-    launch_ccast<float, double>(H.lv[0].x, z, op.g0.N, op.st);
+    launch_ccast<float, double>(H.lv[0].x, z, op.g0.N * op.B, op.st);
   }
   return ADR_OK;
 }
 
 static int read_scalars(Op& op, const double* dev, int count) {
+  if ((size_t)count > op.host_scal_count) return fail(ADR_ERR_STATE, "scalar read larger than the host buffer");
   ADR_CUDA(cudaMemcpyAsync(op.host_scal, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, op.st));
   ADR_CUDA(cudaStreamSynchronize(op.st));
   prof_collect(op);
@@ -646,22 +669,28 @@ int adr_params_default(adr_params_t* p) {
   return ADR_OK;
 }
 
-int adr_operator_create(int dim, const int* n, const double* h, const int* src, double omega, const double* kappa,
-                        const double* tau1, const double* gamma, const adr_params_t* params, void* stream, adr_op_t* out) {
+static int create_impl(int dim, const int* n, const double* h, int B, const int* src, const double* omega,
+                       const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
+                       void* stream, adr_op_t* out) {
   if (!out) return fail(ADR_ERR_ARG, "out is null");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(ADR_ERR_ARG, "dim must be 2 or 3");
-  if (!n || !h || !src || !kappa || !tau1 || !gamma) return fail(ADR_ERR_ARG, "null argument");
-  if (!(omega > 0.0)) return fail(ADR_ERR_ARG, "omega must be positive");
+  if (B < 1 || B > 65535) return fail(ADR_ERR_ARG, "problems must be in [1, 65535]");
+  if (!n || !h || !src || !omega || !kappa || !tau1 || !gamma) return fail(ADR_ERR_ARG, "null argument");
   for (int d = 0; d < dim; ++d) {
     if (n[d] < 4) return fail(ADR_ERR_ARG, "every axis needs at least 4 nodes");
     if (!(h[d] > 0.0)) return fail(ADR_ERR_ARG, "spacings must be positive");
-    if (src[d] < 0 || src[d] >= n[d]) return fail(ADR_ERR_ARG, "source outside the grid");
+  }
+  for (int pb = 0; pb < B; ++pb) {
+    if (!(omega[pb] > 0.0)) return fail(ADR_ERR_ARG, "omega must be positive");
+    for (int d = 0; d < dim; ++d)
+      if (src[3 * pb + d] < 0 || src[3 * pb + d] >= n[d]) return fail(ADR_ERR_ARG, "source outside the grid");
   }
   adr_params_t p;
   if (params) p = *params;
   else adr_params_default(&p);
   ADR_TRY(validate_params(p));
+  if (p.adjoint && B > 1) return fail(ADR_ERR_ARG, "the adjoint operator is built for one problem at a time");
   const int64_t N = (int64_t)n[0] * n[1] * (dim > 2 ? n[2] : 1);
   if (N > ((int64_t)1 << 31) - 1) return fail(ADR_ERR_ARG, "grid too large (more than 2^31 - 1 nodes)");
 
@@ -669,14 +698,18 @@ int adr_operator_create(int dim, const int* n, const double* h, const int* src, 
   if (!h_) return fail(ADR_ERR_OOM, "host allocation failed");
   Op& op = h_->op;
   op.dim = dim;
+  op.B = B;
   op.g0 = make_dims(dim, n);
+  op.g0.B = B;
   op.p = p;
   op.st = (cudaStream_t)stream;
-  op.omega = omega;
-  for (int d = 0; d < 3; ++d) {
-    op.h[d] = d < dim ? h[d] : 1.0;
-    op.src[d] = d < dim ? src[d] : 0;
-  }
+  for (int d = 0; d < 3; ++d) op.h[d] = d < dim ? h[d] : 1.0;
+  op.omegas.assign(omega, omega + B);
+  op.srcs.assign(3 * (size_t)B, 0);
+  for (int pb = 0; pb < B; ++pb)
+    for (int d = 0; d < dim; ++d) op.srcs[3 * pb + d] = src[3 * pb + d];
+  op.omega = op.omegas[0];
+  for (int d = 0; d < 3; ++d) op.src[d] = op.srcs[d];
   op.src_index = op.src[0] + op.g0.s1 * op.src[1] + op.g0.s2 * op.src[2];
 
   Arena sizing;
@@ -688,7 +721,8 @@ int adr_operator_create(int dim, const int* n, const double* h, const int* src, 
     cudaGetLastError();
     return fail(ADR_ERR_OOM, std::string("cudaMalloc of the operator arena failed: ") + cudaGetErrorString(e));
   }
-  e = cudaMallocHost(&op.host_scal, 8 * sizeof(double));
+  op.host_scal_count = std::max<size_t>(16, (size_t)B * (kNumScal > 2 ? kNumScal : 2));
+  e = cudaMallocHost(&op.host_scal, op.host_scal_count * sizeof(double));
   if (e != cudaSuccess) {
     cudaFree(op.arena);
     delete h_;
@@ -699,7 +733,9 @@ int adr_operator_create(int dim, const int* n, const double* h, const int* src, 
   plan(op, real);
   op.cluster_size = prepare_coarse_cluster(dim, p.precond_precision == ADR_F32);
   e = cudaStreamCreateWithFlags(&op.cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMemsetAsync(op.ks.ticket, 0, sizeof(unsigned), op.st);
+  // all of the arena starts at zero: reduction tickets, convergence targets of
+  // the inner Krylov instances (0 = never frozen)
+  if (e == cudaSuccess) e = cudaMemsetAsync(op.arena, 0, op.arena_bytes, op.st);
   if (e != cudaSuccess) {
     if (op.cap) cudaStreamDestroy(op.cap);
     cudaFree(op.arena);
@@ -721,17 +757,50 @@ int adr_operator_create(int dim, const int* n, const double* h, const int* src, 
   return ADR_OK;
 }
 
+int adr_operator_create(int dim, const int* n, const double* h, const int* src, double omega, const double* kappa,
+                        const double* tau1, const double* gamma, const adr_params_t* params, void* stream, adr_op_t* out) {
+  if (!src) return fail(ADR_ERR_ARG, "null argument");
+  const int s3[3] = {src[0], dim > 1 ? src[1] : 0, dim > 2 ? src[2] : 0};
+  return create_impl(dim, n, h, 1, s3, &omega, kappa, tau1, gamma, params, stream, out);
+}
+
+int adr_batch_create(int dim, const int* n, const double* h, int problems, const int* src, const double* omega,
+                     const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
+                     void* stream, adr_op_t* out) {
+  return create_impl(dim, n, h, problems, src, omega, kappa, tau1, gamma, params, stream, out);
+}
+
+static int update_impl(Op& op, const int* src, const double* omega, const double* kappa, const double* tau1,
+                       const double* gamma) {
+  if (!src || !omega || !kappa || !tau1 || !gamma) return fail(ADR_ERR_ARG, "null argument");
+  for (int pb = 0; pb < op.B; ++pb) {
+    if (!(omega[pb] > 0.0)) return fail(ADR_ERR_ARG, "omega must be positive");
+    for (int d = 0; d < op.dim; ++d)
+      if (src[3 * pb + d] < 0 || src[3 * pb + d] >= op.g0.n[d]) return fail(ADR_ERR_ARG, "source outside the grid");
+  }
+  for (int pb = 0; pb < op.B; ++pb) {
+    op.omegas[pb] = omega[pb];
+    for (int d = 0; d < 3; ++d) op.srcs[3 * pb + d] = d < op.dim ? src[3 * pb + d] : 0;
+  }
+  op.omega = op.omegas[0];
+  for (int d = 0; d < 3; ++d) op.src[d] = op.srcs[d];
+  op.src_index = op.src[0] + op.g0.s1 * op.src[1] + op.g0.s2 * op.src[2];
+  return setup(op, kappa, tau1, gamma);
+}
+
 int adr_operator_update(adr_op_t h, const int* src, double omega, const double* kappa, const double* tau1,
                         const double* gamma) {
-  if (!h || !src || !kappa || !tau1 || !gamma) return fail(ADR_ERR_ARG, "null argument");
+  if (!h || !src) return fail(ADR_ERR_ARG, "null argument");
   Op& op = h->op;
-  if (!(omega > 0.0)) return fail(ADR_ERR_ARG, "omega must be positive");
-  for (int d = 0; d < op.dim; ++d)
-    if (src[d] < 0 || src[d] >= op.g0.n[d]) return fail(ADR_ERR_ARG, "source outside the grid");
-  for (int d = 0; d < 3; ++d) op.src[d] = d < op.dim ? src[d] : 0;
-  op.src_index = op.src[0] + op.g0.s1 * op.src[1] + op.g0.s2 * op.src[2];
-  op.omega = omega;
-  return setup(op, kappa, tau1, gamma);
+  if (op.B != 1) return fail(ADR_ERR_STATE, "batched operator: use adr_batch_update");
+  const int s3[3] = {src[0], op.dim > 1 ? src[1] : 0, op.dim > 2 ? src[2] : 0};
+  return update_impl(op, s3, &omega, kappa, tau1, gamma);
+}
+
+int adr_batch_update(adr_op_t h, const int* src, const double* omega, const double* kappa, const double* tau1,
+                     const double* gamma) {
+  if (!h) return fail(ADR_ERR_ARG, "null argument");
+  return update_impl(h->op, src, omega, kappa, tau1, gamma);
 }
 
 long long adr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
@@ -798,6 +867,7 @@ int adr_operator_info(adr_op_t h, adr_op_info_t* info) {
     info->level[l].stencil_points = l == 0 ? 0 : (op.dim == 2 ? kPattern2 : kPattern3);
   }
   info->arena_bytes = (int64_t)op.arena_bytes;
+  info->problems = op.B;
   return ADR_OK;
 }
 
@@ -833,9 +903,9 @@ int adr_level_stencil(adr_op_t h, int level, void* out) {
   if (level < 1 || level >= L) return fail(ADR_ERR_ARG, "level must be in [1, levels)");
   const int S = op.dim == 2 ? kPattern2 : kPattern3;
   if (op.p.precond_precision == ADR_F64)
-    launch_stencil_export<double>(op.h64.lv[level].A, (double2*)out, op.h64.lv[level].g.N, S, op.st);
+    launch_stencil_export<double>(op.h64.lv[level].A, (double2*)out, op.h64.lv[level].g.N, S, op.B, op.st);
   else
-    launch_stencil_export<float>(op.h32.lv[level].A, (float2*)out, op.h32.lv[level].g.N, S, op.st);
+    launch_stencil_export<float>(op.h32.lv[level].A, (float2*)out, op.h32.lv[level].g.N, S, op.B, op.st);
   ADR_TRY(check_launch("adr_level_stencil"));
   return ADR_OK;
 }
@@ -844,7 +914,7 @@ int adr_vcycle(adr_op_t h, const void* r, void* z) {
   if (!h || !r || !z) return fail(ADR_ERR_ARG, "null argument");
   if (r == z) return fail(ADR_ERR_ARG, "z may not alias r");
   Op& op = h->op;
-  const int64_t N = op.g0.N;
+  const int64_t N = op.g0.N * op.B;
   if (op.p.precond_precision == ADR_F64) {
     launch_copy<double>((const double2*)r, op.h64.lv[0].b, N, op.st);
     ADR_TRY(run_cycle(op, op.h64));
@@ -862,92 +932,124 @@ int adr_point_source_rhs(adr_op_t h, void* q) {
   Op& op = h->op;
   double vol = 1.0;
   for (int d = 0; d < op.dim; ++d) vol *= op.h[d];
-  launch_rhs_point((double2*)q, op.g0.N, op.src_index, 1.0 / vol, op.st);
+  launch_rhs_point((double2*)q, op.g0.N, op.dyn, 1.0 / vol, op.B, op.st);
   return check_launch("adr_point_source_rhs");
 }
 
 int adr_reconstruct(adr_op_t h, const void* a, void* u) {
   if (!h || !a || !u) return fail(ADR_ERR_ARG, "null argument");
   Op& op = h->op;
-  launch_reconstruct((const double2*)a, op.tau, op.omega, (double2*)u, op.g0.N, op.st);
+  launch_reconstruct((const double2*)a, op.tau, op.dyn, (double2*)u, op.g0.N, op.B, op.st);
   return check_launch("adr_reconstruct");
 }
 
 // Flexible GMRES(m) on H_2up (adj: on H_2up^H with the cycle on A^H),
-// right-preconditioned, float64 (Sec. 3.1; readings K1-K4).
+// right-preconditioned, float64 (Sec. 3.1; readings K1-K4).  The B problems of
+// a batch iterate in lockstep, one launch per step for all of them; a problem
+// whose estimate meets its tolerance is frozen on the device (its later
+// columns are ignored by the back substitution), and a restart cycle ends
+// when every problem is frozen, broken down or the budget is spent.  info
+// receives B entries.
 static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, double tol, int maxit, adr_solve_info_t* info) {
   cudaStream_t st = op.st;
+  const int B = op.B;
   const int64_t N = op.g0.N;
+  const int64_t NB = N * B;
   const int m = op.p.restart;
   const double2* rows = adj ? op.rows2upT : op.rows2up;
+  const double* hs = op.host_scal;
 
-  launch_norm_start<double>(b, N, op.ks, nullptr, st);
-  ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
-  const double bnorm = sqrt(op.host_scal[0]);
-  adr_solve_info_t res{};
-  if (bnorm == 0.0) {
-    launch_zero<double>(a, N, st);
-    if (info) *info = res;
-    return check_launch("adr_solve");
-  }
+  launch_norm_start<double>(b, N, op.ks, nullptr, st, B);
+  launch_set_target(op.ost, op.ks.nrm2, tol, st, B);
+  ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2 * B));
+  std::vector<double> bnorm(B), beta(B), est(B);
+  std::vector<int> its_p(B, 0), status(B, ADR_OK), done(B, 0);
+  for (int pb = 0; pb < B; ++pb) bnorm[pb] = sqrt(hs[2 * pb]);
   if (use_x0) {
     launch_rows_residual(op.g0, rows, b, a, op.r, st);
   } else {
-    launch_zero<double>(a, N, st);
-    launch_copy<double>(b, op.r, N, st);
+    launch_zero<double>(a, NB, st);
+    launch_copy<double>(b, op.r, NB, st);
   }
-  launch_norm_start<double>(op.r, N, op.ks, &op.ost, st);
-  ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
-  double beta = sqrt(op.host_scal[0]);
+  launch_norm_start<double>(op.r, N, op.ks, &op.ost, st, B);
+  ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2 * B));
+  int active = 0;
+  for (int pb = 0; pb < B; ++pb) {
+    beta[pb] = sqrt(hs[2 * pb]);
+    est[pb] = bnorm[pb] > 0.0 ? beta[pb] / bnorm[pb] : 0.0;
+    done[pb] = bnorm[pb] == 0.0 || beta[pb] <= tol * bnorm[pb];
+    active += !done[pb];
+  }
   int its = 0, cycles = 0;
-  double est = beta / bnorm;
-  int status = ADR_OK;
-  while (beta > tol * bnorm && its < maxit) {
-    // op.ks.nrm2 holds |r|^2 and op.ost a fresh cycle here
-    launch_scale_inv_norm<double>(op.r, op.V, op.ks.nrm2, N, st);
+  bool nan = false;
+  std::vector<int> frozen(B);
+  while (active > 0 && its < maxit) {
+    // op.ks.nrm2 holds |r|^2 and op.ost fresh cycles here
+    launch_scale_inv_norm<double>(op.r, op.V, op.ks.nrm2, N, st, B);
+    for (int pb = 0; pb < B; ++pb) frozen[pb] = done[pb];
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      double2* vj = op.V + (int64_t)j * N;
-      double2* zj = op.Z + (int64_t)j * N;
-      double2* w = op.V + (int64_t)(j + 1) * N;  // A z_j, orthogonalised and normalised in place
+      double2* vj = op.V + (int64_t)j * NB;
+      double2* zj = op.Z + (int64_t)j * NB;
+      double2* w = op.V + (int64_t)(j + 1) * NB;  // A z_j, orthogonalised and normalised in place
       ADR_TRY(precondition(op, vj, zj, adj));
       {
         const int pk = adj ? -1 : prof_begin(op, ADR_PROF_OUTER_APPLY, st);
         launch_rows_apply(op.g0, rows, zj, w, st);
         prof_end(op, pk, st);
       }
-      launch_cgs_selective<double>(op.V, N, j + 1, w, N, op.ks, op.ost, j, op.p.reorth_eta, st);
-      launch_scale_inv_norm<double>(w, w, op.ks.nrm2, N, st);
+      launch_cgs_selective<double>(op.V, NB, j + 1, w, N, op.ks, op.ost, j, op.p.reorth_eta, st, B);
+      launch_scale_inv_norm<double>(w, w, op.ks.nrm2, N, st, B);
       ADR_TRY(check_launch("adr_solve iteration"));
-      ADR_TRY(read_scalars(op, op.ost.scal, kNumScal));
+      ADR_TRY(read_scalars(op, op.ost.scal, kNumScal * B));
       ++its;
       k = j + 1;
-      est = op.host_scal[kScalEst] / bnorm;
-      const double hn = op.host_scal[kScalHn];
-      if (!std::isfinite(est) || !std::isfinite(hn)) { status = ADR_ERR_NAN; break; }
-      if (hn == 0.0) break;
-      if (op.host_scal[kScalEst] <= tol * bnorm || its >= maxit) break;
+      int open = 0;
+      for (int pb = 0; pb < B; ++pb) {
+        if (frozen[pb]) continue;
+        const double* sc = hs + (size_t)pb * kNumScal;
+        ++its_p[pb];
+        est[pb] = sc[kScalEst] / bnorm[pb];
+        if (!std::isfinite(est[pb]) || !std::isfinite(sc[kScalHn])) { nan = true; status[pb] = ADR_ERR_NAN; }
+        if (sc[kScalHn] == 0.0 || sc[kScalEst] <= sc[kScalTarget]) frozen[pb] = 1;
+        else ++open;
+      }
+      if (nan || open == 0 || its >= maxit) break;
     }
-    if (status == ADR_ERR_NAN) break;
-    launch_backsolve(op.ost, k, st);
-    launch_combine<double>(a, op.Z, N, k, op.ost, false, N, st);
+    if (nan) break;
+    launch_backsolve(op.ost, k, st, B);
+    launch_combine<double>(a, op.Z, NB, k, op.ost, false, N, st, B);
     launch_rows_residual(op.g0, rows, b, a, op.r, st);
-    launch_norm_start<double>(op.r, N, op.ks, &op.ost, st);
-    ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 1));
-    beta = sqrt(op.host_scal[0]);
+    launch_norm_start<double>(op.r, N, op.ks, &op.ost, st, B);
+    ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2 * B));
     ++cycles;
-    if (!std::isfinite(beta)) { status = ADR_ERR_NAN; break; }
+    active = 0;
+    for (int pb = 0; pb < B; ++pb) {
+      if (done[pb]) continue;
+      beta[pb] = sqrt(hs[2 * pb]);
+      if (!std::isfinite(beta[pb])) { nan = true; status[pb] = ADR_ERR_NAN; continue; }
+      done[pb] = beta[pb] <= tol * bnorm[pb];
+      active += !done[pb];
+    }
+    if (nan) break;
   }
+  for (int pb = 0; pb < B; ++pb)
+    if (bnorm[pb] == 0.0) launch_zero<double>(a + (int64_t)pb * N, N, st);   // zero right-hand side: a = 0
   ADR_TRY(check_launch("adr_solve"));
-  res.iterations = its;
-  res.restarts = cycles;
-  res.rel_residual = beta / bnorm;
-  res.rel_estimate = est;
-  if (status == ADR_OK && beta > tol * bnorm) status = ADR_ERR_NOT_CONVERGED;
-  res.status = status;
-  if (info) *info = res;
-  if (status == ADR_ERR_NAN) return fail(ADR_ERR_NAN, "NaN or Inf in the Krylov iteration");
-  if (status == ADR_ERR_NOT_CONVERGED) return fail(ADR_ERR_NOT_CONVERGED, "iteration budget spent above the tolerance");
+  bool all_ok = true;
+  for (int pb = 0; pb < B; ++pb) {
+    adr_solve_info_t res{};
+    res.iterations = its_p[pb];
+    res.restarts = cycles;
+    res.rel_residual = bnorm[pb] > 0.0 ? beta[pb] / bnorm[pb] : 0.0;
+    res.rel_estimate = est[pb];
+    if (status[pb] == ADR_OK && !done[pb]) status[pb] = ADR_ERR_NOT_CONVERGED;
+    res.status = status[pb];
+    all_ok = all_ok && status[pb] == ADR_OK;
+    if (info) info[pb] = res;
+  }
+  if (nan) return fail(ADR_ERR_NAN, "NaN or Inf in the Krylov iteration");
+  if (!all_ok) return fail(ADR_ERR_NOT_CONVERGED, "iteration budget spent above the tolerance");
   return ADR_OK;
 }
 
@@ -1003,6 +1105,7 @@ int adr_receivers(adr_op_t h, int nrec, const int64_t* rec, const void* d, const
                   double* misfit) {
   if (!h || nrec < 0 || (nrec > 0 && (!rec || !d || !u))) return fail(ADR_ERR_ARG, "null argument");
   Op& op = h->op;
+  if (op.B != 1) return fail(ADR_ERR_STATE, "receivers are sampled for one problem at a time");
   if (rhs) launch_zero<double>((double2*)rhs, op.g0.N, op.st);
   if (nrec == 0) {
     if (misfit) *misfit = 0.0;
@@ -1023,6 +1126,7 @@ int adr_kappa_gradient(adr_op_t h, const double* kappa, const double* gamma, con
                        double* grad) {
   if (!h || !kappa || !gamma || !a || !lambda || !grad) return fail(ADR_ERR_ARG, "null argument");
   Op& op = h->op;
+  if (op.B != 1) return fail(ADR_ERR_STATE, "the gradient is accumulated for one problem at a time");
   launch_kappa_gradient(op.g0.N, op.omega, kappa, gamma, (const double2*)a, (const double2*)lambda, grad, op.st);
   return check_launch("adr_kappa_gradient");
 }

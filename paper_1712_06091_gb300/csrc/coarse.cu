@@ -11,10 +11,17 @@ namespace adr {
 static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 
-template <int DIM, typename T>
+// BT: batched launch (grid.y = problems).  The single-problem instantiation
+// carries no per-problem pointer arithmetic, which keeps these
+// register-capped kernels' spills at their unbatched level.
+template <int DIM, typename T, bool BT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  if (BT) {
+    batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
+    batch_shift(g.N, x, y);
+  }
   int i0, i1, i2;
   unravel(g, j, i0, i1, i2);
   y[j] = stencil_dot<DIM, T>(g, A, x, j, i0, i1, i2);
@@ -25,6 +32,8 @@ __global__ void k_stencil_residual(Dims g, const C<T>* __restrict__ A, const C<T
                                    const C<T>* __restrict__ x, C<T>* __restrict__ r) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
+  batch_shift(g.N, b, x, r);
   int i0, i1, i2;
   unravel(g, j, i0, i1, i2);
   r[j] = csub(b[j], stencil_dot<DIM, T>(g, A, x, j, i0, i1, i2));
@@ -35,6 +44,9 @@ __global__ void k_stencil_jacobi(Dims g, const C<T>* __restrict__ A, const C<T>*
                                  const C<T>* __restrict__ b, const C<T>* __restrict__ xin, C<T>* __restrict__ xout, T w) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
+  batch_shift(g.N, dinv, b, xout);
+  batch_shift_opt(g.N, xin);
   if (xin == nullptr) {
     xout[j] = cscale(cmul(dinv[j], b[j]), w);
     return;
@@ -52,6 +64,9 @@ __global__ void k_galerkin_stored(Dims gf, Dims gc, const C<T>* __restrict__ Af,
   constexpr int S = PatternSize<DIM>::value;
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= gc.N) return;
+  batch_shift(stencil_entries(gf.N, S), Af);
+  batch_shift(stencil_entries(gc.N, S), out);
+  batch_shift(gc.N, dinv);
   int Ii[3];
   unravel(gc, I, Ii[0], Ii[1], Ii[2]);
   C<T> acc[S];
@@ -98,6 +113,8 @@ template <int DIM, typename T>
 __global__ void k_restrict(Dims gf, Dims gc, const C<T>* __restrict__ rf, C<T>* __restrict__ rc) {
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= gc.N) return;
+  batch_shift(gf.N, rf);
+  batch_shift(gc.N, rc);
   int Ii[3];
   unravel(gc, I, Ii[0], Ii[1], Ii[2]);
   C<T> acc = czero<T>();
@@ -124,6 +141,8 @@ template <int DIM, typename T>
 __global__ void k_prolong_add(Dims gf, Dims gc, const C<T>* __restrict__ ec, C<T>* __restrict__ xf) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= gf.N) return;
+  batch_shift(gc.N, ec);
+  batch_shift(gf.N, xf);
   int ii[3];
   unravel(gf, j, ii[0], ii[1], ii[2]);
   int pj[3][2];
@@ -147,45 +166,48 @@ template <typename T>
 __global__ void k_stencil_export(const C<T>* __restrict__ A, C<T>* __restrict__ out, int64_t N, int S) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= N * S) return;
+  batch_shift(stencil_entries(N, S), A);
+  batch_shift(N * S, out);
   const int p = (int)(e / N);
   const int64_t j = e - (int64_t)p * N;
   out[e] = A[stencil_index(p, j, S)];
 }
-template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, cudaStream_t st) {
-  count_launches(1), k_stencil_export<T><<<blocks_for(N * S, 256), 256, 0, st>>>(A, out, N, S);
+template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, int B, cudaStream_t st) {
+  count_launches(1), k_stencil_export<T><<<dim3(blocks_for(N * S, 256), B), 256, 0, st>>>(A, out, N, S);
 }
-template void launch_stencil_export<double>(const double2*, double2*, int64_t, int, cudaStream_t);
-template void launch_stencil_export<float>(const float2*, float2*, int64_t, int, cudaStream_t);
+template void launch_stencil_export<double>(const double2*, double2*, int64_t, int, int, cudaStream_t);
+template void launch_stencil_export<float>(const float2*, float2*, int64_t, int, int, cudaStream_t);
 
 template <typename T> void launch_stencil_apply(const Dims& g, const C<T>* A, const C<T>* x, C<T>* y, cudaStream_t st) {
   const int th = 256;
-  if (g.dim == 2) count_launches(1), k_stencil_apply<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, A, x, y);
-  else count_launches(1), k_stencil_apply<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, A, x, y);
+  const dim3 grid(blocks_for(g.N, th), g.B);
+  if (g.dim == 2) count_launches(1), (g.B > 1 ? k_stencil_apply<2, T, true> : k_stencil_apply<2, T, false>)<<<grid, th, 0, st>>>(g, A, x, y);
+  else count_launches(1), (g.B > 1 ? k_stencil_apply<3, T, true> : k_stencil_apply<3, T, false>)<<<grid, th, 0, st>>>(g, A, x, y);
 }
 template <typename T> void launch_stencil_residual(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x, C<T>* r, cudaStream_t st) {
   const int th = 256;
-  if (g.dim == 2) count_launches(1), k_stencil_residual<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, A, b, x, r);
-  else count_launches(1), k_stencil_residual<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, A, b, x, r);
+  if (g.dim == 2) count_launches(1), k_stencil_residual<2, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, A, b, x, r);
+  else count_launches(1), k_stencil_residual<3, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, A, b, x, r);
 }
 template <typename T> void launch_stencil_jacobi(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, const C<T>* xin, C<T>* xout, T w, cudaStream_t st) {
   const int th = 256;
-  if (g.dim == 2) count_launches(1), k_stencil_jacobi<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, A, dinv, b, xin, xout, w);
-  else count_launches(1), k_stencil_jacobi<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, A, dinv, b, xin, xout, w);
+  if (g.dim == 2) count_launches(1), k_stencil_jacobi<2, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, A, dinv, b, xin, xout, w);
+  else count_launches(1), k_stencil_jacobi<3, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, A, dinv, b, xin, xout, w);
 }
 template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st) {
   const int th = 64;
-  if (gf.dim == 2) count_launches(1), k_galerkin_stored<2, T><<<blocks_for(gc.N, th), th, 0, st>>>(gf, gc, Af, Ac, dinv);
-  else count_launches(1), k_galerkin_stored<3, T><<<blocks_for(gc.N, th), th, 0, st>>>(gf, gc, Af, Ac, dinv);
+  if (gf.dim == 2) count_launches(1), k_galerkin_stored<2, T><<<dim3(blocks_for(gc.N, th), gf.B), th, 0, st>>>(gf, gc, Af, Ac, dinv);
+  else count_launches(1), k_galerkin_stored<3, T><<<dim3(blocks_for(gc.N, th), gf.B), th, 0, st>>>(gf, gc, Af, Ac, dinv);
 }
 template <typename T> void launch_restrict(const Dims& gf, const Dims& gc, const C<T>* rf, C<T>* rc, cudaStream_t st) {
   const int th = 256;
-  if (gf.dim == 2) count_launches(1), k_restrict<2, T><<<blocks_for(gc.N, th), th, 0, st>>>(gf, gc, rf, rc);
-  else count_launches(1), k_restrict<3, T><<<blocks_for(gc.N, th), th, 0, st>>>(gf, gc, rf, rc);
+  if (gf.dim == 2) count_launches(1), k_restrict<2, T><<<dim3(blocks_for(gc.N, th), gf.B), th, 0, st>>>(gf, gc, rf, rc);
+  else count_launches(1), k_restrict<3, T><<<dim3(blocks_for(gc.N, th), gf.B), th, 0, st>>>(gf, gc, rf, rc);
 }
 template <typename T> void launch_prolong_add(const Dims& gf, const Dims& gc, const C<T>* ec, C<T>* xf, cudaStream_t st) {
   const int th = 256;
-  if (gf.dim == 2) count_launches(1), k_prolong_add<2, T><<<blocks_for(gf.N, th), th, 0, st>>>(gf, gc, ec, xf);
-  else count_launches(1), k_prolong_add<3, T><<<blocks_for(gf.N, th), th, 0, st>>>(gf, gc, ec, xf);
+  if (gf.dim == 2) count_launches(1), k_prolong_add<2, T><<<dim3(blocks_for(gf.N, th), gf.B), th, 0, st>>>(gf, gc, ec, xf);
+  else count_launches(1), k_prolong_add<3, T><<<dim3(blocks_for(gf.N, th), gf.B), th, 0, st>>>(gf, gc, ec, xf);
 }
 
 #define ADR_INSTANTIATE_COARSE(T)                                                                                          \
@@ -206,11 +228,17 @@ ADR_INSTANTIATE_COARSE(float)
 // ===========================================================================
 namespace adr {
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool BT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_mr_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ z,
                                                           const C<T>* __restrict__ r, C<T>* __restrict__ w,
                                                           double2* partial, unsigned* ticket, double2* alpha) {
   __shared__ double2 sh[32 * 2];
+  if (BT) {
+    batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
+    batch_shift(g.N, z, r, w);
+    batch_shift(kPartialStride, partial);
+    batch_shift(1, ticket, alpha);
+  }
   C<T> s[2] = {czero<T>(), czero<T>()};
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < g.N; j += (int64_t)gridDim.x * blockDim.x) {
     int i0, i1, i2;
@@ -228,12 +256,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_mr_appl
   }
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool BT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_residual_dinv(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ b,
                                         const C<T>* __restrict__ x, const C<T>* __restrict__ dinv, C<T>* __restrict__ r,
                                         C<T>* __restrict__ z) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  if (BT) {
+    batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
+    batch_shift(g.N, b, x, dinv, r, z);
+  }
   int i0, i1, i2;
   unravel(g, j, i0, i1, i2);
   const C<T> rj = csub(b[j], stencil_dot<DIM, T>(g, A, x, j, i0, i1, i2));
@@ -243,7 +275,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_residua
 
 // Sums conj(V_i) w over the block for i < k into hh[i] (all threads see it after return).
 template <typename T>
-__device__ __forceinline__ void cta_dots(const C<T>* V, int64_t n, int k, const C<T>* w, double2* hh, double2* sh) {
+__device__ __forceinline__ void cta_dots(const C<T>* V, int64_t ld, int64_t n, int k, const C<T>* w, double2* hh,
+                                         double2* sh) {
   for (int c = 0; c < k; c += 4) {
     C<T> acc[4];
 #pragma unroll
@@ -252,7 +285,7 @@ __device__ __forceinline__ void cta_dots(const C<T>* V, int64_t n, int k, const 
       const C<T> we = w[e];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * n + e], we, acc[q]);
+        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * ld + e], we, acc[q]);
     }
     double2 o[4];
     block_sum_t<T, 4>(acc, sh, o);
@@ -274,6 +307,10 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
   __shared__ C<T> cv[kMaxKrylov + 1];
   __shared__ double s_scale;
   const int64_t n = g.N;
+  const int64_t ld = (int64_t)g.B * n;   // basis stride
+  batch_shift(stencil_entries(n, PatternSize<DIM>::value), A);
+  batch_shift(n, dinv, b, x, V, z);
+  st = arnoldi_at(st, blockIdx.y);
   // beta = |b|, V_0 = b / beta
   {
     C<T> s[1] = {czero<T>()};
@@ -287,6 +324,7 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
       st.scal[kScalBeta] = beta;
       st.scal[kScalEst] = beta;
       st.iscal[kIScalStop] = beta > 0.0 ? -1 : 0;
+      st.iscal[kIScalConv] = beta > 0.0 ? -1 : 0;
       s_scale = beta > 0.0 ? 1.0 / beta : 0.0;
     }
     __syncthreads();
@@ -295,8 +333,8 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
     __syncthreads();
   }
   for (int j = 0; j < k; ++j) {
-    const C<T>* vj = V + (int64_t)j * n;
-    C<T>* w = V + (int64_t)(j + 1) * n;
+    const C<T>* vj = V + (int64_t)j * ld;
+    C<T>* w = V + (int64_t)(j + 1) * ld;
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) z[e] = cmul(dinv[e], vj[e]);
     __syncthreads();
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
@@ -305,22 +343,22 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
       w[e] = stencil_dot<DIM, T>(g, A, z, e, i0, i1, i2);
     }
     __syncthreads();
-    cta_dots<T>(V, n, j + 1, w, ha, sh);
+    cta_dots<T>(V, ld, n, j + 1, w, ha, sh);
     for (int i = threadIdx.x; i <= j; i += blockDim.x) cv[i] = mk<T>((T)(-ha[i].x), (T)(-ha[i].y));
     __syncthreads();
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       C<T> acc = w[e];
-      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
+      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * ld + e], cv[i], acc);
       w[e] = acc;
     }
     __syncthreads();
-    cta_dots<T>(V, n, j + 1, w, hb, sh);
+    cta_dots<T>(V, ld, n, j + 1, w, hb, sh);
     for (int i = threadIdx.x; i <= j; i += blockDim.x) cv[i] = mk<T>((T)(-hb[i].x), (T)(-hb[i].y));
     __syncthreads();
     C<T> s[1] = {czero<T>()};
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       C<T> acc = w[e];
-      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
+      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * ld + e], cv[i], acc);
       w[e] = acc;
       s[0] = cfma_conj(acc, acc, s[0]);
     }
@@ -344,7 +382,7 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
   __syncthreads();
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
     C<T> acc = czero<T>();
-    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
+    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], cv[i], acc);
     x[e] = cmul(dinv[e], acc);
   }
 }
@@ -358,20 +396,30 @@ template <typename T>
 void launch_stencil_mr_apply(const Dims& g, const C<T>* A, const C<T>* z, const C<T>* r, C<T>* w, double2* partial,
                              unsigned* ticket, double2* alpha, cudaStream_t st) {
   const unsigned nb = mr_blocks_c(g.N);
-  if (g.dim == 2) count_launches(1), k_stencil_mr_apply<2, T><<<nb, 256, 0, st>>>(g, A, z, r, w, partial, ticket, alpha);
-  else count_launches(1), k_stencil_mr_apply<3, T><<<nb, 256, 0, st>>>(g, A, z, r, w, partial, ticket, alpha);
+  const dim3 grid(nb, g.B);
+  if (g.dim == 2)
+    count_launches(1), (g.B > 1 ? k_stencil_mr_apply<2, T, true> : k_stencil_mr_apply<2, T, false>)<<<grid, 256, 0, st>>>(
+                           g, A, z, r, w, partial, ticket, alpha);
+  else
+    count_launches(1), (g.B > 1 ? k_stencil_mr_apply<3, T, true> : k_stencil_mr_apply<3, T, false>)<<<grid, 256, 0, st>>>(
+                           g, A, z, r, w, partial, ticket, alpha);
 }
 template <typename T>
 void launch_stencil_residual_dinv(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x, const C<T>* dinv, C<T>* r,
                                   C<T>* z, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_stencil_residual_dinv<2, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, A, b, x, dinv, r, z);
-  else count_launches(1), k_stencil_residual_dinv<3, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, A, b, x, dinv, r, z);
+  const dim3 grid(blocks_for(g.N, 256), g.B);
+  if (g.dim == 2)
+    count_launches(1), (g.B > 1 ? k_stencil_residual_dinv<2, T, true> : k_stencil_residual_dinv<2, T, false>)<<<grid, 256, 0, st>>>(
+                           g, A, b, x, dinv, r, z);
+  else
+    count_launches(1), (g.B > 1 ? k_stencil_residual_dinv<3, T, true> : k_stencil_residual_dinv<3, T, false>)<<<grid, 256, 0, st>>>(
+                           g, A, b, x, dinv, r, z);
 }
 template <typename T>
 void launch_coarse_gmres_cta(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, C<T>* x, C<T>* V, C<T>* z, int k,
                              const ArnoldiState& s, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_coarse_gmres_cta<2, T><<<1, 1024, 0, st>>>(g, A, dinv, b, x, V, z, k, s);
-  else count_launches(1), k_coarse_gmres_cta<3, T><<<1, 1024, 0, st>>>(g, A, dinv, b, x, V, z, k, s);
+  if (g.dim == 2) count_launches(1), k_coarse_gmres_cta<2, T><<<dim3(1, g.B), 1024, 0, st>>>(g, A, dinv, b, x, V, z, k, s);
+  else count_launches(1), k_coarse_gmres_cta<3, T><<<dim3(1, g.B), 1024, 0, st>>>(g, A, dinv, b, x, V, z, k, s);
 }
 
 #define ADR_INSTANTIATE_COARSE2(T)                                                                                          \

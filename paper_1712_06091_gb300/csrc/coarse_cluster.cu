@@ -27,7 +27,7 @@ constexpr int kClusterMaxK = 32;   // Krylov dimension limit of this kernel
 
 // Slice sums of conj(V_i) w for i < k into red[i] (valid in all threads after the call).
 template <typename T>
-__device__ __forceinline__ void slice_dots(const C<T>* V, int64_t n, int64_t lo, int64_t hi, int k, const C<T>* w,
+__device__ __forceinline__ void slice_dots(const C<T>* V, int64_t ld, int64_t lo, int64_t hi, int k, const C<T>* w,
                                            double2* red, double2* sh) {
   for (int c = 0; c < k; c += 4) {
     C<T> acc[4];
@@ -37,7 +37,7 @@ __device__ __forceinline__ void slice_dots(const C<T>* V, int64_t n, int64_t lo,
       const C<T> we = w[e];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * n + e], we, acc[q]);
+        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * ld + e], we, acc[q]);
     }
     double2 o[4];
     block_sum_t<T, 4>(acc, sh, o);
@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_gmres_cluster(Dims g
   const int nb = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int64_t n = g.N;
+  const int64_t ld = (int64_t)g.B * n;   // basis stride (problem = blockIdx.y)
+  batch_shift(stencil_entries(n, PatternSize<DIM>::value), A);
+  batch_shift(n, dinv, b, x, V, z);
+  st = arnoldi_at(st, blockIdx.y);
   const int64_t chunk = (n + nb - 1) / nb;
   const int64_t lo = rank * chunk < n ? rank * chunk : n;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
@@ -99,13 +103,14 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_gmres_cluster(Dims g
       st.scal[kScalBeta] = beta;
       st.scal[kScalEst] = beta;
       st.iscal[kIScalStop] = beta > 0.0 ? -1 : 0;
+      st.iscal[kIScalConv] = beta > 0.0 ? -1 : 0;
     }
     const T inv = beta > 0.0 ? (T)(1.0 / beta) : T(0);
     for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) V[e] = cscale(b[e], inv);
   }
   for (int j = 0; j < k; ++j) {
-    const C<T>* vj = V + (int64_t)j * n;
-    C<T>* w = V + (int64_t)(j + 1) * n;
+    const C<T>* vj = V + (int64_t)j * ld;
+    C<T>* w = V + (int64_t)(j + 1) * ld;
     for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) z[e] = cmul(dinv[e], vj[e]);
     cl.sync();  // z complete on every slice
     for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_gmres_cluster(Dims g
     }
     __syncthreads();
     // first Gram-Schmidt pass
-    slice_dots<T>(V, n, lo, hi, j + 1, w, red[buf], sh);
+    slice_dots<T>(V, ld, lo, hi, j + 1, w, red[buf], sh);
     cl.sync();
     cluster_totals(cl, red[buf], j + 1, ha);
     buf ^= 1;
@@ -123,12 +128,12 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_gmres_cluster(Dims g
     __syncthreads();
     for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
       C<T> acc = w[e];
-      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
+      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * ld + e], cv[i], acc);
       w[e] = acc;
     }
     __syncthreads();
     // second pass
-    slice_dots<T>(V, n, lo, hi, j + 1, w, red[buf], sh);
+    slice_dots<T>(V, ld, lo, hi, j + 1, w, red[buf], sh);
     cl.sync();
     cluster_totals(cl, red[buf], j + 1, hb);
     buf ^= 1;
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_gmres_cluster(Dims g
     C<T> s[1] = {czero<T>()};
     for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
       C<T> acc = w[e];
-      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
+      for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * ld + e], cv[i], acc);
       w[e] = acc;
       s[0] = cfma_conj(acc, acc, s[0]);
     }
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_gmres_cluster(Dims g
   __syncthreads();
   for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
     C<T> acc = czero<T>();
-    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * n + e], cv[i], acc);
+    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], cv[i], acc);
     x[e] = cmul(dinv[e], acc);
   }
 }
@@ -206,7 +211,7 @@ template <typename T>
 void launch_coarse_gmres_cluster(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, C<T>* x, C<T>* V, C<T>* z,
                                  int k, const ArnoldiState& s, int cluster, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cluster, 1, 1);
+  cfg.gridDim = dim3(cluster, g.B, 1);   // one cluster per problem
   cfg.blockDim = dim3(kClusterThreads, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;

@@ -103,7 +103,7 @@ __global__ void k_source_row(Dims g, FineInputs in, const double* tau, double2* 
 void launch_coefficients(const Dims& g, const FineInputs& in, double* const gd[3], double* const td[3], double2* rho,
                          double* tau, double2* src_row, cudaStream_t st) {
   const int th = 256;
-  count_launches(1), k_coefficients<<<blocks_for(g.N, th), th, 0, st>>>(g, in, gd[0], gd[1], gd[2], td[0], td[1], td[2], rho, tau);
+  count_launches(1), k_coefficients<<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, in, gd[0], gd[1], gd[2], td[0], td[1], td[2], rho, tau);
   count_launches(1), k_source_row<<<1, 32, 0, st>>>(g, in, tau, src_row);
 }
 
@@ -121,30 +121,37 @@ void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
 // Writes the row of node j (coordinates ii) in cross form into c[1 + 4*DIM].
 template <int DIM, typename T>
 __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int64_t j, const int ii[3], C<T>* c) {
+  // Problem blockIdx.y of a batch: its coefficients start pb * N entries in,
+  // its FineDyn and source row are entry pb of theirs.
+  const int pb = blockIdx.y;
+  const int64_t jo = j + (int64_t)pb * g.N;
   if (f.rows) {
+    const C<T>* rows = f.rows + (int64_t)pb * (1 + 4 * DIM) * g.N;
 #pragma unroll
-    for (int q = 0; q < 1 + 4 * DIM; ++q) c[q] = __ldg(f.rows + (int64_t)q * g.N + j);
+    for (int q = 0; q < 1 + 4 * DIM; ++q) c[q] = __ldg(rows + (int64_t)q * g.N + j);
     return;
   }
-  if (j == f.dyn->src_index) {
-    c[0] = f.src_row[0];
+  const FineDyn* dyn = f.dyn + pb;
+  if (j == dyn->src_index) {
+    const C<T>* srow = f.src_row + (int64_t)pb * kCross3;
+    c[0] = srow[0];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) c[1 + 4 * d + q] = f.src_row[1 + 4 * d + q];
+      for (int q = 0; q < 4; ++q) c[1 + 4 * d + q] = srow[1 + 4 * d + q];
     }
     return;
   }
   bool near = true;
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) near = near && (abs(ii[d] - f.dyn->src[d]) <= f.near);
-  const C<T> rho = f.rho[j];
-  const T omega = (T)f.dyn->omega;
+  for (int d = 0; d < DIM; ++d) near = near && (abs(ii[d] - dyn->src[d]) <= f.near);
+  const C<T> rho = f.rho[jo];
+  const T omega = (T)dyn->omega;
   T cre = rho.x, cim = rho.y;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const T gd = f.g[d][j];
-    const T td = f.t[d][j];
+    const T gd = f.g[d][jo];
+    const T td = f.t[d][jo];
     const T h = f.h[d];
     const T ih2 = f.ih2[d];
     const int k = ii[d], n = g.n[d];
@@ -233,6 +240,7 @@ template <int DIM, typename T>
 __global__ void k_fine_apply(Dims g, FineOp<T> f, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift(g.N, x, y);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -245,6 +253,7 @@ __global__ void k_fine_residual(Dims g, FineOp<T> f, const C<T>* __restrict__ b,
                                 C<T>* __restrict__ r) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift(g.N, b, x, r);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -257,6 +266,8 @@ __global__ void k_fine_jacobi(Dims g, FineOp<T> f, const C<T>* __restrict__ b, c
                               C<T>* __restrict__ xout, T w) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift(g.N, b, xout);
+  batch_shift_opt(g.N, xin);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -274,6 +285,8 @@ template <int DIM, typename T>
 __global__ void k_fine_dinv(Dims g, FineOp<T> f, const C<T>* __restrict__ v, C<T>* __restrict__ z) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift(g.N, z);
+  batch_shift_opt(g.N, v);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -331,6 +344,8 @@ __global__ void k_galerkin_fine(Dims gf, Dims gc, FineOp<T> f, C<T>* __restrict_
   constexpr int S = PatternSize<DIM>::value;
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= gc.N) return;
+  batch_shift(stencil_entries(gc.N, S), out);
+  batch_shift(gc.N, dinv);
   int Ii[3];
   unravel(gc, I, Ii[0], Ii[1], Ii[2]);
   C<T> acc[S];
@@ -357,28 +372,28 @@ __global__ void k_galerkin_fine(Dims gf, Dims gc, FineOp<T> f, C<T>* __restrict_
 // ---------------------------------------------------------------------------
 template <typename T> void launch_fine_apply(const Dims& g, const FineOp<T>& f, const C<T>* x, C<T>* y, cudaStream_t st) {
   const int th = 256;
-  if (g.dim == 2) count_launches(1), k_fine_apply<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, x, y);
-  else count_launches(1), k_fine_apply<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, x, y);
+  if (g.dim == 2) count_launches(1), k_fine_apply<2, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, f, x, y);
+  else count_launches(1), k_fine_apply<3, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, f, x, y);
 }
 template <typename T> void launch_fine_residual(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* x, C<T>* r, cudaStream_t st) {
   const int th = 256;
-  if (g.dim == 2) count_launches(1), k_fine_residual<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, b, x, r);
-  else count_launches(1), k_fine_residual<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, b, x, r);
+  if (g.dim == 2) count_launches(1), k_fine_residual<2, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, f, b, x, r);
+  else count_launches(1), k_fine_residual<3, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, f, b, x, r);
 }
 template <typename T> void launch_fine_jacobi(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* xin, C<T>* xout, T w, cudaStream_t st) {
   const int th = 256;
-  if (g.dim == 2) count_launches(1), k_fine_jacobi<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, b, xin, xout, w);
-  else count_launches(1), k_fine_jacobi<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, b, xin, xout, w);
+  if (g.dim == 2) count_launches(1), k_fine_jacobi<2, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, f, b, xin, xout, w);
+  else count_launches(1), k_fine_jacobi<3, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, f, b, xin, xout, w);
 }
 template <typename T> void launch_fine_dinv(const Dims& g, const FineOp<T>& f, const C<T>* v, C<T>* z, cudaStream_t st) {
   const int th = 256;
-  if (g.dim == 2) count_launches(1), k_fine_dinv<2, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, v, z);
-  else count_launches(1), k_fine_dinv<3, T><<<blocks_for(g.N, th), th, 0, st>>>(g, f, v, z);
+  if (g.dim == 2) count_launches(1), k_fine_dinv<2, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, f, v, z);
+  else count_launches(1), k_fine_dinv<3, T><<<dim3(blocks_for(g.N, th), g.B), th, 0, st>>>(g, f, v, z);
 }
 template <typename T> void launch_galerkin_fine(const Dims& gf, const Dims& gc, const FineOp<T>& f, C<T>* stencil, C<T>* dinv, cudaStream_t st) {
   const int th = 64;
-  if (gf.dim == 2) count_launches(1), k_galerkin_fine<2, T><<<blocks_for(gc.N, th), th, 0, st>>>(gf, gc, f, stencil, dinv);
-  else count_launches(1), k_galerkin_fine<3, T><<<blocks_for(gc.N, th), th, 0, st>>>(gf, gc, f, stencil, dinv);
+  if (gf.dim == 2) count_launches(1), k_galerkin_fine<2, T><<<dim3(blocks_for(gc.N, th), gf.B), th, 0, st>>>(gf, gc, f, stencil, dinv);
+  else count_launches(1), k_galerkin_fine<3, T><<<dim3(blocks_for(gc.N, th), gf.B), th, 0, st>>>(gf, gc, f, stencil, dinv);
 }
 
 #define ADR_INSTANTIATE_FINE(T)                                                                                     \
@@ -393,29 +408,36 @@ ADR_INSTANTIATE_FINE(float)
 // ---------------------------------------------------------------------------
 // Point source, reconstruction, coefficient export
 // ---------------------------------------------------------------------------
-__global__ void k_rhs_point(double2* q, int64_t N, int64_t src, double value) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < N) q[i] = make_double2(i == src ? value : 0.0, 0.0);
-}
-void launch_rhs_point(double2* q, int64_t N, int64_t src_index, double value, cudaStream_t st) {
-  count_launches(1), k_rhs_point<<<blocks_for(N, 256), 256, 0, st>>>(q, N, src_index, value);
-}
-
-__global__ void k_reconstruct(const double2* a, const double* tau, double omega, double2* u, int64_t N) {
+__global__ void k_rhs_point(double2* q, int64_t N, const FineDyn* dyn, double value) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
+  batch_shift(N, q);
+  q[i] = make_double2(i == dyn[blockIdx.y].src_index ? value : 0.0, 0.0);
+}
+void launch_rhs_point(double2* q, int64_t N, const FineDyn* dyn, double value, int B, cudaStream_t st) {
+  count_launches(1), k_rhs_point<<<dim3(blocks_for(N, 256), B), 256, 0, st>>>(q, N, dyn, value);
+}
+
+__global__ void k_reconstruct(const double2* a, const double* tau, const FineDyn* dyn, double2* u, int64_t N) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  batch_shift(N, a, tau, u);
   double s, c;
-  sincos(-omega * tau[i], &s, &c);
+  sincos(-dyn[blockIdx.y].omega * tau[i], &s, &c);
   u[i] = cmul(a[i], make_double2(c, s));
 }
-void launch_reconstruct(const double2* a, const double* tau, double omega, double2* u, int64_t N, cudaStream_t st) {
-  count_launches(1), k_reconstruct<<<blocks_for(N, 256), 256, 0, st>>>(a, tau, omega, u, N);
+void launch_reconstruct(const double2* a, const double* tau, const FineDyn* dyn, double2* u, int64_t N, int B,
+                        cudaStream_t st) {
+  count_launches(1), k_reconstruct<<<dim3(blocks_for(N, 256), B), 256, 0, st>>>(a, tau, dyn, u, N);
 }
 
 __global__ void k_pack(Dims g, const double* g0, const double* g1, const double* g2, const double* t0, const double* t1,
                        const double* t2, const double2* rho, const double* tau, double* out) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift(g.N, g0, t0, rho, tau);
+  batch_shift_opt(g.N, g1, g2, t1, t2);
+  batch_shift((2 * g.dim + 3) * g.N, out);
   const double* gs[3] = {g0, g1, g2};
   const double* ts[3] = {t0, t1, t2};
   int k = 0;
@@ -427,7 +449,7 @@ __global__ void k_pack(Dims g, const double* g0, const double* g1, const double*
 }
 void launch_pack_coefficients(const Dims& g, const double* const gd[3], const double* const td[3], const double2* rho,
                               const double* tau, double* out, cudaStream_t st) {
-  count_launches(1), k_pack<<<blocks_for(g.N, 256), 256, 0, st>>>(g, gd[0], gd[1], gd[2], td[0], td[1], td[2], rho, tau, out);
+  count_launches(1), k_pack<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, gd[0], gd[1], gd[2], td[0], td[1], td[2], rho, tau, out);
 }
 
 }  // namespace adr
@@ -444,6 +466,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_fine_mr_apply(D
                                                        const C<T>* __restrict__ r, C<T>* __restrict__ w,
                                                        double2* partial, unsigned* ticket, double2* alpha) {
   __shared__ double2 sh[32 * 2];
+  batch_shift(g.N, z, r, w);
   C<T> s[2] = {czero<T>(), czero<T>()};
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < g.N; j += (int64_t)gridDim.x * blockDim.x) {
     int ii[3];
@@ -455,6 +478,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_fine_mr_apply(D
     s[0] = cfma_conj(wj, r[j], s[0]);
     s[1] = cfma_conj(wj, wj, s[1]);
   }
+  batch_shift(kPartialStride, partial);
+  batch_shift(1, ticket, alpha);
   double2 mine[2], tot[2];
   block_sum_t<T, 2>(s, sh, mine);
   if (last_block_total<2>(mine, partial, ticket, tot, sh) && threadIdx.x == 0) {
@@ -469,6 +494,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_fine_residual_d
                                      const C<T>* __restrict__ dinv, C<T>* __restrict__ r, C<T>* __restrict__ z) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift(g.N, b, x, dinv, r, z);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -492,14 +518,14 @@ template <typename T>
 void launch_fine_mr_apply(const Dims& g, const FineOp<T>& f, const C<T>* z, const C<T>* r, C<T>* w, double2* partial,
                           unsigned* ticket, double2* alpha, cudaStream_t st) {
   const unsigned nb = mr_blocks(g.N);
-  if (g.dim == 2) count_launches(1), k_fine_mr_apply<2, T><<<nb, 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
-  else count_launches(1), k_fine_mr_apply<3, T><<<nb, 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
+  if (g.dim == 2) count_launches(1), k_fine_mr_apply<2, T><<<dim3(nb, g.B), 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
+  else count_launches(1), k_fine_mr_apply<3, T><<<dim3(nb, g.B), 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
 }
 template <typename T>
 void launch_fine_residual_dinv(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* x, const C<T>* dinv, C<T>* r,
                                C<T>* z, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_fine_residual_dinv<2, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, b, x, dinv, r, z);
-  else count_launches(1), k_fine_residual_dinv<3, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, b, x, dinv, r, z);
+  if (g.dim == 2) count_launches(1), k_fine_residual_dinv<2, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, b, x, dinv, r, z);
+  else count_launches(1), k_fine_residual_dinv<3, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, b, x, dinv, r, z);
 }
 template void launch_fine_mr_apply<double>(const Dims&, const FineOp<double>&, const double2*, const double2*, double2*,
                                            double2*, unsigned*, double2*, cudaStream_t);
@@ -523,6 +549,7 @@ template <int DIM, typename T>
 __global__ void k_fine_store_rows(Dims g, FineOp<T> f, C<T>* __restrict__ rows) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift((1 + 4 * DIM) * g.N, rows);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -545,6 +572,8 @@ template <int DIM, typename T>
 __global__ void k_rows_apply(Dims g, const C<T>* __restrict__ rows, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift((1 + 4 * DIM) * g.N, rows);
+  batch_shift(g.N, x, y);
   y[j] = rows_dot<DIM, T>(g, rows, j, x);
 }
 
@@ -553,16 +582,18 @@ __global__ void k_rows_residual(Dims g, const C<T>* __restrict__ rows, const C<T
                                 const C<T>* __restrict__ x, C<T>* __restrict__ r) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
+  batch_shift((1 + 4 * DIM) * g.N, rows);
+  batch_shift(g.N, b, x, r);
   r[j] = csub(b[j], rows_dot<DIM, T>(g, rows, j, x));
 }
 
 void launch_fine_store_rows(const Dims& g, const FineOp<double>& f, double2* rows, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_fine_store_rows<2, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
-  else count_launches(1), k_fine_store_rows<3, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
+  if (g.dim == 2) count_launches(1), k_fine_store_rows<2, double><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, rows);
+  else count_launches(1), k_fine_store_rows<3, double><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, rows);
 }
 void launch_fine_store_rows(const Dims& g, const FineOp<float>& f, float2* rows, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_fine_store_rows<2, float><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
-  else count_launches(1), k_fine_store_rows<3, float><<<blocks_for(g.N, 256), 256, 0, st>>>(g, f, rows);
+  if (g.dim == 2) count_launches(1), k_fine_store_rows<2, float><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, rows);
+  else count_launches(1), k_fine_store_rows<3, float><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, rows);
 }
 
 // Conjugate transpose of stored cross rows: row i of A^H holds, at the slot
@@ -572,6 +603,7 @@ template <int DIM, typename T>
 __global__ void k_rows_adjoint(Dims g, const C<T>* __restrict__ rows, C<T>* __restrict__ rowsT) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
+  batch_shift((1 + 4 * DIM) * g.N, rows, rowsT);
   int ii[3];
   unravel(g, i, ii[0], ii[1], ii[2]);
   const C<T> c0 = rows[i];
@@ -595,18 +627,18 @@ __global__ void k_rows_adjoint(Dims g, const C<T>* __restrict__ rows, C<T>* __re
 }
 template <typename T>
 void launch_rows_adjoint(const Dims& g, const C<T>* rows, C<T>* rowsT, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_rows_adjoint<2, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, rowsT);
-  else count_launches(1), k_rows_adjoint<3, T><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, rowsT);
+  if (g.dim == 2) count_launches(1), k_rows_adjoint<2, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, rowsT);
+  else count_launches(1), k_rows_adjoint<3, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, rowsT);
 }
 template void launch_rows_adjoint<double>(const Dims&, const double2*, double2*, cudaStream_t);
 template void launch_rows_adjoint<float>(const Dims&, const float2*, float2*, cudaStream_t);
 void launch_rows_apply(const Dims& g, const double2* rows, const double2* x, double2* y, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_rows_apply<2, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, x, y);
-  else count_launches(1), k_rows_apply<3, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, x, y);
+  if (g.dim == 2) count_launches(1), k_rows_apply<2, double><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, x, y);
+  else count_launches(1), k_rows_apply<3, double><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, x, y);
 }
 void launch_rows_residual(const Dims& g, const double2* rows, const double2* b, const double2* x, double2* r, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_rows_residual<2, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, b, x, r);
-  else count_launches(1), k_rows_residual<3, double><<<blocks_for(g.N, 256), 256, 0, st>>>(g, rows, b, x, r);
+  if (g.dim == 2) count_launches(1), k_rows_residual<2, double><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, b, x, r);
+  else count_launches(1), k_rows_residual<3, double><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, b, x, r);
 }
 
 }  // namespace adr

@@ -1,11 +1,13 @@
-// Krylov building blocks: deterministic multi-dot reductions (warp shuffles,
-// then a fixed-order pass over per-block partials), multi-AXPY, scaling, and
-// the small single-thread kernels that keep the Arnoldi Hessenberg matrix,
-// its Givens rotations and the least-squares right-hand side on the device.
+// Krylov building blocks: fused Gram-Schmidt passes with deterministic
+// last-block reductions (warp shuffles, then a fixed-order pass over
+// per-block partials), scaling, the combination x += Z y, and the
+// single-thread pieces that keep the Arnoldi Hessenberg matrix, its Givens
+// rotations and the least-squares right-hand side on the device.
 //
-// These serve the outer flexible GMRES, the inner FGMRES of the K-cycle
+// They serve the outer flexible GMRES, the inner FGMRES of the K-cycle
 // (Alg. Kcycle), the fixed-count Jacobi-preconditioned GMRES of the coarsest
-// grid and the minimal-residual Jacobi relaxation (Sec. 3.1).
+// grid and the minimal-residual Jacobi relaxation (Sec. 3.1).  Every kernel
+// handles a batch of problems with grid.y = problems (see krylov.cuh).
 #include "krylov.cuh"
 #include "reduce.cuh"
 #include "krylov_dev.cuh"
@@ -21,103 +23,9 @@ int reduction_blocks(int64_t n) {
   return (int)b;
 }
 
-__device__ __forceinline__ double2 warp_sum(double2 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
-
-// Block-wide sum in a fixed order; result valid in thread 0.
-__device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    v = lane < nw ? sh[lane] : make_double2(0.0, 0.0);
-    v = warp_sum(v);
-  }
-  return v;
-}
-
-constexpr int kDotChunk = 4;
-
-// partial[b * k + i] = sum over this block's elements of conj(V_i) w
-template <typename T>
-__global__ void __launch_bounds__(256) k_dots_partial(const C<T>* __restrict__ V, int64_t ld, int k,
-                                                      const C<T>* __restrict__ w, int64_t n, double2* __restrict__ partial) {
-  __shared__ double2 sh[32];
-  for (int c = 0; c < k; c += kDotChunk) {
-    C<T> acc[kDotChunk];
-#pragma unroll
-    for (int q = 0; q < kDotChunk; ++q) acc[q] = czero<T>();
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-      const C<T> we = w[e];
-#pragma unroll
-      for (int q = 0; q < kDotChunk; ++q)
-        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * ld + e], we, acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < kDotChunk; ++q) {
-      if (c + q >= k) break;
-      const double2 s = block_sum(make_double2((double)acc[q].x, (double)acc[q].y), sh);
-      if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * k + c + q] = s;
-    }
-  }
-}
-
-// out[i] = sum_b partial[b * k + i]  (one block, fixed order)
-__global__ void __launch_bounds__(256) k_dots_final(const double2* __restrict__ partial, int nb, int k,
-                                                    double2* __restrict__ out, int accumulate) {
-  __shared__ double2 sh[32];
-  for (int i = 0; i < k; ++i) {
-    double2 v = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      v.x += partial[(int64_t)b * k + i].x;
-      v.y += partial[(int64_t)b * k + i].y;
-    }
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0) {
-      if (accumulate) { out[i].x += v.x; out[i].y += v.y; }
-      else out[i] = v;
-    }
-  }
-}
-
-template <typename T>
-void launch_dots(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, double2* partial, double2* out,
-                 cudaStream_t st, bool accumulate) {
-  const int nb = reduction_blocks(n);
-  count_launches(1), k_dots_partial<T><<<nb, 256, 0, st>>>(V, ld, k, w, n, partial);
-  count_launches(1), k_dots_final<<<1, 256, 0, st>>>(partial, nb, k, out, accumulate ? 1 : 0);
-}
-
-// w += sign * sum_i V_i coef[i]
-template <typename T>
-__global__ void k_axpy_multi(C<T>* __restrict__ w, const C<T>* __restrict__ V, int64_t ld, int k,
-                             const double2* __restrict__ coef, double sign, int64_t n) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  C<T> acc = w[e];
-  for (int i = 0; i < k; ++i) {
-    const double2 cd = coef[i];
-    const C<T> c = mk<T>((T)(sign * cd.x), (T)(sign * cd.y));
-    acc = cfma(V[(int64_t)i * ld + e], c, acc);
-  }
-  w[e] = acc;
-}
-template <typename T>
-void launch_axpy_multi(C<T>* w, const C<T>* V, int64_t ld, int k, const double2* coef, double sign, int64_t n,
-                       cudaStream_t st) {
-  if (k <= 0) return;
-  count_launches(1), k_axpy_multi<T><<<blocks_for(n, 256), 256, 0, st>>>(w, V, ld, k, coef, sign, n);
-}
-
+// ---------------------------------------------------------------------------
+// Elementwise
+// ---------------------------------------------------------------------------
 // out = w / |w| with the reciprocal norm precomputed in nrm2->y by the kernel
 // that reduced nrm2->x (zero if the norm vanishes): no per-thread float64
 // square root or division.
@@ -125,12 +33,13 @@ template <typename T>
 __global__ void k_scale_inv_norm(const C<T>* w, C<T>* out, const double2* __restrict__ nrm2, int64_t n) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const T inv = (T)nrm2->y;
+  batch_shift(n, w, out);
+  const T inv = (T)nrm2[blockIdx.y].y;
   out[e] = cscale(w[e], inv);
 }
 template <typename T>
-void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, int64_t n, cudaStream_t st) {
-  count_launches(1), k_scale_inv_norm<T><<<blocks_for(n, 256), 256, 0, st>>>(w, out, nrm2, n);
+void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, int64_t n, cudaStream_t st, int B) {
+  count_launches(1), k_scale_inv_norm<T><<<dim3(blocks_for(n, 256), B), 256, 0, st>>>(w, out, nrm2, n);
 }
 
 template <typename T>
@@ -140,6 +49,15 @@ __global__ void k_copy(const C<T>* __restrict__ a, C<T>* __restrict__ b, int64_t
 }
 template <typename T> void launch_copy(const C<T>* a, C<T>* b, int64_t n, cudaStream_t st) {
   count_launches(1), k_copy<T><<<blocks_for(n, 256), 256, 0, st>>>(a, b, n);
+}
+
+template <typename T>
+__global__ void k_zero(C<T>* __restrict__ a, int64_t n) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < n) a[e] = czero<T>();
+}
+template <typename T> void launch_zero(C<T>* a, int64_t n, cudaStream_t st) {
+  count_launches(1), k_zero<T><<<blocks_for(n, 256), 256, 0, st>>>(a, n);
 }
 
 template <typename Ts, typename Td>
@@ -161,118 +79,33 @@ template <typename T> void launch_cmul_vec(const C<T>* a, const C<T>* b, C<T>* o
 }
 
 // ---------------------------------------------------------------------------
-// Small device-side Arnoldi state (one thread)
+// Single-thread Arnoldi pieces (one block per problem)
 // ---------------------------------------------------------------------------
-__global__ void k_cycle_start(ArnoldiState st, const double2* nrm2) {
-  if (threadIdx.x != 0) return;
-  const double beta = sqrt(nrm2->x);
-  for (int i = 0; i <= st.m; ++i) st.g[i] = make_double2(0.0, 0.0);
-  st.g[0] = make_double2(beta, 0.0);
-  st.scal[kScalBeta] = beta;
-  st.scal[kScalEst] = beta;
-  st.iscal[kIScalStop] = beta > 0.0 ? -1 : 0;  // k at exact breakdown, -1 while none
-}
-
-// Column j of the Hessenberg matrix from the two Gram-Schmidt passes and the
-// squared norm of the orthogonalised vector; rotations and g updated.
-__global__ void k_arnoldi_column(ArnoldiState st, int j, const double2* ha, const double2* hb, const double2* nrm2) {
-  if (threadIdx.x != 0) return;
-  arnoldi_column_dev(st, j, ha, hb, nrm2->x);
-}
-
-// y = R^{-1} g for the leading k x k block (k = breakdown index if any).
 __global__ void k_backsolve(ArnoldiState st, int k) {
   if (threadIdx.x != 0) return;
-  backsolve_dev(st, k);
+  backsolve_dev(arnoldi_at(st, blockIdx.y), k);
+}
+void launch_backsolve(const ArnoldiState& s, int k, cudaStream_t st, int B) {
+  count_launches(1), k_backsolve<<<dim3(1, B), 32, 0, st>>>(s, k);
 }
 
-// alpha = (w^H r) / (w^H w) from d[0] = w^H r, d[1] = w^H w (0 if w = 0).
-__global__ void k_mr_alpha(const double2* d, double2* alpha) {
+__global__ void k_set_target(ArnoldiState st, const double2* nrm2, double tol) {
   if (threadIdx.x != 0) return;
-  const double den = d[1].x;
-  *alpha = den > 0.0 ? make_double2(d[0].x / den, d[0].y / den) : make_double2(0.0, 0.0);
+  const ArnoldiState s = arnoldi_at(st, blockIdx.y);
+  s.scal[kScalTarget] = tol * sqrt(nrm2[blockIdx.y].x);
 }
-
-void launch_cycle_start(const ArnoldiState& s, const double2* nrm2, cudaStream_t st) { count_launches(1), k_cycle_start<<<1, 32, 0, st>>>(s, nrm2); }
-void launch_arnoldi_column(const ArnoldiState& s, int j, const double2* ha, const double2* hb, const double2* nrm2, cudaStream_t st) {
-  count_launches(1), k_arnoldi_column<<<1, 32, 0, st>>>(s, j, ha, hb, nrm2);
+void launch_set_target(const ArnoldiState& s, const double2* nrm2, double tol, cudaStream_t st, int B) {
+  count_launches(1), k_set_target<<<dim3(1, B), 32, 0, st>>>(s, nrm2, tol);
 }
-void launch_backsolve(const ArnoldiState& s, int k, cudaStream_t st) { count_launches(1), k_backsolve<<<1, 32, 0, st>>>(s, k); }
-void launch_mr_alpha(const double2* d, double2* alpha, cudaStream_t st) { count_launches(1), k_mr_alpha<<<1, 32, 0, st>>>(d, alpha); }
-
-// Two dots against one vector a: d[0] = a^H b, d[1] = a^H c.
-template <typename T>
-__global__ void __launch_bounds__(256) k_dot2_partial(const C<T>* __restrict__ a, const C<T>* __restrict__ b,
-                                                      const C<T>* __restrict__ c, int64_t n, double2* __restrict__ partial) {
-  __shared__ double2 sh[32];
-  C<T> s0 = czero<T>(), s1 = czero<T>();
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const C<T> ae = a[e];
-    s0 = cfma_conj(ae, b[e], s0);
-    s1 = cfma_conj(ae, c[e], s1);
-  }
-  double2 v0 = block_sum(make_double2((double)s0.x, (double)s0.y), sh);
-  if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 2 + 0] = v0;
-  double2 v1 = block_sum(make_double2((double)s1.x, (double)s1.y), sh);
-  if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 2 + 1] = v1;
-}
-template <typename T>
-void launch_dot2(const C<T>* a, const C<T>* b, const C<T>* c, int64_t n, double2* partial, double2* out, cudaStream_t st) {
-  const int nb = reduction_blocks(n);
-  count_launches(1), k_dot2_partial<T><<<nb, 256, 0, st>>>(a, b, c, n, partial);
-  count_launches(1), k_dots_final<<<1, 256, 0, st>>>(partial, nb, 2, out, 0);
-}
-
-// x += alpha z ; r -= alpha w ; (optional) znext = dinv .* r
-template <typename T>
-__global__ void k_mr_update(C<T>* __restrict__ x, const C<T>* __restrict__ z, C<T>* __restrict__ r,
-                            const C<T>* __restrict__ w, const double2* __restrict__ alpha, const C<T>* __restrict__ dinv,
-                            C<T>* __restrict__ znext, int64_t n) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const C<T> al = mk<T>((T)alpha->x, (T)alpha->y);
-  x[e] = cfma(al, z[e], x[e]);
-  const C<T> rn = csub(r[e], cmul(al, w[e]));
-  r[e] = rn;
-  if (znext) znext[e] = cmul(dinv[e], rn);
-}
-template <typename T>
-void launch_mr_update(C<T>* x, const C<T>* z, C<T>* r, const C<T>* w, const double2* alpha, const C<T>* dinv, C<T>* znext,
-                      int64_t n, cudaStream_t st) {
-  count_launches(1), k_mr_update<T><<<blocks_for(n, 256), 256, 0, st>>>(x, z, r, w, alpha, dinv, znext, n);
-}
-
-template <typename T>
-__global__ void k_zero(C<T>* __restrict__ a, int64_t n) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < n) a[e] = czero<T>();
-}
-template <typename T> void launch_zero(C<T>* a, int64_t n, cudaStream_t st) {
-  count_launches(1), k_zero<T><<<blocks_for(n, 256), 256, 0, st>>>(a, n);
-}
-
-#define ADR_INSTANTIATE_KRYLOV(T)                                                                                    \
-  template void launch_dots<T>(const C<T>*, int64_t, int, const C<T>*, int64_t, double2*, double2*, cudaStream_t, bool); \
-  template void launch_axpy_multi<T>(C<T>*, const C<T>*, int64_t, int, const double2*, double, int64_t, cudaStream_t); \
-  template void launch_scale_inv_norm<T>(const C<T>*, C<T>*, const double2*, int64_t, cudaStream_t);                  \
-  template void launch_copy<T>(const C<T>*, C<T>*, int64_t, cudaStream_t);                                            \
-  template void launch_cmul_vec<T>(const C<T>*, const C<T>*, C<T>*, int64_t, cudaStream_t);                           \
-  template void launch_dot2<T>(const C<T>*, const C<T>*, const C<T>*, int64_t, double2*, double2*, cudaStream_t);     \
-  template void launch_mr_update<T>(C<T>*, const C<T>*, C<T>*, const C<T>*, const double2*, const C<T>*, C<T>*, int64_t, cudaStream_t); \
-  template void launch_zero<T>(C<T>*, int64_t, cudaStream_t);
-ADR_INSTANTIATE_KRYLOV(double)
-ADR_INSTANTIATE_KRYLOV(float)
-template void launch_ccast<double, float>(const C<double>*, C<float>*, int64_t, cudaStream_t);
-template void launch_ccast<float, double>(const C<float>*, C<double>*, int64_t, cudaStream_t);
 
 // ===========================================================================
 // Fused Arnoldi / Krylov kernels (one launch per pass, deterministic
 // last-block reductions; see reduce.cuh)
 // ===========================================================================
 
-// Block sums of k values held per thread in chunks; the block's k totals are
-// left in blk[0..k) (shared memory).  acc_fn(i) returns thread's value i.
-// Then the last block reduces partials over blocks into out[0..k).
+// Thread 0 holds the block's k sums in blk[0..k); writes them as this block's
+// partials; the last block of the problem to arrive reduces them in block
+// order into out[0..k) and resets the ticket.  Returns true in that block.
 __device__ __forceinline__ bool last_block_rt(int k, const double2* blk, double2* partial, unsigned* ticket, double2* out,
                                               double2* sh) {
   __shared__ bool is_last;
@@ -324,37 +157,8 @@ __device__ __forceinline__ void block_dots(const C<T>* __restrict__ V, int64_t l
   }
 }
 
-// pass 1: ha = V^H w
-template <typename T>
-__global__ void __launch_bounds__(256) k_cgs_pass1(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w, int64_t n,
-                                                   double2* partial, unsigned* ticket, double2* ha) {
-  __shared__ double2 sh[32 * 4];
-  __shared__ double2 blk[kMaxKrylov + 1];
-  block_dots<T>(V, ld, k, w, n, blk, sh);
-  last_block_rt(k, blk, partial, ticket, ha, sh);
-}
-
-// pass 2: w -= V ha ; hb = V^H w
-template <typename T>
-__global__ void __launch_bounds__(256) k_cgs_pass2(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
-                                                   const double2* __restrict__ ha, double2* partial, unsigned* ticket,
-                                                   double2* hb) {
-  __shared__ double2 sh[32 * 4];
-  __shared__ double2 blk[kMaxKrylov + 1];
-  __shared__ C<T> coef[kMaxKrylov + 1];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-ha[i].x), (T)(-ha[i].y));
-  __syncthreads();
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    C<T> acc = w[e];
-    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
-    w[e] = acc;
-  }
-  block_dots<T>(V, ld, k, w, n, blk, sh);   // each thread re-reads only its own elements of w
-  last_block_rt(k, blk, partial, ticket, hb, sh);
-}
-
-// w -= V c ; |w|^2 reduced over the grid.  Returns true in the last block
-// (total in nrm2->x, valid in thread 0).
+// w -= V c ; |w|^2 reduced over the problem's blocks.  Returns true in the
+// last block (total in nrm2->x, valid in thread 0).
 template <typename T>
 __device__ __forceinline__ bool update_norm(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
                                             const double2* c, double2* partial, unsigned* ticket, double2* nrm2) {
@@ -377,15 +181,48 @@ __device__ __forceinline__ bool update_norm(const C<T>* __restrict__ V, int64_t 
   return last_block_rt(1, blk, partial, ticket, nrm2, sh);
 }
 
+// pass 1: ha = V^H w
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgs_pass1(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w, int64_t n,
+                                                   KrylovScratch s) {
+  __shared__ double2 sh[32 * 4];
+  __shared__ double2 blk[kMaxKrylov + 1];
+  batch_shift(n, V, w);
+  s = scratch_at(s, blockIdx.y);
+  block_dots<T>(V, ld, k, w, n, blk, sh);
+  last_block_rt(k, blk, s.partial, s.ticket, s.ha, sh);
+}
+
+// pass 2: w -= V ha ; hb = V^H w
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgs_pass2(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+                                                   KrylovScratch s) {
+  __shared__ double2 sh[32 * 4];
+  __shared__ double2 blk[kMaxKrylov + 1];
+  __shared__ C<T> coef[kMaxKrylov + 1];
+  batch_shift(n, V, w);
+  s = scratch_at(s, blockIdx.y);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-s.ha[i].x), (T)(-s.ha[i].y));
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    C<T> acc = w[e];
+    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
+    w[e] = acc;
+  }
+  block_dots<T>(V, ld, k, w, n, blk, sh);   // each thread re-reads only its own elements of w
+  last_block_rt(k, blk, s.partial, s.ticket, s.hb, sh);
+}
+
 // pass 3: w -= V hb ; |w|^2 ; Arnoldi column j and Givens rotation (last block)
 template <typename T>
 __global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
-                                                   const double2* __restrict__ ha, const double2* __restrict__ hb,
-                                                   double2* partial, unsigned* ticket, double2* nrm2, ArnoldiState st, int j) {
-  if (update_norm<T>(V, ld, k, w, n, hb, partial, ticket, nrm2) && threadIdx.x == 0) {
-    const double s2t = nrm2->x;
-    nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
-    if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, s2t);
+                                                   KrylovScratch s, ArnoldiState st, int j) {
+  batch_shift(n, V, w);
+  s = scratch_at(s, blockIdx.y);
+  if (update_norm<T>(V, ld, k, w, n, s.hb, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
+    const double s2t = s.nrm2->x;
+    s.nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
+    if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, s2t);
   }
 }
 
@@ -401,9 +238,11 @@ __global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, i
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_sgs_dots_norm(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w,
-                                                       int64_t n, double2* partial, unsigned* ticket, double2* ha) {
+                                                       int64_t n, KrylovScratch s) {
   __shared__ double2 sh[32 * 5];
   __shared__ double2 blk[kMaxKrylov + 2];
+  batch_shift(n, V, w);
+  s = scratch_at(s, blockIdx.y);
   for (int c = 0; c < k; c += 4) {
     C<T> acc[5];
 #pragma unroll
@@ -423,55 +262,59 @@ __global__ void __launch_bounds__(256) k_sgs_dots_norm(const C<T>* __restrict__ 
     }
     __syncthreads();
   }
-  last_block_rt(k + 1, blk, partial, ticket, ha, sh);
+  last_block_rt(k + 1, blk, s.partial, s.ticket, s.ha, sh);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sgs_update_test(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
-                                                         double2* ha, double2* hb, double2* partial, unsigned* ticket,
-                                                         double2* nrm2, ArnoldiState st, int j, double eta2) {
-  if (update_norm<T>(V, ld, k, w, n, ha, partial, ticket, nrm2) && threadIdx.x == 0) {
-    const double t = nrm2->x;
-    if (t >= eta2 * ha[k].x) {
-      ha[k].y = 0.0;
-      for (int i = 0; i < k; ++i) hb[i] = make_double2(0.0, 0.0);
-      nrm2->y = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
-      if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, t);
+                                                         KrylovScratch s, ArnoldiState st, int j, double eta2) {
+  batch_shift(n, V, w);
+  s = scratch_at(s, blockIdx.y);
+  if (update_norm<T>(V, ld, k, w, n, s.ha, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
+    const double t = s.nrm2->x;
+    if (t >= eta2 * s.ha[k].x) {
+      s.ha[k].y = 0.0;
+      for (int i = 0; i < k; ++i) s.hb[i] = make_double2(0.0, 0.0);
+      s.nrm2->y = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+      if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, t);
     } else {
-      ha[k].y = 1.0;
+      s.ha[k].y = 1.0;
     }
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sgs_reorth_dots(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w,
-                                                         int64_t n, const double2* ha, double2* partial, unsigned* ticket,
-                                                         double2* hb) {
-  if (ha[k].y == 0.0) return;   // uniform over the grid
+                                                         int64_t n, KrylovScratch s) {
+  s = scratch_at(s, blockIdx.y);
+  if (s.ha[k].y == 0.0) return;   // uniform over the problem's blocks
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[kMaxKrylov + 1];
+  batch_shift(n, V, w);
   block_dots<T>(V, ld, k, w, n, blk, sh);
-  last_block_rt(k, blk, partial, ticket, hb, sh);
+  last_block_rt(k, blk, s.partial, s.ticket, s.hb, sh);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sgs_reorth_update(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
-                                                           const double2* ha, const double2* hb, double2* partial,
-                                                           unsigned* ticket, double2* nrm2, ArnoldiState st, int j) {
-  if (ha[k].y == 0.0) return;   // uniform over the grid
-  if (update_norm<T>(V, ld, k, w, n, hb, partial, ticket, nrm2) && threadIdx.x == 0) {
-    const double s2t = nrm2->x;
-    nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
-    if (st.m > 0) arnoldi_column_dev(st, j, ha, hb, s2t);
+                                                           KrylovScratch s, ArnoldiState st, int j) {
+  s = scratch_at(s, blockIdx.y);
+  if (s.ha[k].y == 0.0) return;   // uniform over the problem's blocks
+  batch_shift(n, V, w);
+  if (update_norm<T>(V, ld, k, w, n, s.hb, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
+    const double s2t = s.nrm2->x;
+    s.nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
+    if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, s2t);
   }
 }
 
 // |b|^2 and (optionally) the start of an Arnoldi cycle with beta = |b|.
 template <typename T>
-__global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, double2* partial, unsigned* ticket,
-                                                    double2* nrm2, ArnoldiState st, int start) {
+__global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, KrylovScratch s, ArnoldiState st, int start) {
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[1];
+  batch_shift(n, b);
+  s = scratch_at(s, blockIdx.y);
   C<T> s2[1] = {czero<T>()};
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     s2[0] = cfma_conj(b[e], b[e], s2[0]);
@@ -479,15 +322,17 @@ __global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, do
   block_sum_t<T, 1>(s2, sh, o);
   if (threadIdx.x == 0) blk[0] = o[0];
   __syncthreads();
-  if (last_block_rt(1, blk, partial, ticket, nrm2, sh) && threadIdx.x == 0) {
-    const double beta = sqrt(nrm2->x);
-    nrm2->y = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (last_block_rt(1, blk, s.partial, s.ticket, s.nrm2, sh) && threadIdx.x == 0) {
+    const double beta = sqrt(s.nrm2->x);
+    s.nrm2->y = beta > 0.0 ? 1.0 / beta : 0.0;
     if (!start) return;
-    for (int i = 0; i <= st.m; ++i) st.g[i] = make_double2(0.0, 0.0);
-    st.g[0] = make_double2(beta, 0.0);
-    st.scal[kScalBeta] = beta;
-    st.scal[kScalEst] = beta;
-    st.iscal[kIScalStop] = beta > 0.0 ? -1 : 0;
+    const ArnoldiState a = arnoldi_at(st, blockIdx.y);
+    for (int i = 0; i <= a.m; ++i) a.g[i] = make_double2(0.0, 0.0);
+    a.g[0] = make_double2(beta, 0.0);
+    a.scal[kScalBeta] = beta;
+    a.scal[kScalEst] = beta;
+    a.iscal[kIScalStop] = beta > 0.0 ? -1 : 0;
+    a.iscal[kIScalConv] = beta <= a.scal[kScalTarget] ? 0 : -1;
   }
 }
 
@@ -495,10 +340,12 @@ __global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, do
 template <typename T>
 __global__ void k_combine(C<T>* x, const C<T>* __restrict__ Z, int64_t ld, int k, ArnoldiState st, int assign, int64_t n) {
   __shared__ C<T> coef[kMaxKrylov];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)st.y[i].x, (T)st.y[i].y);
+  const ArnoldiState a = arnoldi_at(st, blockIdx.y);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)a.y[i].x, (T)a.y[i].y);
   __syncthreads();
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
+  batch_shift(n, x, Z);
   C<T> acc = assign ? czero<T>() : x[e];
   for (int i = 0; i < k; ++i) acc = cfma(Z[(int64_t)i * ld + e], coef[i], acc);
   x[e] = acc;
@@ -511,7 +358,10 @@ __global__ void k_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_
                              C<T>* znext, int x_zero, int64_t n) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const C<T> al = mk<T>((T)alpha->x, (T)alpha->y);
+  batch_shift(n, x, z, r_src, r_dst, w, dinv);
+  batch_shift_opt(n, znext);
+  const double2 ad = alpha[blockIdx.y];
+  const C<T> al = mk<T>((T)ad.x, (T)ad.y);
   x[e] = cfma(al, z[e], x_zero ? czero<T>() : x[e]);
   const C<T> rn = csub(r_src[e], cmul(al, w[e]));
   r_dst[e] = rn;
@@ -520,52 +370,58 @@ __global__ void k_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_
 
 template <typename T>
 void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s, const ArnoldiState& st, int j,
-                 cudaStream_t stream) {
-  const int nb = reduction_blocks(n);
-  count_launches(1), k_cgs_pass1<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.partial, s.ticket, s.ha);
-  count_launches(1), k_cgs_pass2<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.partial, s.ticket, s.hb);
-  count_launches(1), k_cgs_pass3<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.hb, s.partial, s.ticket, s.nrm2, st, j);
+                 cudaStream_t stream, int B) {
+  const dim3 grid(reduction_blocks(n), B);
+  count_launches(1), k_cgs_pass1<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
+  count_launches(1), k_cgs_pass2<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
+  count_launches(1), k_cgs_pass3<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j);
 }
 template <typename T>
 void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
-                          const ArnoldiState& st, int j, double eta, cudaStream_t stream) {
+                          const ArnoldiState& st, int j, double eta, cudaStream_t stream, int B) {
   if (!(eta < 1.0)) {
-    launch_cgs2<T>(V, ld, k, w, n, s, st, j, stream);
+    launch_cgs2<T>(V, ld, k, w, n, s, st, j, stream, B);
     return;
   }
-  const int nb = reduction_blocks(n);
-  count_launches(1), k_sgs_dots_norm<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.partial, s.ticket, s.ha);
-  count_launches(1), k_sgs_update_test<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.hb, s.partial, s.ticket, s.nrm2,
-                                                                    st, j, eta * eta);
-  count_launches(1), k_sgs_reorth_dots<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.partial, s.ticket, s.hb);
-  count_launches(1), k_sgs_reorth_update<T><<<nb, 256, 0, stream>>>(V, ld, k, w, n, s.ha, s.hb, s.partial, s.ticket,
-                                                                      s.nrm2, st, j);
+  const dim3 grid(reduction_blocks(n), B);
+  count_launches(1), k_sgs_dots_norm<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
+  count_launches(1), k_sgs_update_test<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j, eta * eta);
+  count_launches(1), k_sgs_reorth_dots<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
+  count_launches(1), k_sgs_reorth_update<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j);
 }
 template <typename T>
-void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream) {
-  const int nb = reduction_blocks(n);
+void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream, int B) {
   ArnoldiState dummy{};
-  count_launches(1), k_norm_start<T><<<nb, 256, 0, stream>>>(b, n, s.partial, s.ticket, s.nrm2, st ? *st : dummy, st ? 1 : 0);
+  count_launches(1), k_norm_start<T><<<dim3(reduction_blocks(n), B), 256, 0, stream>>>(b, n, s, st ? *st : dummy, st ? 1 : 0);
 }
 template <typename T>
-void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n, cudaStream_t stream) {
-  count_launches(1), k_combine<T><<<blocks_for(n, 256), 256, 0, stream>>>(x, Z, ld, k, st, assign ? 1 : 0, n);
+void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n,
+                    cudaStream_t stream, int B) {
+  count_launches(1), k_combine<T><<<dim3(blocks_for(n, 256), B), 256, 0, stream>>>(x, Z, ld, k, st, assign ? 1 : 0, n);
 }
 template <typename T>
 void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, const C<T>* w, const double2* alpha,
-                       const C<T>* dinv, C<T>* znext, bool x_zero, int64_t n, cudaStream_t stream) {
-  count_launches(1), k_mr_update2<T><<<blocks_for(n, 256), 256, 0, stream>>>(x, z, r_src, r_dst, w, alpha, dinv, znext,
-                                                                               x_zero ? 1 : 0, n);
+                       const C<T>* dinv, C<T>* znext, bool x_zero, int64_t n, cudaStream_t stream, int B) {
+  count_launches(1), k_mr_update2<T><<<dim3(blocks_for(n, 256), B), 256, 0, stream>>>(x, z, r_src, r_dst, w, alpha, dinv,
+                                                                                       znext, x_zero ? 1 : 0, n);
 }
 
-#define ADR_INSTANTIATE_FUSED(T)                                                                                           \
-  template void launch_cgs2<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, int, cudaStream_t); \
-  template void launch_cgs_selective<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, int, \
-                                        double, cudaStream_t);                                                              \
-  template void launch_norm_start<T>(const C<T>*, int64_t, const KrylovScratch&, const ArnoldiState*, cudaStream_t);        \
-  template void launch_combine<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, bool, int64_t, cudaStream_t);     \
-  template void launch_mr_update2<T>(C<T>*, const C<T>*, const C<T>*, C<T>*, const C<T>*, const double2*, const C<T>*, C<T>*, bool, int64_t, cudaStream_t);
-ADR_INSTANTIATE_FUSED(double)
-ADR_INSTANTIATE_FUSED(float)
+#define ADR_INSTANTIATE_KRYLOV(T)                                                                                        \
+  template void launch_scale_inv_norm<T>(const C<T>*, C<T>*, const double2*, int64_t, cudaStream_t, int);               \
+  template void launch_copy<T>(const C<T>*, C<T>*, int64_t, cudaStream_t);                                               \
+  template void launch_zero<T>(C<T>*, int64_t, cudaStream_t);                                                            \
+  template void launch_cmul_vec<T>(const C<T>*, const C<T>*, C<T>*, int64_t, cudaStream_t);                              \
+  template void launch_cgs2<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, int, \
+                               cudaStream_t, int);                                                                       \
+  template void launch_cgs_selective<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&,                 \
+                                        const ArnoldiState&, int, double, cudaStream_t, int);                            \
+  template void launch_norm_start<T>(const C<T>*, int64_t, const KrylovScratch&, const ArnoldiState*, cudaStream_t, int); \
+  template void launch_combine<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, bool, int64_t, cudaStream_t, int); \
+  template void launch_mr_update2<T>(C<T>*, const C<T>*, const C<T>*, C<T>*, const C<T>*, const double2*, const C<T>*,    \
+                                     C<T>*, bool, int64_t, cudaStream_t, int);
+ADR_INSTANTIATE_KRYLOV(double)
+ADR_INSTANTIATE_KRYLOV(float)
+template void launch_ccast<double, float>(const C<double>*, C<float>*, int64_t, cudaStream_t);
+template void launch_ccast<float, double>(const C<float>*, C<double>*, int64_t, cudaStream_t);
 
 }  // namespace adr

@@ -1,4 +1,11 @@
 // Krylov building blocks (see krylov.cu).
+//
+// Batched launches: a level of B problems on one grid runs every kernel once
+// with grid.y = B (problem = blockIdx.y).  Vectors of a level are packed
+// problem-major (problem p's n entries at p * n); a Krylov basis keeps its
+// vectors at stride ld = B * n, so vector i of problem p starts at
+// V + i * ld + p * n.  Per-problem scalars (Arnoldi state, reduction scratch)
+// are packed problem-major too, see arnoldi_at / scratch_at.
 #pragma once
 
 #include "adr_common.cuh"
@@ -7,10 +14,16 @@ namespace adr {
 
 constexpr int kMaxReduceBlocks = 304;  // 2 x 152 SMs: per-block partials of a reduction
 constexpr int kMaxKrylov = 64;         // largest restart / inner Krylov dimension
+constexpr int kMaxDots = kMaxKrylov + 2;
+static_assert(kPartialStride >= (int64_t)kMaxReduceBlocks * kMaxDots, "partial sums of the Gram-Schmidt passes");
+static_assert(kPartialStride >= (int64_t)kMaxMrBlocks * 2, "partial sums of the relaxation apply");
 
 // Device-resident Arnoldi state of one (F)GMRES instance with restart m.
-enum { kScalBeta = 0, kScalEst = 1, kScalHn = 2, kScalNrm2 = 3, kNumScal = 4 };
-enum { kIScalStop = 0, kNumIScal = 2 };
+//   scal: beta, Givens estimate |g_{j+1}|, last h_{j+1,j}, last |w|^2, and the
+//         convergence target (estimate <= target freezes the instance; 0 = never)
+//   iscal: exact-breakdown column (-1: none), convergence column (-1: none)
+enum { kScalBeta = 0, kScalEst = 1, kScalHn = 2, kScalNrm2 = 3, kScalTarget = 4, kNumScal = 5 };
+enum { kIScalStop = 0, kIScalConv = 1, kNumIScal = 2 };
 struct ArnoldiState {
   int m;
   double2* H;      // (m+1) x m, column-major
@@ -22,52 +35,77 @@ struct ArnoldiState {
   int* iscal;      // kNumIScal
 };
 
+// Problem pb's state in an allocation of B states packed problem-major.
+__host__ __device__ inline ArnoldiState arnoldi_at(ArnoldiState s, int pb) {
+  const int64_t m = s.m;
+  s.H += pb * (m + 1) * m;
+  s.cs += pb * m;
+  s.sn += pb * m;
+  s.g += pb * (m + 1);
+  s.y += pb * m;
+  s.scal += (int64_t)pb * kNumScal;
+  s.iscal += (int64_t)pb * kNumIScal;
+  return s;
+}
+
 int reduction_blocks(int64_t n);
 
 // Scratch shared by the fused reductions (all launches on one stream).
 struct KrylovScratch {
-  double2* partial;   // per-block partials (>= blocks x values of the largest launch)
+  double2* partial;   // per-block partials, kPartialStride per problem
   unsigned* ticket;   // arrival counter of the last-block reductions (kept at 0 between launches)
-  double2* ha;        // first Gram-Schmidt coefficients
-  double2* hb;        // second Gram-Schmidt coefficients
-  double2* nrm2;      // squared norm
+  double2* ha;        // first Gram-Schmidt coefficients (kMaxDots per problem)
+  double2* hb;        // second Gram-Schmidt coefficients (kMaxDots per problem)
+  double2* nrm2;      // squared norm (x) and reciprocal norm (y)
   double2* alpha;     // minimal-residual weight
 };
+
+__host__ __device__ inline KrylovScratch scratch_at(KrylovScratch s, int pb) {
+  s.partial += (int64_t)pb * kPartialStride;
+  s.ticket += pb;
+  s.ha += (int64_t)pb * kMaxDots;
+  s.hb += (int64_t)pb * kMaxDots;
+  s.nrm2 += pb;
+  s.alpha += pb;
+  return s;
+}
+
+// In the launchers below n is the length of one problem's vectors and B the
+// number of problems (grid.y); V/Z bases have stride ld between vectors.
 
 // CGS2 step j: w <- w - V (V^H w) twice, |w|^2, Arnoldi column j and Givens
 // rotation in st (three launches).
 template <typename T>
 void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s, const ArnoldiState& st, int j,
-                 cudaStream_t stream);
+                 cudaStream_t stream, int B = 1);
 // Gram-Schmidt step j with the second pass only when the first one cancelled
 // |w| below eta |w| (four launches; eta >= 1 is launch_cgs2).
 template <typename T>
 void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
-                          const ArnoldiState& st, int j, double eta, cudaStream_t stream);
+                          const ArnoldiState& st, int j, double eta, cudaStream_t stream, int B = 1);
 // |b|^2 into s.nrm2; with st, also starts an Arnoldi cycle with beta = |b|.
 template <typename T>
-void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream);
+void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream,
+                       int B = 1);
 // x = (assign ? 0 : x) + sum_{i<k} Z_i y_i with y from st.
 template <typename T>
-void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n, cudaStream_t stream);
+void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n,
+                    cudaStream_t stream, int B = 1);
 // x = (x_zero ? 0 : x) + alpha z ; r_dst = r_src - alpha w ; znext = dinv .* r_dst (if not null)
 template <typename T>
 void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, const C<T>* w, const double2* alpha,
-                       const C<T>* dinv, C<T>* znext, bool x_zero, int64_t n, cudaStream_t stream);
-
-template <typename T>
-void launch_dots(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, double2* partial, double2* out,
-                 cudaStream_t st, bool accumulate = false);
-template <typename T>
-void launch_dot2(const C<T>* a, const C<T>* b, const C<T>* c, int64_t n, double2* partial, double2* out, cudaStream_t st);
-template <typename T>
-void launch_axpy_multi(C<T>* w, const C<T>* V, int64_t ld, int k, const double2* coef, double sign, int64_t n, cudaStream_t st);
-template <typename T> void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, int64_t n, cudaStream_t st);
+                       const C<T>* dinv, C<T>* znext, bool x_zero, int64_t n, cudaStream_t stream, int B = 1);
+// out = w * (1 / |w|) with the reciprocal norm from s.nrm2 (per problem).
+template <typename T> void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, int64_t n, cudaStream_t st,
+                                                 int B = 1);
+// Whole-array elementwise operations (n = all problems' entries).
 template <typename T> void launch_copy(const C<T>* a, C<T>* b, int64_t n, cudaStream_t st);
 template <typename T> void launch_zero(C<T>* a, int64_t n, cudaStream_t st);
-template <typename T>
-void launch_mr_update(C<T>* x, const C<T>* z, C<T>* r, const C<T>* w, const double2* alpha, const C<T>* dinv, C<T>* znext,
-                      int64_t n, cudaStream_t st);
+// y = R^{-1} g for the leading block of each problem's rotated Hessenberg
+// matrix, k cut to its breakdown or convergence column.
+void launch_backsolve(const ArnoldiState& s, int k, cudaStream_t st, int B = 1);
+// Convergence targets: st.scal[kScalTarget] = tol * sqrt(nrm2.x) per problem.
+void launch_set_target(const ArnoldiState& s, const double2* nrm2, double tol, cudaStream_t st, int B = 1);
 
 // The same solve on one thread-block cluster (cluster = 16 or 8 CTAs), for
 // Krylov dimensions up to kClusterKMax.  prepare_coarse_cluster returns the
@@ -79,14 +117,10 @@ void launch_coarse_gmres_cluster(const Dims& g, const C<T>* A, const C<T>* dinv,
                                  int k, const ArnoldiState& s, int cluster, cudaStream_t st);
 
 // Whole fixed-count Jacobi-preconditioned GMRES of a small stored-stencil
-// level in one block of 1024 threads (V: (k+1) n scratch, z: n scratch).
+// level in one block of 1024 threads per problem (V: basis of stride B n,
+// z: scratch vector).
 template <typename T>
 void launch_coarse_gmres_cta(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, C<T>* x, C<T>* V, C<T>* z, int k,
                              const ArnoldiState& s, cudaStream_t st);
-
-void launch_cycle_start(const ArnoldiState& s, const double2* nrm2, cudaStream_t st);
-void launch_arnoldi_column(const ArnoldiState& s, int j, const double2* ha, const double2* hb, const double2* nrm2, cudaStream_t st);
-void launch_backsolve(const ArnoldiState& s, int k, cudaStream_t st);
-void launch_mr_alpha(const double2* d, double2* alpha, cudaStream_t st);
 
 }  // namespace adr

@@ -50,18 +50,22 @@ __device__ __forceinline__ void arnoldi_column_dev(ArnoldiState st, int j, const
   const double2 gj = st.g[j];
   st.g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
   st.g[j] = make_double2(c * gj.x, c * gj.y);
-  st.scal[kScalEst] = hypot(st.g[j + 1].x, st.g[j + 1].y);
+  const double est = hypot(st.g[j + 1].x, st.g[j + 1].y);
+  st.scal[kScalEst] = est;
   st.scal[kScalHn] = hn;
   st.scal[kScalNrm2] = nrm2;
   if (hn == 0.0) st.iscal[kIScalStop] = j + 1;
+  if (st.iscal[kIScalConv] < 0 && est <= st.scal[kScalTarget]) st.iscal[kIScalConv] = j + 1;
 }
 
 // y = R^{-1} g for the leading k x k block of the rotated Hessenberg matrix
-// (k is cut to the breakdown index if there was one).
+// (k is cut to the breakdown or the convergence column if there was one).
 __device__ __forceinline__ void backsolve_dev(ArnoldiState st, int k) {
   const int m1 = st.m + 1;
   const int stop = st.iscal[kIScalStop];
   if (stop >= 0 && stop < k) k = stop;
+  const int conv = st.iscal[kIScalConv];
+  if (conv >= 0 && conv < k) k = conv;
   for (int i = 0; i < st.m; ++i) st.y[i] = make_double2(0.0, 0.0);
   for (int i = k - 1; i >= 0; --i) {
     double2 acc = st.g[i];
