@@ -96,6 +96,11 @@ typedef struct adr_params {
                                           operator and its hierarchy (adr_adjoint_solve,
                                           adr_apply_adjoint, adr_vcycle_adjoint); about
                                           doubles the operator's memory.  Default 0 */
+  int relax_blocks;                    /* grid of the fused relaxation applies (blocks
+                                          per problem, grid-stride beyond); 0 selects
+                                          2432 (16 per SM).  A launch shape, not
+                                          arithmetic: results do not depend on it
+                                          beyond rounding order.  0..10240 */
 } adr_params_t;
 
 typedef struct adr_level_info {

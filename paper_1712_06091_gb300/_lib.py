@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("near_source", ctypes.c_int),
         ("reorth_eta", ctypes.c_double),
         ("adjoint", ctypes.c_int),
+        ("relax_blocks", ctypes.c_int),
     ]
 
 

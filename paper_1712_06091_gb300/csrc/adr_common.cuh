@@ -76,6 +76,7 @@ struct Dims {
   int64_t N;
   int64_t s1, s2;  // strides of axes 1 and 2
   int B;           // problems sharing this grid in a batched launch (grid.y)
+  int mrcap;       // largest grid of the relaxation applies (0: kMaxMrBlocks)
 };
 
 inline Dims make_dims(int dim, const int* n) {
@@ -88,6 +89,7 @@ inline Dims make_dims(int dim, const int* n) {
   g.s2 = (int64_t)g.n[0] * g.n[1];
   g.N = g.s2 * g.n[2];
   g.B = 1;
+  g.mrcap = 0;
   return g;
 }
 

@@ -228,6 +228,7 @@ template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
       for (int d = 0; d < 3; ++d) nc[d] = (H.lv[l - 1].g.n[d] - 1) / 2 + 1;
       g = make_dims(op.dim, nc);
       g.B = op.B;
+      g.mrcap = op.g0.mrcap;
     }
     H.L = l + 1;
     H.lv[l].g = g;
@@ -627,6 +628,8 @@ static int validate_params(const adr_params_t& p) {
   if (p.near_source < 1 || p.near_source > 4) return fail(ADR_ERR_ARG, "near_source must be in [1, 4]");
   if (!(p.reorth_eta >= 0.0 && p.reorth_eta <= 1e6)) return fail(ADR_ERR_ARG, "reorth_eta must be in [0, 1e6]");
   if (p.adjoint != 0 && p.adjoint != 1) return fail(ADR_ERR_ARG, "adjoint must be 0 or 1");
+  if (p.relax_blocks < 0 || (int64_t)p.relax_blocks * 2 > kPartialStride)
+    return fail(ADR_ERR_ARG, "relax_blocks must be in [0, 10240]");
   for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
     if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
       return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");
@@ -701,6 +704,7 @@ static int create_impl(int dim, const int* n, const double* h, int B, const int*
   op.B = B;
   op.g0 = make_dims(dim, n);
   op.g0.B = B;
+  op.g0.mrcap = p.relax_blocks;
   op.p = p;
   op.st = (cudaStream_t)stream;
   for (int d = 0; d < 3; ++d) op.h[d] = d < dim ? h[d] : 1.0;

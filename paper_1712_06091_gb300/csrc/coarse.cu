@@ -387,15 +387,16 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
   }
 }
 
-static inline unsigned mr_blocks_c(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (unsigned)(b < kMaxMrBlocks ? (b < 1 ? 1 : b) : kMaxMrBlocks);
+static inline unsigned mr_blocks_c(const Dims& g) {
+  const int64_t cap = g.mrcap > 0 ? g.mrcap : kMaxMrBlocks;
+  const int64_t b = (g.N + 255) / 256;
+  return (unsigned)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 template <typename T>
 void launch_stencil_mr_apply(const Dims& g, const C<T>* A, const C<T>* z, const C<T>* r, C<T>* w, double2* partial,
                              unsigned* ticket, double2* alpha, cudaStream_t st) {
-  const unsigned nb = mr_blocks_c(g.N);
+  const unsigned nb = mr_blocks_c(g);
   const dim3 grid(nb, g.B);
   if (g.dim == 2)
     count_launches(1), (g.B > 1 ? k_stencil_mr_apply<2, T, true> : k_stencil_mr_apply<2, T, false>)<<<grid, 256, 0, st>>>(

@@ -509,15 +509,16 @@ __global__ void k_set_dyn(FineDyn* d, FineDyn v) {
 }
 void launch_set_dyn(FineDyn* d, const FineDyn& v, cudaStream_t st) { count_launches(1), k_set_dyn<<<1, 32, 0, st>>>(d, v); }
 
-static inline unsigned mr_blocks(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (unsigned)(b < kMaxMrBlocks ? (b < 1 ? 1 : b) : kMaxMrBlocks);
+static inline unsigned mr_blocks(const Dims& g) {
+  const int64_t cap = g.mrcap > 0 ? g.mrcap : kMaxMrBlocks;
+  const int64_t b = (g.N + 255) / 256;
+  return (unsigned)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 template <typename T>
 void launch_fine_mr_apply(const Dims& g, const FineOp<T>& f, const C<T>* z, const C<T>* r, C<T>* w, double2* partial,
                           unsigned* ticket, double2* alpha, cudaStream_t st) {
-  const unsigned nb = mr_blocks(g.N);
+  const unsigned nb = mr_blocks(g);
   if (g.dim == 2) count_launches(1), k_fine_mr_apply<2, T><<<dim3(nb, g.B), 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
   else count_launches(1), k_fine_mr_apply<3, T><<<dim3(nb, g.B), 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
 }

@@ -118,3 +118,26 @@ def test_batch_update_and_refusals(adrlib, cuda):
     with pytest.raises(L.ADRError):
         gpu.BatchOperator(n, h, [probs[0][2]] * 2, [probs[0][3]] * 2, np.stack([probs[0][4]] * 2),
                           np.stack([probs[0][5]] * 2), np.stack([probs[0][6]] * 2), params=gpu.default_params(adjoint=1))
+
+
+def test_autotune_and_packed_solver(adrlib, cuda):
+    """The tuner measures every candidate and the packed solve returns each
+    problem's single-operator solution whatever the packing."""
+    from paper_1712_06091_gb300 import adr as gpu
+    from paper_1712_06091_gb300 import autotune
+    probs = _problems("marine2d_65")
+    n, h = probs[0][0], probs[0][1]
+    problems = [(p[2], p[3], torch.from_numpy(p[4]).cuda(), torch.from_numpy(p[5]).cuda(), torch.from_numpy(p[6]).cuda())
+                for p in probs]
+    params = gpu.default_params(precision="f32", levels=3)
+    tuned = autotune.tune(n, h, problems, params=params, packings=(1, 2, 3), relax_blocks=(8, 64))
+    assert tuned["packing"] in (1, 2, 3) and tuned["relax_blocks"] in (8, 64)
+    assert len(tuned["table"]) == 4 and all(r["ms_per_problem_iteration"] > 0 for r in tuned["table"])
+    for packing in (2, 3):
+        solver = autotune.PackedSolver(n, h, packing, params=params)
+        us, infos = solver.solve(problems, tol=1e-8)
+        solver.close()
+        for p, (src, omega, kappa, tau1, gamma) in enumerate(problems):
+            op = gpu.Operator(n, h, src, omega, kappa, tau1, gamma, params=params)
+            a, info = op.solve(tol=1e-8)
+            assert torch.equal(us[p], op.reconstruct(a)) and infos[p]["iterations"] == info["iterations"]
