@@ -101,7 +101,16 @@ typedef struct adr_params {
                                           2432 (16 per SM).  A launch shape, not
                                           arithmetic: results do not depend on it
                                           beyond rounding order.  0..10240 */
+  int coarse_solver;                   /* form of the coarsest-grid GMRES (same arithmetic):
+                                          ADR_COARSE_AUTO picks by size; the others force
+                                          one (cluster and grid need <= 32 iterations) */
 } adr_params_t;
+
+#define ADR_COARSE_AUTO 0      /* cluster up to 32768 nodes, else one block up to 8192, else kernels */
+#define ADR_COARSE_KERNELS 1   /* one launch per step (reductions across launches) */
+#define ADR_COARSE_CTA 2       /* one 1024-thread block per problem */
+#define ADR_COARSE_CLUSTER 3   /* one thread-block cluster per problem (DSMEM reductions) */
+#define ADR_COARSE_GRID 4      /* one cooperative launch over all SMs (grid barriers) */
 
 typedef struct adr_level_info {
   int n[3];            /* nodes per axis (n[2] = 1 in 2D) */

@@ -23,6 +23,7 @@ ADR_F32 = 1
 SCHEMES = {"2up": 0, "1up": 1, "cen": 2, "prec": 3}
 CYCLES = {"V": 0, "K": 1}
 RELAX = {"jacobi": 0, "mr": 1}
+COARSE_SOLVERS = {"auto": 0, "kernels": 1, "cta": 2, "cluster": 3, "grid": 4}
 MAX_LEVELS = 8
 TRAVELTIME_STATIC_MAX_SWEEPS = 8192
 
@@ -56,6 +57,7 @@ class Params(ctypes.Structure):
         ("reorth_eta", ctypes.c_double),
         ("adjoint", ctypes.c_int),
         ("relax_blocks", ctypes.c_int),
+        ("coarse_solver", ctypes.c_int),
     ]
 
 

@@ -31,6 +31,8 @@ def default_params(**overrides) -> L.Params:
             p.cycle = L.CYCLES[val] if isinstance(val, str) else int(val)
         elif key == "relax":
             p.relax = L.RELAX[val] if isinstance(val, str) else int(val)
+        elif key == "coarse_solver":
+            p.coarse_solver = L.COARSE_SOLVERS[val] if isinstance(val, str) else int(val)
         elif key in ("precision", "precond_precision"):
             p.precond_precision = {"f64": L.ADR_F64, "f32": L.ADR_F32}.get(val, val)
         elif key in ("pre_sweeps", "post_sweeps", "jacobi_weight"):
@@ -54,7 +56,7 @@ def params_dict(p: L.Params) -> dict:
         "jacobi_weight": list(p.jacobi_weight), "coarse_iterations": p.coarse_iterations,
         "kcycle_iterations": p.kcycle_iterations, "restart": p.restart,
         "precision": ["f64", "f32"][p.precond_precision], "reorth_eta": p.reorth_eta,
-        "relax_blocks": p.relax_blocks,
+        "relax_blocks": p.relax_blocks, "coarse_solver": p.coarse_solver,
     }
 
 

@@ -204,6 +204,7 @@ template <typename T> struct FineOp {
   int near;          // Chebyshev radius around the source with central advection
   const C<T>* rows;  // if set: stored cross rows (entry q of node j at q * N + j) used
                      // instead of building the row (the conjugate-transposed operator)
+  const T* packed;   // if set: the row's varying parts, stored once per setup (see fine_row)
 };
 
 
@@ -252,6 +253,8 @@ template <typename T> void launch_fine_residual_dinv(const Dims& g, const FineOp
 // and the plain stencil apply / residual with them.
 void launch_fine_store_rows(const Dims& g, const FineOp<double>& f, double2* rows, cudaStream_t st);
 void launch_fine_store_rows(const Dims& g, const FineOp<float>& f, float2* rows, cudaStream_t st);
+// Packed rows of f ((2 + 4 dim) reals per node and problem), for FineOp::packed.
+template <typename T> void launch_fine_pack(const Dims& g, const FineOp<T>& f, T* packed, cudaStream_t st);
 // rowsT = conjugate transpose of the stored cross rows (same layout).
 template <typename T> void launch_rows_adjoint(const Dims& g, const C<T>* rows, C<T>* rowsT, cudaStream_t st);
 void launch_rows_apply(const Dims& g, const double2* rows, const double2* x, double2* y, cudaStream_t st);

@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       int i0, i1, i2;
       unravel(g, e, i0, i1, i2);
-      w[e] = stencil_dot<DIM, T>(g, A, z, e, i0, i1, i2);
+      w[e] = stencil_dot<DIM, T, true>(g, A, z, e, i0, i1, i2);   // z was written in this launch
     }
     __syncthreads();
     cta_dots<T>(V, ld, n, j + 1, w, ha, sh);

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_gmres_cluster(Dims g
     for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
       int i0, i1, i2;
       unravel(g, e, i0, i1, i2);
-      w[e] = stencil_dot<DIM, T>(g, A, z, e, i0, i1, i2);
+      w[e] = stencil_dot<DIM, T, true>(g, A, z, e, i0, i1, i2);   // z was written in this launch
     }
     __syncthreads();
     // first Gram-Schmidt pass

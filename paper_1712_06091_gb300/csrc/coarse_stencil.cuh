@@ -42,28 +42,37 @@ __host__ __device__ __forceinline__ int64_t stencil_entries(int64_t N, int S) { 
 // itself, whose product with the (exactly zero) Galerkin coefficient of that
 // point adds nothing.  All loads can be issued back to back; four partial
 // sums break the dependent FMA chain.
-template <int DIM, typename T, int... P>
+// x loads: read-only path (__ldg) when x is constant for the whole kernel;
+// COH (x rewritten by other blocks or CTAs of the same launch between
+// barriers): ordinary coherent loads, which the acquire side of those
+// barriers orders after the writers' release (no read-only path).
+template <bool COH, typename V> __device__ __forceinline__ V load_x(const V* p) {
+  if constexpr (COH) return *p;
+  else return __ldg(p);
+}
+
+template <int DIM, typename T, bool COH, int... P>
 __device__ __forceinline__ C<T> stencil_dot_seq(const C<T>* __restrict__ A, const C<T>* __restrict__ x, int64_t j,
                                                 int64_t N, int64_t s1, int64_t s2, unsigned m0, unsigned m1, unsigned m2,
                                                 std::integer_sequence<int, P...>) {
   C<T> acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
   const C<T>* Aj = A + stencil_index(0, j, (int)sizeof...(P));
   ((acc[P & 3] = cfma(__ldg(Aj + P * 32),
-                      __ldg(x + ((((m0 >> (Off<DIM, P>::o0 + 2)) & (m1 >> (Off<DIM, P>::o1 + 2)) &
-                                   (m2 >> (Off<DIM, P>::o2 + 2))) & 1u)
-                                     ? j + Off<DIM, P>::o0 + Off<DIM, P>::o1 * s1 + Off<DIM, P>::o2 * s2
-                                     : j)),
+                      load_x<COH>(x + ((((m0 >> (Off<DIM, P>::o0 + 2)) & (m1 >> (Off<DIM, P>::o1 + 2)) &
+                                         (m2 >> (Off<DIM, P>::o2 + 2))) & 1u)
+                                           ? j + Off<DIM, P>::o0 + Off<DIM, P>::o1 * s1 + Off<DIM, P>::o2 * s2
+                                           : j)),
                       acc[P & 3])),
    ...);
   return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool COH = false>
 __device__ __forceinline__ C<T> stencil_dot(const Dims& g, const C<T>* __restrict__ A, const C<T>* __restrict__ x,
                                             int64_t j, int i0, int i1, int i2) {
   constexpr int S = PatternSize<DIM>::value;
   const unsigned m0 = axis_mask(i0, g.n[0]), m1 = axis_mask(i1, g.n[1]), m2 = DIM > 2 ? axis_mask(i2, g.n[2]) : 4u;
-  return stencil_dot_seq<DIM, T>(A, x, j, g.N, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
+  return stencil_dot_seq<DIM, T, COH>(A, x, j, g.N, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
 }
 
 }  // namespace adr

@@ -142,6 +142,27 @@ __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int6
     }
     return;
   }
+  if (f.packed) {
+    // Packed row: entry 0/1 = centre (re, im); 2 + 4 d + q = imaginary part
+    // of neighbour slot q of axis d.  The real parts of the neighbour entries
+    // are the Laplacian's 1/h^2, doubled onto the inner neighbour on a face
+    // (ghost elimination) and zero at the eliminated ghost and at +-2, the
+    // same values the computed row holds.
+    const T* pk = f.packed + (int64_t)pb * (2 + 4 * DIM) * g.N + j;
+    c[0] = mk<T>(__ldg(pk), __ldg(pk + g.N));
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const T ih2 = f.ih2[d];
+      const int k = ii[d], n = g.n[d];
+      const T re_m1 = k == 0 ? T(0) : (k == n - 1 ? ih2 + ih2 : ih2);
+      const T re_p1 = k == n - 1 ? T(0) : (k == 0 ? ih2 + ih2 : ih2);
+      c[1 + 4 * d + 0] = mk<T>(re_m1, __ldg(pk + (int64_t)(2 + 4 * d + 0) * g.N));
+      c[1 + 4 * d + 1] = mk<T>(re_p1, __ldg(pk + (int64_t)(2 + 4 * d + 1) * g.N));
+      c[1 + 4 * d + 2] = mk<T>(T(0), __ldg(pk + (int64_t)(2 + 4 * d + 2) * g.N));
+      c[1 + 4 * d + 3] = mk<T>(T(0), __ldg(pk + (int64_t)(2 + 4 * d + 3) * g.N));
+    }
+    return;
+  }
   bool near = true;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) near = near && (abs(ii[d] - dyn->src[d]) <= f.near);
@@ -558,6 +579,29 @@ __global__ void k_fine_store_rows(Dims g, FineOp<T> f, C<T>* __restrict__ rows) 
 #pragma unroll
   for (int q = 0; q < 1 + 4 * DIM; ++q) rows[(int64_t)q * g.N + j] = c[q];
 }
+
+// The packed form of the rows (see fine_row), built from the computed rows.
+template <int DIM, typename T>
+__global__ void k_fine_pack(Dims g, FineOp<T> f, T* __restrict__ packed) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  f.packed = nullptr;
+  batch_shift((2 + 4 * DIM) * g.N, packed);
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  C<T> c[1 + 4 * DIM];
+  fine_row<DIM, T>(g, f, j, ii, c);
+  packed[j] = c[0].x;
+  packed[g.N + j] = c[0].y;
+#pragma unroll
+  for (int q = 0; q < 4 * DIM; ++q) packed[(int64_t)(2 + q) * g.N + j] = c[1 + q].y;
+}
+template <typename T> void launch_fine_pack(const Dims& g, const FineOp<T>& f, T* packed, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_fine_pack<2, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, packed);
+  else count_launches(1), k_fine_pack<3, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, packed);
+}
+template void launch_fine_pack<double>(const Dims&, const FineOp<double>&, double*, cudaStream_t);
+template void launch_fine_pack<float>(const Dims&, const FineOp<float>&, float*, cudaStream_t);
 
 template <int DIM, typename T>
 __device__ __forceinline__ C<T> rows_dot(const Dims& g, const C<T>* __restrict__ rows, int64_t j, const C<T>* __restrict__ x) {

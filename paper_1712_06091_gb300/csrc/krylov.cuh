@@ -116,6 +116,23 @@ template <typename T>
 void launch_coarse_gmres_cluster(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, C<T>* x, C<T>* V, C<T>* z,
                                  int k, const ArnoldiState& s, int cluster, cudaStream_t st);
 
+// The same solve as one persistent cooperative launch: gs.nblk co-resident
+// blocks per problem meeting at grid barriers (bounded spins; on a timeout
+// the problem's error word is raised and x is set to NaN).
+// prepare_coarse_grid returns how many such blocks the device holds at once
+// (0: no cooperative launch); call it outside capture.
+constexpr int kGridMaxK = 32;
+struct GridScratch {
+  double2* part;   // per problem: 2 x nblk x kGridMaxK partial sums
+  unsigned* bar;   // per problem: arrival count, generation
+  int* err;        // per problem: barrier timeout flag (sticky)
+  int nblk;        // blocks per problem
+};
+int prepare_coarse_grid(int dim, bool f32);
+template <typename T>
+void launch_coarse_gmres_grid(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, C<T>* x, C<T>* V, C<T>* z,
+                              int k, const GridScratch& gs, cudaStream_t st);
+
 // Whole fixed-count Jacobi-preconditioned GMRES of a small stored-stencil
 // level in one block of 1024 threads per problem (V: basis of stride B n,
 // z: scratch vector).

@@ -141,3 +141,13 @@ def test_autotune_and_packed_solver(adrlib, cuda):
             op = gpu.Operator(n, h, src, omega, kappa, tau1, gamma, params=params)
             a, info = op.solve(tol=1e-8)
             assert torch.equal(us[p], op.reconstruct(a)) and infos[p]["iterations"] == info["iterations"]
+
+
+@pytest.mark.parametrize("form", ["grid", "cluster", "cta", "kernels"])
+def test_batch_coarse_forms_equal_single(adrlib, cuda, form):
+    probs, batch, singles = _operators("marine2d_65", precision="f32", levels=2, coarse_solver=form)
+    a, infos = batch.solve(tol=1e-8)
+    a = a.reshape(len(probs), -1)
+    for p, op in enumerate(singles):
+        ap, info = op.solve(tol=1e-8)
+        assert torch.equal(a[p], ap) and infos[p]["iterations"] == info["iterations"], (form, p)

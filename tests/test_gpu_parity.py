@@ -222,3 +222,21 @@ def test_not_converged_and_zero_rhs(adrlib, cuda):
     z = torch.zeros(op.N, dtype=torch.complex128, device="cuda")
     a, info = op.solve(rhs=z, tol=1e-8)
     assert info["iterations"] == 0 and torch.count_nonzero(a) == 0
+
+
+@pytest.mark.parametrize("name,levels", [("marine2d_65", 2), ("layered3d_17", 2), ("const2d_33", 3),
+                                         ("corner3d_9x11x13", 2)])
+@pytest.mark.parametrize("form", ["kernels", "cta", "cluster", "grid"])
+def test_coarse_solver_forms(adrlib, cuda, name, levels, form):
+    """Every form of the coarsest-grid GMRES (one launch per step, one block,
+    one cluster, one cooperative grid with barriers) against the oracle; the
+    2-level cases put 1000-4000 nodes on the coarsest grid, several blocks of
+    the cooperative form."""
+    P, params, op = make_operator(name, precision="f64", levels=levels, coarse_solver=form)
+    hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
+    r = W.random_complex(hier[0]["A"].shape[0], 13)
+    z = op.vcycle(_cvec(r)).cpu().numpy()
+    assert rel(z, mg.cycle(hier, r, oracle_cycle_params(params))) <= 1e-10
+    a, info = op.solve(tol=1e-10, maxit=400)
+    xe = spla.spsolve(oracle_matrix(name, "2up").tocsc(), adr.point_source_rhs(adr.Grid(P.n, P.h), P.src))
+    assert info["rel_residual"] <= 1e-10 and rel(a.cpu().numpy(), xe) <= 1e-8
