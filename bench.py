@@ -46,9 +46,10 @@ WORKLOADS = {
 # (measured fastest on this workload; iteration counts are about the same).
 BENCH_LEVELS = 3
 # The kernel whose roofline is reported, and its algorithmic bytes per node of
-# level 1: 81 stencil coefficients + z + r read, w written (complex float32).
+# level 1: the 81-point stencil stored as 27 complex box entries and 54
+# imaginary parts (float32), z and r read, w written (complex float32).
 ROOFLINE_KERNEL = "k_stencil_mr_apply<3,float> on level 1 (minimal-residual relaxation apply, 81-point Galerkin stencil)"
-ROOFLINE_BYTES_PER_NODE = 81 * 8 + 3 * 8
+ROOFLINE_BYTES_PER_NODE = 27 * 8 + 54 * 4 + 3 * 8
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_stencil_mr_apply_level1_traffic.txt")
 TRAFFIC_SOURCES = ["paper_1712_06091_gb300/csrc/coarse.cu", "paper_1712_06091_gb300/csrc/coarse_stencil.cuh",
                    "paper_1712_06091_gb300/csrc/reduce.cuh"]

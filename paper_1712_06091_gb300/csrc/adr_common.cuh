@@ -127,11 +127,16 @@ template <int DIM> struct PatternSize { static constexpr int value = DIM == 2 ? 
 
 // Offsets of each pattern point (third component 0 in 2D) and the inverse map
 // from (o0+2) + 5 (o1+2) + 25 (o2+2) to the point index (-1 outside).
+// two*[p] = 1 for the points with an offset of +-2 (their Galerkin entries
+// are purely imaginary, see coarse_stencil.cuh); part*[p] = index of p among
+// the points of its kind (box points |o| <= 1 or two-points).
 struct PatternTables {
   int8_t off2[kPattern2][3];
   int8_t off3[kPattern3][3];
   int8_t slot2[25];
   int8_t slot3[125];
+  int8_t two2[kPattern2], part2[kPattern2];
+  int8_t two3[kPattern3], part3[kPattern3];
 };
 
 constexpr PatternTables make_pattern_tables() {
@@ -157,6 +162,21 @@ constexpr PatternTables make_pattern_tables() {
         t.slot3[(o0 + 2) + 5 * (o1 + 2) + 25 * (o2 + 2)] = (int8_t)p;
         ++p;
       }
+  {
+    int nb = 0, nt = 0;
+    for (int q = 0; q < kPattern2; ++q) {
+      const bool two = t.off2[q][0] == 2 || t.off2[q][0] == -2 || t.off2[q][1] == 2 || t.off2[q][1] == -2;
+      t.two2[q] = two ? 1 : 0;
+      t.part2[q] = (int8_t)(two ? nt++ : nb++);
+    }
+    nb = 0; nt = 0;
+    for (int q = 0; q < kPattern3; ++q) {
+      bool two = false;
+      for (int d = 0; d < 3; ++d) two = two || t.off3[q][d] == 2 || t.off3[q][d] == -2;
+      t.two3[q] = two ? 1 : 0;
+      t.part3[q] = (int8_t)(two ? nt++ : nb++);
+    }
+  }
   return t;
 }
 
@@ -165,6 +185,12 @@ static __constant__ PatternTables c_pattern = make_pattern_tables();
 
 template <int DIM> __device__ __forceinline__ const int8_t* pattern_offset(int p) {
   return DIM == 2 ? c_pattern.off2[p] : c_pattern.off3[p];
+}
+template <int DIM> __device__ __forceinline__ bool pattern_two(int p) {
+  return DIM == 2 ? c_pattern.two2[p] != 0 : c_pattern.two3[p] != 0;
+}
+template <int DIM> __device__ __forceinline__ int pattern_part(int p) {
+  return DIM == 2 ? c_pattern.part2[p] : c_pattern.part3[p];
 }
 template <int DIM> __device__ __forceinline__ int pattern_slot(int o0, int o1, int o2) {
   return DIM == 2 ? c_pattern.slot2[(o0 + 2) + 5 * (o1 + 2)]

@@ -87,7 +87,7 @@ __global__ void k_galerkin_stored(Dims gf, Dims gc, const C<T>* __restrict__ Af,
           bool in = true;
           for (int d = 0; d < DIM; ++d) in = in && k[d] >= 0 && k[d] < gf.n[d];
           if (!in) continue;
-          const C<T> wa = cscale(Af[stencil_index(p, fj, S)], wi);
+          const C<T> wa = cscale(stencil_get<DIM, T>(Af, p, fj), wi);
           int pj[3][2];
           T pw[3][2];
           int pc[3];
@@ -104,7 +104,7 @@ __global__ void k_galerkin_stored(Dims gf, Dims gc, const C<T>* __restrict__ Af,
               }
         }
       }
-  for (int p = 0; p < S; ++p) out[stencil_index(p, I, S)] = acc[p];
+  for (int p = 0; p < S; ++p) stencil_put<DIM, T>(out, p, I, acc[p]);
   dinv[I] = cinv(acc[(S - 1) / 2]);
 }
 
@@ -170,7 +170,7 @@ __global__ void k_stencil_export(const C<T>* __restrict__ A, C<T>* __restrict__ 
   batch_shift(N * S, out);
   const int p = (int)(e / N);
   const int64_t j = e - (int64_t)p * N;
-  out[e] = A[stencil_index(p, j, S)];
+  out[e] = S == kPattern2 ? stencil_get<2, T>(A, p, j) : stencil_get<3, T>(A, p, j);
 }
 template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, int B, cudaStream_t st) {
   count_launches(1), k_stencil_export<T><<<dim3(blocks_for(N * S, 256), B), 256, 0, st>>>(A, out, N, S);

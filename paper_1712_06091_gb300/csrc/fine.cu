@@ -384,7 +384,7 @@ __global__ void k_galerkin_fine(Dims gf, Dims gc, FineOp<T> f, C<T>* __restrict_
     }
   };
   galerkin_accumulate<DIM, T>(gf, gc, I, Ii, row_of, acc);
-  for (int p = 0; p < S; ++p) out[stencil_index(p, I, S)] = acc[p];
+  for (int p = 0; p < S; ++p) stencil_put<DIM, T>(out, p, I, acc[p]);
   dinv[I] = cinv(acc[(S - 1) / 2]);
 }
 
