@@ -104,6 +104,13 @@ typedef struct adr_params {
   int coarse_solver;                   /* form of the coarsest-grid GMRES (same arithmetic):
                                           ADR_COARSE_AUTO picks by size; the others force
                                           one (cluster and grid need <= 32 iterations) */
+  int tma;                             /* 1: the float32 relaxation applies of the stored-
+                                          stencil levels stream their coefficients into
+                                          shared memory with bulk copies (16 warps, one
+                                          buffer each); 2: the same with 8 warps, two
+                                          buffers each; 0: plain loads.  Same per-node
+                                          arithmetic; the weight's block sums follow the
+                                          kernel's grid.  Default 1 */
 } adr_params_t;
 
 #define ADR_COARSE_AUTO 0      /* cluster up to 32768 nodes, else one block up to 8192, else kernels */

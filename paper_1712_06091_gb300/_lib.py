@@ -58,6 +58,7 @@ class Params(ctypes.Structure):
         ("adjoint", ctypes.c_int),
         ("relax_blocks", ctypes.c_int),
         ("coarse_solver", ctypes.c_int),
+        ("tma", ctypes.c_int),
     ]
 
 

@@ -56,7 +56,7 @@ def params_dict(p: L.Params) -> dict:
         "jacobi_weight": list(p.jacobi_weight), "coarse_iterations": p.coarse_iterations,
         "kcycle_iterations": p.kcycle_iterations, "restart": p.restart,
         "precision": ["f64", "f32"][p.precond_precision], "reorth_eta": p.reorth_eta,
-        "relax_blocks": p.relax_blocks, "coarse_solver": p.coarse_solver,
+        "relax_blocks": p.relax_blocks, "coarse_solver": p.coarse_solver, "tma": p.tma,
     }
 
 

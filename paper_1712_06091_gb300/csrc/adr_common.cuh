@@ -298,6 +298,15 @@ template <typename T> void launch_stencil_mr_apply(const Dims& g, const C<T>* A,
                                                    double2* partial, unsigned* ticket, double2* alpha, cudaStream_t st);
 template <typename T> void launch_stencil_residual_dinv(const Dims& g, const C<T>* A, const C<T>* b, const C<T>* x,
                                                         const C<T>* dinv, C<T>* r, C<T>* z, cudaStream_t st);
+// The minimal-residual apply with the coefficient tiles streamed into shared
+// memory by bulk copies (float32 only); err: per-problem error words (a
+// bounded wait that ran out sets it and the weight to NaN).  blocks: grid
+// size per problem.  prepare_stencil_tma opts the kernel into its shared
+// memory; call it outside capture, false if unavailable.
+bool prepare_stencil_tma();
+void launch_stencil_mr_apply_tma(const Dims& g, const float2* A, const float2* z, const float2* r, float2* w,
+                                 double2* partial, unsigned* ticket, double2* alpha, int* err, int blocks, int variant,
+                                 cudaStream_t st);
 template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, int B, cudaStream_t st);
 template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st);
 

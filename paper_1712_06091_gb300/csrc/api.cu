@@ -160,6 +160,9 @@ struct Op {
   bool use_graph = true;
   int cluster_size = 0;             // CTAs of the coarsest-grid cluster solver (0: not available)
   int grid_coresident = 0;          // co-resident blocks of the persistent coarsest solve (0: not available)
+  bool tma_ok = false;              // bulk-copy relaxation apply available (and enabled by params.tma)
+  int num_sms = 0;
+  int* tma_err = nullptr;           // per problem: error words of the bulk-copy kernels
   // instrumentation (adr_profile_kernel): event pairs 2k, 2k+1 of prof_pool
   int prof_class = ADR_PROF_NONE;
   std::vector<cudaEvent_t> prof_pool;
@@ -316,6 +319,7 @@ static void plan(Op& op, Arena& a) {
   op.ks.nrm2 = a.take<double2>(B);
   op.ks.alpha = a.take<double2>(B);
   op.dyn = a.take<FineDyn>(B);
+  op.tma_err = a.take<int>(B);
   if (op.p.adjoint) {
     const size_t cross = (size_t)(1 + 4 * op.dim) * N;
     const size_t cbytes = op.p.precond_precision == ADR_F64 ? sizeof(double2) : sizeof(float2);
@@ -375,8 +379,17 @@ template <typename T> struct Cycle {
   }
   void mr_apply(int l, const C<T>* z, const C<T>* r, C<T>* w) {
     const int pk = prof_begin(op, l == 0 ? ADR_PROF_FINE_RELAX : (l == 1 ? ADR_PROF_LEVEL1_RELAX : -1), st);
-    if (l == 0) launch_fine_mr_apply<T>(H.lv[0].g, H.prec, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
-    else launch_stencil_mr_apply<T>(H.lv[l].g, H.lv[l].A, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
+    if (l == 0) {
+      launch_fine_mr_apply<T>(H.lv[0].g, H.prec, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
+    } else if constexpr (sizeof(T) == 4) {
+      if (op.tma_ok)
+        launch_stencil_mr_apply_tma(H.lv[l].g, H.lv[l].A, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, op.tma_err,
+                                    op.num_sms, op.p.tma, st);
+      else
+        launch_stencil_mr_apply<T>(H.lv[l].g, H.lv[l].A, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
+    } else {
+      launch_stencil_mr_apply<T>(H.lv[l].g, H.lv[l].A, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
+    }
     prof_end(op, pk, st);
   }
 
@@ -662,6 +675,7 @@ static int validate_params(const adr_params_t& p) {
     return fail(ADR_ERR_ARG, "relax_blocks must be in [0, 10240]");
   if (p.coarse_solver < ADR_COARSE_AUTO || p.coarse_solver > ADR_COARSE_GRID)
     return fail(ADR_ERR_ARG, "unknown coarse_solver");
+  if (p.tma < 0 || p.tma > 2) return fail(ADR_ERR_ARG, "tma must be 0, 1 or 2");
   for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
     if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
       return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");
@@ -701,6 +715,7 @@ int adr_params_default(adr_params_t* p) {
   p->precond_precision = ADR_F32;
   p->near_source = 1;
   p->reorth_eta = 0.1;
+  p->tma = 1;
   return ADR_OK;
 }
 
@@ -749,6 +764,13 @@ static int create_impl(int dim, const int* n, const double* h, int B, const int*
   op.src_index = op.src[0] + op.g0.s1 * op.src[1] + op.g0.s2 * op.src[2];
 
   op.grid_coresident = prepare_coarse_grid(dim, p.precond_precision == ADR_F32);
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&op.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+  }
+  op.tma_ok = p.tma && p.precond_precision == ADR_F32 && op.num_sms > 0 && prepare_stencil_tma();
   Arena sizing;
   plan(op, sizing);
   op.arena_bytes = sizing.used + 256;

@@ -1,0 +1,230 @@
+// Relaxation apply of the stored-stencil levels with the coefficient stream
+// moved by the bulk-copy (TMA) engine.
+//
+// The level-1 minimal-residual apply reads ~456 B of stencil per node and
+// little else; in the plain kernel each thread issues those loads itself, so
+// the bytes in flight per SM are bounded by its registers (64 per thread at 4
+// blocks per SM) and the kernel waits on DRAM latency.  Here every warp owns a
+// stream of 32-node tiles (a tile's coefficients are one contiguous block of
+// the stored layout, 13.8 KB in 3D float) and keeps two of them in shared
+// memory: while it computes on one, the copy engine fills the other
+// (cp.async.bulk global -> shared, completion counted on an mbarrier).  One
+// block of sixteen warps per SM, one tile buffer per warp (a warp's copy is
+// overlapped by the other warps' work; a two-buffer variant with eight warps
+// is also built): up to sixteen tiles (221 KB) in flight per SM, independent
+// of registers.  The neighbour values z still come through the read-only
+// cache; each node's arithmetic is the plain kernel's (the weight's block
+// sums follow this kernel's grid).
+//
+// Every mbarrier wait is bounded.  A warp whose wait runs out raises the
+// launch's error word, waits (bounded) for its other copy, and stops; the last
+// block then publishes a NaN weight, which the relaxation and the Krylov
+// iteration above report as a failure.
+#include <cstdint>
+
+#include "coarse_stencil.cuh"
+#include "reduce.cuh"
+
+namespace adr {
+
+constexpr unsigned kTmaWaitSpins = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on phase `parity` of an mbarrier; false if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity) {
+  for (unsigned spins = 0; spins < kTmaWaitSpins; ++spins)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+// One bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completing on mbar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// One point's term with the coefficients in shared memory (tile layout as in
+// global memory: box entries complex, two-points imaginary only).
+template <int DIM, typename T, int P>
+__device__ __forceinline__ void stencil_term_smem(const C<T>* tb, const T* tr, const C<T>* __restrict__ x, int64_t j,
+                                                  int64_t s1, int64_t s2, unsigned m0, unsigned m1, unsigned m2, C<T>& acc) {
+  const bool in = ((m0 >> (Off<DIM, P>::o0 + 2)) & (m1 >> (Off<DIM, P>::o1 + 2)) & (m2 >> (Off<DIM, P>::o2 + 2))) & 1u;
+  const C<T> xv = __ldg(x + (in ? j + Off<DIM, P>::o0 + Off<DIM, P>::o1 * s1 + Off<DIM, P>::o2 * s2 : j));
+  if constexpr (PointKind<DIM, P>::two) {
+    const T a = tr[PointKind<DIM, P>::part * 32];
+    acc.x = fma(-a, xv.y, acc.x);
+    acc.y = fma(a, xv.x, acc.y);
+  } else {
+    acc = cfma(tb[PointKind<DIM, P>::part * 32], xv, acc);
+  }
+}
+
+// One node's stencil row from a tile in shared memory (box entries complex,
+// two-points imaginary only), times the neighbour values of x.
+template <int DIM, typename T, int... P>
+__device__ __forceinline__ C<T> tile_dot_seq(const C<T>* __restrict__ tb, const T* __restrict__ tr, const C<T>* __restrict__ x,
+                                             int64_t j, int64_t s1, int64_t s2, unsigned m0, unsigned m1, unsigned m2,
+                                             std::integer_sequence<int, P...>) {
+  C<T> acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+  (stencil_term_smem<DIM, T, P>(tb, tr, x, j, s1, s2, m0, m1, m2, acc[P & 3]), ...);
+  return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+}
+
+// w = A z and the partial sums of w^H r, w^H w; alpha by the last block.
+// WARPS warps per block, each with STAGES tile buffers (1: the other warps
+// of the SM overlap its copy; 2: it overlaps its own).
+template <int DIM, typename T, bool BT, int WARPS, int STAGES>
+__global__ void __launch_bounds__(WARPS * 32, 1)
+    k_stencil_mr_apply_tma(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ z, const C<T>* __restrict__ r,
+                           C<T>* __restrict__ w, double2* partial, unsigned* ticket, double2* alpha, int* err) {
+  constexpr int W = Split<DIM>::W, NB = Split<DIM>::NB, S = PatternSize<DIM>::value;
+  constexpr unsigned kTileBytes = W * 32 * sizeof(C<T>);
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(8) uint64_t mbar[WARPS][2];
+  __shared__ double2 sh[32 * 2];
+  __shared__ int s_fail;
+  if (BT) {
+    batch_shift(stencil_entries(g.N, S), A);
+    batch_shift(g.N, z, r, w);
+    batch_shift(kPartialStride, partial);
+    batch_shift(1, ticket, alpha, err);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C<T>* const buf0 = reinterpret_cast<C<T>*>(tma_smem) + (size_t)warp * STAGES * W * 32;
+  C<T>* const buf1 = buf0 + (STAGES > 1 ? W * 32 : 0);
+  if (threadIdx.x == 0) s_fail = 0;
+  if (lane == 0) {
+    for (int q = 0; q < STAGES; ++q) mbar_init(&mbar[warp][q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const int64_t ntiles = (g.N + 31) >> 5;
+  const int64_t stride = (int64_t)gridDim.x * WARPS;
+  const int64_t t0 = (int64_t)blockIdx.x * WARPS + warp;
+  auto issue = [&](int64_t t, int s) {
+    if (lane == 0 && t < ntiles) {
+      mbar_expect_tx(&mbar[warp][s], kTileBytes);
+      bulk_load(s ? buf1 : buf0, A + t * (int64_t)W * 32, kTileBytes, &mbar[warp][s]);
+    }
+  };
+  issue(t0, 0);
+  if (STAGES > 1) issue(t0 + stride, 1);
+  unsigned phase = 0u;   // bit s: parity of stage s's next completion
+  bool fail = false;
+  C<T> sacc[2] = {czero<T>(), czero<T>()};
+  int s = 0;
+  for (int64_t t = t0; t < ntiles; t += stride, s = STAGES > 1 ? s ^ 1 : 0) {
+    if (!mbar_wait(&mbar[warp][s], (phase >> s) & 1u)) fail = true;
+    fail = __any_sync(0xffffffffu, fail);
+    if (fail) break;
+    phase ^= 1u << s;
+    const int64_t j = t * 32 + lane;
+    if (j < g.N) {
+      int i0, i1, i2;
+      unravel(g, j, i0, i1, i2);
+      const unsigned m0 = axis_mask(i0, g.n[0]), m1 = axis_mask(i1, g.n[1]), m2 = DIM > 2 ? axis_mask(i2, g.n[2]) : 4u;
+      const C<T>* bs = s ? buf1 : buf0;
+      const C<T>* tb = bs + lane;
+      const T* tr = reinterpret_cast<const T*>(bs + NB * 32) + lane;
+      const C<T> wj = tile_dot_seq<DIM, T>(tb, tr, z, j, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
+      w[j] = wj;
+      sacc[0] = cfma_conj(wj, r[j], sacc[0]);
+      sacc[1] = cfma_conj(wj, wj, sacc[1]);
+    }
+    __syncwarp();
+    // the generic-proxy reads of buf[s] are done before the copy engine refills it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(t + STAGES * stride, s);
+  }
+  if (fail) {
+    // wait (bounded) for this warp's copies still in flight before the block exits
+    for (int q = 0; q < STAGES; ++q) mbar_wait(&mbar[warp][q], (phase >> q) & 1u);
+    if (lane == 0) {
+      atomicExch(err, 1);
+      s_fail = 1;
+    }
+  }
+  double2 mine[2], tot[2];
+  block_sum_t<T, 2>(sacc, sh, mine);
+  if (last_block_total<2>(mine, partial, ticket, tot, sh) && threadIdx.x == 0) {
+    const double den = tot[1].x;
+    const bool bad = *(volatile int*)err != 0 || s_fail;
+    *alpha = bad ? make_double2(NAN, NAN)
+                 : (den > 0.0 ? make_double2(tot[0].x / den, tot[0].y / den) : make_double2(0.0, 0.0));
+  }
+}
+
+template <int DIM, int WARPS, int STAGES> constexpr size_t tma_smem_bytes() {
+  return (size_t)WARPS * STAGES * Split<DIM>::W * 32 * sizeof(float2);
+}
+template <int DIM, int WARPS, int STAGES> static bool tma_attr() {
+  constexpr int bytes = (int)tma_smem_bytes<DIM, WARPS, STAGES>();
+  return cudaFuncSetAttribute(k_stencil_mr_apply_tma<DIM, float, false, WARPS, STAGES>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(k_stencil_mr_apply_tma<DIM, float, true, WARPS, STAGES>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+}
+
+// Opts the kernels into their dynamic shared memory (call outside capture);
+// returns false if the device cannot give it.
+bool prepare_stencil_tma() {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if ((size_t)optin < tma_smem_bytes<3, 16, 1>() + 2048 || (size_t)optin < tma_smem_bytes<3, 8, 2>() + 2048) return false;
+  const bool ok = tma_attr<3, 8, 2>() && tma_attr<2, 8, 2>() && tma_attr<3, 16, 1>() && tma_attr<2, 16, 1>();
+  cudaGetLastError();
+  return ok;
+}
+
+template <int DIM, int WARPS, int STAGES>
+static void launch_tma(const Dims& g, const float2* A, const float2* z, const float2* r, float2* w, double2* partial,
+                       unsigned* ticket, double2* alpha, int* err, int blocks, cudaStream_t st) {
+  const int64_t ntiles = (g.N + 31) >> 5;
+  int64_t nb = (ntiles + WARPS - 1) / WARPS;
+  if (nb > blocks) nb = blocks;
+  if (nb < 1) nb = 1;
+  const dim3 grid((unsigned)nb, g.B);
+  constexpr size_t smem = tma_smem_bytes<DIM, WARPS, STAGES>();
+  count_launches(1), (g.B > 1 ? k_stencil_mr_apply_tma<DIM, float, true, WARPS, STAGES>
+                              : k_stencil_mr_apply_tma<DIM, float, false, WARPS, STAGES>)
+                         <<<grid, WARPS * 32, smem, st>>>(g, A, z, r, w, partial, ticket, alpha, err);
+}
+
+// variant 1: 16 warps per block, one tile buffer each (95 us per level-1
+// launch of the 257x257x129 workload); variant 2: 8 warps, two buffers each
+// (98 us); the plain-load kernel takes 115 us.
+void launch_stencil_mr_apply_tma(const Dims& g, const float2* A, const float2* z, const float2* r, float2* w,
+                                 double2* partial, unsigned* ticket, double2* alpha, int* err, int blocks, int variant,
+                                 cudaStream_t st) {
+  if (variant == 2) {
+    if (g.dim == 2) launch_tma<2, 8, 2>(g, A, z, r, w, partial, ticket, alpha, err, blocks, st);
+    else launch_tma<3, 8, 2>(g, A, z, r, w, partial, ticket, alpha, err, blocks, st);
+  } else {
+    if (g.dim == 2) launch_tma<2, 16, 1>(g, A, z, r, w, partial, ticket, alpha, err, blocks, st);
+    else launch_tma<3, 16, 1>(g, A, z, r, w, partial, ticket, alpha, err, blocks, st);
+  }
+}
+
+}  // namespace adr
