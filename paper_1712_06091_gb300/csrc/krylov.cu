@@ -118,16 +118,18 @@ __device__ __forceinline__ bool last_block_rt(int k, const double2* blk, double2
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  for (int i = 0; i < k; ++i) {
+  // one warp per value: lanes stride over the blocks' partials, then a fixed
+  // shuffle tree (no block-wide step per value)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < k; i += nw) {
     double2 acc = make_double2(0.0, 0.0);
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    for (unsigned b = lane; b < gridDim.x; b += 32) {
       const double2 p = __ldcg(&partial[(size_t)b * k + i]);
       acc.x += p.x;
       acc.y += p.y;
     }
-    double2 v[1] = {acc}, o[1];
-    block_sum_k<1>(v, sh, o);
-    if (threadIdx.x == 0) out[i] = o[0];
+    acc = warp_sum2(acc);
+    if (lane == 0) out[i] = acc;
   }
   if (threadIdx.x == 0) *ticket = 0u;
   __syncthreads();
