@@ -307,6 +307,12 @@ bool prepare_stencil_tma();
 void launch_stencil_mr_apply_tma(const Dims& g, const float2* A, const float2* z, const float2* r, float2* w,
                                  double2* partial, unsigned* ticket, double2* alpha, int* err, int blocks, int variant,
                                  cudaStream_t st);
+// y = A x and r = b - A x, z = dinv .* r with the same streaming (NaN output on a failed wait).
+void launch_stencil_apply_tma(const Dims& g, const float2* A, const float2* x, float2* y, int* err, int blocks,
+                              int variant, cudaStream_t st);
+void launch_stencil_residual_dinv_tma(const Dims& g, const float2* A, const float2* b, const float2* x,
+                                      const float2* dinv, float2* r, float2* z, int* err, int blocks, int variant,
+                                      cudaStream_t st);
 template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, int B, cudaStream_t st);
 template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st);
 

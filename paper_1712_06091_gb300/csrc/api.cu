@@ -362,8 +362,14 @@ template <typename T> struct Cycle {
   cudaStream_t st;
 
   void apply(int l, const C<T>* x, C<T>* y) {
-    if (l == 0) launch_fine_apply<T>(H.lv[0].g, H.prec, x, y, st);
-    else launch_stencil_apply<T>(H.lv[l].g, H.lv[l].A, x, y, st);
+    if (l == 0) {
+      launch_fine_apply<T>(H.lv[0].g, H.prec, x, y, st);
+    } else if constexpr (sizeof(T) == 4) {
+      if (op.tma_ok) launch_stencil_apply_tma(H.lv[l].g, H.lv[l].A, x, y, op.tma_err, op.num_sms, op.p.tma, st);
+      else launch_stencil_apply<T>(H.lv[l].g, H.lv[l].A, x, y, st);
+    } else {
+      launch_stencil_apply<T>(H.lv[l].g, H.lv[l].A, x, y, st);
+    }
   }
   void residual(int l, const C<T>* b, const C<T>* x, C<T>* r) {
     if (l == 0) launch_fine_residual<T>(H.lv[0].g, H.prec, b, x, r, st);
@@ -374,8 +380,17 @@ template <typename T> struct Cycle {
     else launch_stencil_jacobi<T>(H.lv[l].g, H.lv[l].A, H.lv[l].dinv, b, xin, xout, w, st);
   }
   void residual_dinv(int l, const C<T>* b, const C<T>* x, C<T>* r, C<T>* z) {
-    if (l == 0) launch_fine_residual_dinv<T>(H.lv[0].g, H.prec, b, x, H.lv[0].dinv, r, z, st);
-    else launch_stencil_residual_dinv<T>(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, st);
+    if (l == 0) {
+      launch_fine_residual_dinv<T>(H.lv[0].g, H.prec, b, x, H.lv[0].dinv, r, z, st);
+    } else if constexpr (sizeof(T) == 4) {
+      if (op.tma_ok)
+        launch_stencil_residual_dinv_tma(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, op.tma_err, op.num_sms,
+                                         op.p.tma, st);
+      else
+        launch_stencil_residual_dinv<T>(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, st);
+    } else {
+      launch_stencil_residual_dinv<T>(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, st);
+    }
   }
   void mr_apply(int l, const C<T>* z, const C<T>* r, C<T>* w) {
     const int pk = prof_begin(op, l == 0 ? ADR_PROF_FINE_RELAX : (l == 1 ? ADR_PROF_LEVEL1_RELAX : -1), st);
@@ -472,11 +487,11 @@ template <typename T> struct Cycle {
     const int B = L.g.B;
     const int64_t ld = n * B;
     launch_norm_start<T>(b, n, op.ks, &L.ks, st, B);
-    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st, B);
+    launch_scale_dinv<T>(b, L.KV, L.dinv, L.z, op.ks.nrm2, n, st, B);   // V_0 and z = D^{-1} V_0
     for (int j = 0; j < k; ++j) {
-      launch_cmul_vec<T>(L.dinv, L.KV + (int64_t)j * ld, L.z, ld, st);
       apply(l, L.z, L.t);
-      arnoldi(L.ks, L.KV, ld, j, L.t, n, B, j + 1 < k);
+      launch_cgs2<T>(L.KV, ld, j + 1, L.t, n, op.ks, L.ks, j, st, B);
+      if (j + 1 < k) launch_scale_dinv<T>(L.t, L.KV + (int64_t)(j + 1) * ld, L.dinv, L.z, op.ks.nrm2, n, st, B);
     }
     launch_backsolve(L.ks, k, st, B);
     launch_combine<T>(L.t, L.KV, ld, k, L.ks, true, n, st, B);

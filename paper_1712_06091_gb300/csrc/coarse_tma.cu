@@ -90,13 +90,21 @@ __device__ __forceinline__ C<T> tile_dot_seq(const C<T>* __restrict__ tb, const 
   return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
 
-// w = A z and the partial sums of w^H r, w^H w; alpha by the last block.
-// WARPS warps per block, each with STAGES tile buffers (1: the other warps
-// of the SM overlap its copy; 2: it overlaps its own).
-template <int DIM, typename T, bool BT, int WARPS, int STAGES>
+// Modes of the streamed stencil kernel.
+enum { kTmaMr = 0, kTmaApply = 1, kTmaResid = 2 };
+
+// One pass over the level with the coefficient tiles streamed into shared
+// memory.  WARPS warps per block, each with STAGES tile buffers (1: the other
+// warps of the SM overlap its copy; 2: it overlaps its own).
+//   kTmaMr:    out = A x and the partial sums of out^H aux, out^H out; the last
+//              block writes the minimal-residual weight to alpha
+//   kTmaApply: out = A x
+//   kTmaResid: out = aux - A x, out2 = dinv .* out
+template <int DIM, typename T, bool BT, int WARPS, int STAGES, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, 1)
-    k_stencil_mr_apply_tma(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ z, const C<T>* __restrict__ r,
-                           C<T>* __restrict__ w, double2* partial, unsigned* ticket, double2* alpha, int* err) {
+    k_stencil_tma(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ x, const C<T>* __restrict__ aux,
+                  C<T>* __restrict__ out, const C<T>* __restrict__ dinv, C<T>* __restrict__ out2, double2* partial,
+                  unsigned* ticket, double2* alpha, int* err) {
   constexpr int W = Split<DIM>::W, NB = Split<DIM>::NB, S = PatternSize<DIM>::value;
   constexpr unsigned kTileBytes = W * 32 * sizeof(C<T>);
   extern __shared__ __align__(128) unsigned char tma_smem[];
@@ -105,9 +113,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   __shared__ int s_fail;
   if (BT) {
     batch_shift(stencil_entries(g.N, S), A);
-    batch_shift(g.N, z, r, w);
-    batch_shift(kPartialStride, partial);
-    batch_shift(1, ticket, alpha, err);
+    batch_shift(g.N, x, aux, out);
+    batch_shift_opt(g.N, dinv, out2);
+    batch_shift_opt(kPartialStride, partial);
+    batch_shift_opt(1, ticket, alpha);
+    batch_shift(1, err);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   C<T>* const buf0 = reinterpret_cast<C<T>*>(tma_smem) + (size_t)warp * STAGES * W * 32;
@@ -134,7 +144,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   bool fail = false;
   C<T> sacc[2] = {czero<T>(), czero<T>()};
   int s = 0;
-  for (int64_t t = t0; t < ntiles; t += stride, s = STAGES > 1 ? s ^ 1 : 0) {
+  int64_t t = t0;
+  for (; t < ntiles; t += stride, s = STAGES > 1 ? s ^ 1 : 0) {
     if (!mbar_wait(&mbar[warp][s], (phase >> s) & 1u)) fail = true;
     fail = __any_sync(0xffffffffu, fail);
     if (fail) break;
@@ -147,43 +158,68 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       const C<T>* bs = s ? buf1 : buf0;
       const C<T>* tb = bs + lane;
       const T* tr = reinterpret_cast<const T*>(bs + NB * 32) + lane;
-      const C<T> wj = tile_dot_seq<DIM, T>(tb, tr, z, j, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
-      w[j] = wj;
-      sacc[0] = cfma_conj(wj, r[j], sacc[0]);
-      sacc[1] = cfma_conj(wj, wj, sacc[1]);
+      const C<T> ax = tile_dot_seq<DIM, T>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
+      if constexpr (MODE == kTmaMr) {
+        out[j] = ax;
+        sacc[0] = cfma_conj(ax, aux[j], sacc[0]);
+        sacc[1] = cfma_conj(ax, ax, sacc[1]);
+      } else if constexpr (MODE == kTmaApply) {
+        out[j] = ax;
+      } else {
+        const C<T> rj = csub(aux[j], ax);
+        out[j] = rj;
+        out2[j] = cmul(dinv[j], rj);
+      }
     }
     __syncwarp();
-    // the generic-proxy reads of buf[s] are done before the copy engine refills it
+    // the generic-proxy reads of the buffer are done before the copy engine refills it
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     issue(t + STAGES * stride, s);
   }
   if (fail) {
-    // wait (bounded) for this warp's copies still in flight before the block exits
+    // wait (bounded) for this warp's copies still in flight, mark the failure:
+    // the weight (kTmaMr) or the tiles this warp did not compute become NaN
     for (int q = 0; q < STAGES; ++q) mbar_wait(&mbar[warp][q], (phase >> q) & 1u);
     if (lane == 0) {
       atomicExch(err, 1);
       s_fail = 1;
     }
+    if constexpr (MODE != kTmaMr) {
+      const C<T> nan = mk<T>((T)NAN, (T)NAN);
+      for (; t < ntiles; t += stride) {
+        const int64_t j = t * 32 + lane;
+        if (j < g.N) {
+          out[j] = nan;
+          if constexpr (MODE == kTmaResid) out2[j] = nan;
+        }
+      }
+    }
   }
-  double2 mine[2], tot[2];
-  block_sum_t<T, 2>(sacc, sh, mine);
-  if (last_block_total<2>(mine, partial, ticket, tot, sh) && threadIdx.x == 0) {
-    const double den = tot[1].x;
-    const bool bad = *(volatile int*)err != 0 || s_fail;
-    *alpha = bad ? make_double2(NAN, NAN)
-                 : (den > 0.0 ? make_double2(tot[0].x / den, tot[0].y / den) : make_double2(0.0, 0.0));
+  if constexpr (MODE == kTmaMr) {
+    double2 mine[2], tot[2];
+    block_sum_t<T, 2>(sacc, sh, mine);
+    if (last_block_total<2>(mine, partial, ticket, tot, sh) && threadIdx.x == 0) {
+      const double den = tot[1].x;
+      const bool bad = *(volatile int*)err != 0 || s_fail;
+      *alpha = bad ? make_double2(NAN, NAN)
+                   : (den > 0.0 ? make_double2(tot[0].x / den, tot[0].y / den) : make_double2(0.0, 0.0));
+    }
   }
 }
 
 template <int DIM, int WARPS, int STAGES> constexpr size_t tma_smem_bytes() {
   return (size_t)WARPS * STAGES * Split<DIM>::W * 32 * sizeof(float2);
 }
-template <int DIM, int WARPS, int STAGES> static bool tma_attr() {
+template <int DIM, int WARPS, int STAGES, int MODE> static bool tma_attr_mode() {
   constexpr int bytes = (int)tma_smem_bytes<DIM, WARPS, STAGES>();
-  return cudaFuncSetAttribute(k_stencil_mr_apply_tma<DIM, float, false, WARPS, STAGES>,
+  return cudaFuncSetAttribute(k_stencil_tma<DIM, float, false, WARPS, STAGES, MODE>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
-         cudaFuncSetAttribute(k_stencil_mr_apply_tma<DIM, float, true, WARPS, STAGES>,
+         cudaFuncSetAttribute(k_stencil_tma<DIM, float, true, WARPS, STAGES, MODE>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+}
+template <int DIM, int WARPS, int STAGES> static bool tma_attr() {
+  return tma_attr_mode<DIM, WARPS, STAGES, kTmaMr>() && tma_attr_mode<DIM, WARPS, STAGES, kTmaApply>() &&
+         tma_attr_mode<DIM, WARPS, STAGES, kTmaResid>();
 }
 
 // Opts the kernels into their dynamic shared memory (call outside capture);
@@ -198,33 +234,50 @@ bool prepare_stencil_tma() {
   return ok;
 }
 
-template <int DIM, int WARPS, int STAGES>
-static void launch_tma(const Dims& g, const float2* A, const float2* z, const float2* r, float2* w, double2* partial,
-                       unsigned* ticket, double2* alpha, int* err, int blocks, cudaStream_t st) {
+template <int DIM, int WARPS, int STAGES, int MODE>
+static void launch_tma(const Dims& g, const float2* A, const float2* x, const float2* aux, float2* out,
+                       const float2* dinv, float2* out2, double2* partial, unsigned* ticket, double2* alpha, int* err,
+                       int blocks, cudaStream_t st) {
   const int64_t ntiles = (g.N + 31) >> 5;
   int64_t nb = (ntiles + WARPS - 1) / WARPS;
   if (nb > blocks) nb = blocks;
   if (nb < 1) nb = 1;
   const dim3 grid((unsigned)nb, g.B);
   constexpr size_t smem = tma_smem_bytes<DIM, WARPS, STAGES>();
-  count_launches(1), (g.B > 1 ? k_stencil_mr_apply_tma<DIM, float, true, WARPS, STAGES>
-                              : k_stencil_mr_apply_tma<DIM, float, false, WARPS, STAGES>)
-                         <<<grid, WARPS * 32, smem, st>>>(g, A, z, r, w, partial, ticket, alpha, err);
+  count_launches(1), (g.B > 1 ? k_stencil_tma<DIM, float, true, WARPS, STAGES, MODE>
+                              : k_stencil_tma<DIM, float, false, WARPS, STAGES, MODE>)
+                         <<<grid, WARPS * 32, smem, st>>>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err);
+}
+
+template <int MODE>
+static void launch_variant(const Dims& g, const float2* A, const float2* x, const float2* aux, float2* out,
+                           const float2* dinv, float2* out2, double2* partial, unsigned* ticket, double2* alpha,
+                           int* err, int blocks, int variant, cudaStream_t st) {
+  if (variant == 2) {
+    if (g.dim == 2) launch_tma<2, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st);
+    else launch_tma<3, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st);
+  } else {
+    if (g.dim == 2) launch_tma<2, 16, 1, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st);
+    else launch_tma<3, 16, 1, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st);
+  }
 }
 
 // variant 1: 16 warps per block, one tile buffer each (95 us per level-1
-// launch of the 257x257x129 workload); variant 2: 8 warps, two buffers each
-// (98 us); the plain-load kernel takes 115 us.
+// relaxation launch of the 257x257x129 workload); variant 2: 8 warps, two
+// buffers each (98 us); the plain-load kernel takes 115 us.
 void launch_stencil_mr_apply_tma(const Dims& g, const float2* A, const float2* z, const float2* r, float2* w,
                                  double2* partial, unsigned* ticket, double2* alpha, int* err, int blocks, int variant,
                                  cudaStream_t st) {
-  if (variant == 2) {
-    if (g.dim == 2) launch_tma<2, 8, 2>(g, A, z, r, w, partial, ticket, alpha, err, blocks, st);
-    else launch_tma<3, 8, 2>(g, A, z, r, w, partial, ticket, alpha, err, blocks, st);
-  } else {
-    if (g.dim == 2) launch_tma<2, 16, 1>(g, A, z, r, w, partial, ticket, alpha, err, blocks, st);
-    else launch_tma<3, 16, 1>(g, A, z, r, w, partial, ticket, alpha, err, blocks, st);
-  }
+  launch_variant<kTmaMr>(g, A, z, r, w, nullptr, nullptr, partial, ticket, alpha, err, blocks, variant, st);
+}
+void launch_stencil_apply_tma(const Dims& g, const float2* A, const float2* x, float2* y, int* err, int blocks,
+                              int variant, cudaStream_t st) {
+  launch_variant<kTmaApply>(g, A, x, x, y, nullptr, nullptr, nullptr, nullptr, nullptr, err, blocks, variant, st);
+}
+void launch_stencil_residual_dinv_tma(const Dims& g, const float2* A, const float2* b, const float2* x,
+                                      const float2* dinv, float2* r, float2* z, int* err, int blocks, int variant,
+                                      cudaStream_t st) {
+  launch_variant<kTmaResid>(g, A, x, b, r, dinv, z, nullptr, nullptr, nullptr, err, blocks, variant, st);
 }
 
 }  // namespace adr

@@ -16,10 +16,16 @@ namespace adr {
 
 static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-int reduction_blocks(int64_t n) {
+// Blocks of a reduction over n entries with `values` sums per block: one per
+// 1024 entries (four grid-stride steps per thread), at most kMaxReduceBlocks.
+// Spreading small coarse-level vectors over more blocks (one per 256 entries)
+// measured slower: 699 against 606 us per coarsest solve.
+int reduction_blocks(int64_t n, int values) {
   int64_t b = (n + 1023) / 1024;
   if (b < 1) b = 1;
   if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
+  const int64_t cap = kPartialStride / (values > 0 ? values : 1);
+  if (b > cap) b = cap;
   return (int)b;
 }
 
@@ -40,6 +46,24 @@ __global__ void k_scale_inv_norm(const C<T>* w, C<T>* out, const double2* __rest
 template <typename T>
 void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, int64_t n, cudaStream_t st, int B) {
   count_launches(1), k_scale_inv_norm<T><<<dim3(blocks_for(n, 256), B), 256, 0, st>>>(w, out, nrm2, n);
+}
+
+// out = w / |w| and z = dinv .* out (the next Jacobi-preconditioned direction)
+template <typename T>
+__global__ void k_scale_dinv(const C<T>* w, C<T>* out, const C<T>* __restrict__ dinv, C<T>* z,
+                             const double2* __restrict__ nrm2, int64_t n) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  batch_shift(n, w, out, dinv, z);
+  const T inv = (T)nrm2[blockIdx.y].y;
+  const C<T> v = cscale(w[e], inv);
+  out[e] = v;
+  z[e] = cmul(dinv[e], v);
+}
+template <typename T>
+void launch_scale_dinv(const C<T>* w, C<T>* out, const C<T>* dinv, C<T>* z, const double2* nrm2, int64_t n,
+                       cudaStream_t st, int B) {
+  count_launches(1), k_scale_dinv<T><<<dim3(blocks_for(n, 256), B), 256, 0, st>>>(w, out, dinv, z, nrm2, n);
 }
 
 template <typename T>
@@ -373,7 +397,7 @@ __global__ void k_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_
 template <typename T>
 void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s, const ArnoldiState& st, int j,
                  cudaStream_t stream, int B) {
-  const dim3 grid(reduction_blocks(n), B);
+  const dim3 grid(reduction_blocks(n, k + 2), B);
   count_launches(1), k_cgs_pass1<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
   count_launches(1), k_cgs_pass2<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
   count_launches(1), k_cgs_pass3<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j);
@@ -385,7 +409,7 @@ void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, 
     launch_cgs2<T>(V, ld, k, w, n, s, st, j, stream, B);
     return;
   }
-  const dim3 grid(reduction_blocks(n), B);
+  const dim3 grid(reduction_blocks(n, k + 2), B);
   count_launches(1), k_sgs_dots_norm<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
   count_launches(1), k_sgs_update_test<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j, eta * eta);
   count_launches(1), k_sgs_reorth_dots<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
@@ -394,7 +418,7 @@ void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, 
 template <typename T>
 void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream, int B) {
   ArnoldiState dummy{};
-  count_launches(1), k_norm_start<T><<<dim3(reduction_blocks(n), B), 256, 0, stream>>>(b, n, s, st ? *st : dummy, st ? 1 : 0);
+  count_launches(1), k_norm_start<T><<<dim3(reduction_blocks(n, 1), B), 256, 0, stream>>>(b, n, s, st ? *st : dummy, st ? 1 : 0);
 }
 template <typename T>
 void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n,
@@ -410,6 +434,7 @@ void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, c
 
 #define ADR_INSTANTIATE_KRYLOV(T)                                                                                        \
   template void launch_scale_inv_norm<T>(const C<T>*, C<T>*, const double2*, int64_t, cudaStream_t, int);               \
+  template void launch_scale_dinv<T>(const C<T>*, C<T>*, const C<T>*, C<T>*, const double2*, int64_t, cudaStream_t, int); \
   template void launch_copy<T>(const C<T>*, C<T>*, int64_t, cudaStream_t);                                               \
   template void launch_zero<T>(C<T>*, int64_t, cudaStream_t);                                                            \
   template void launch_cmul_vec<T>(const C<T>*, const C<T>*, C<T>*, int64_t, cudaStream_t);                              \

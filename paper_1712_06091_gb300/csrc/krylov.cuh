@@ -48,7 +48,7 @@ __host__ __device__ inline ArnoldiState arnoldi_at(ArnoldiState s, int pb) {
   return s;
 }
 
-int reduction_blocks(int64_t n);
+int reduction_blocks(int64_t n, int values);
 
 // Scratch shared by the fused reductions (all launches on one stream).
 struct KrylovScratch {
@@ -98,6 +98,9 @@ void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, c
 // out = w * (1 / |w|) with the reciprocal norm from s.nrm2 (per problem).
 template <typename T> void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, int64_t n, cudaStream_t st,
                                                  int B = 1);
+// out = w * (1 / |w|) and z = dinv .* out (per problem).
+template <typename T> void launch_scale_dinv(const C<T>* w, C<T>* out, const C<T>* dinv, C<T>* z, const double2* nrm2,
+                                             int64_t n, cudaStream_t st, int B = 1);
 // Whole-array elementwise operations (n = all problems' entries).
 template <typename T> void launch_copy(const C<T>* a, C<T>* b, int64_t n, cudaStream_t st);
 template <typename T> void launch_zero(C<T>* a, int64_t n, cudaStream_t st);
