@@ -78,7 +78,8 @@ def parse():
 
 
 def dist_env():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1712_06091_gb300 import shard
+    return shard.env()
 
 
 def rank_source(n, rank):
@@ -299,11 +300,8 @@ def run_ours(args):
     launches = gpu.kernel_launches() - launches0
     k_count, k_ms = op.profile_read()
     op.profile("none")
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_1712_06091_gb300 import shard
+    ms = shard.max_over_ranks(ev0.elapsed_time(ev1), device=dev)
     its = [i["iterations"] for i in infos]
     res = max(i["rel_residual"] for i in infos)
     assert res <= args.tol, f"solve did not reach the tolerance: {res}"
@@ -438,13 +436,21 @@ def batch_problems(n, count, seed=3):
 
 def run_batched(args):
     import torch
+    import torch.distributed as dist
     from paper_1712_06091_gb300 import adr as gpu
-    from paper_1712_06091_gb300 import autotune
-    torch.cuda.set_device(0)
+    from paper_1712_06091_gb300 import autotune, shard
+    rank, world, local = shard.env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream()
     groups = []
     for n in BATCH_GRIDS:
+        # this rank's share of the grid's sources (independent problems: no exchange)
+        mine = shard.partition(BATCH_SOURCES, rank, world)
         P, probs = batch_problems(n, BATCH_SOURCES)
+        probs = [probs[i] for i in mine]
         params = gpu.default_params(precision="f32", levels=BENCH_LEVELS, restart=BENCH_RESTART)
         tuned = autotune.tune(P.n, P.h, probs, params=params)
         params.relax_blocks = tuned["relax_blocks"]
@@ -463,15 +469,19 @@ def run_batched(args):
         step()
     torch.cuda.synchronize()
     launches0 = gpu.kernel_launches()
-    with ClockSampler(0) as clocks:
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clocks:
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(args.steps):
             its = step()
         ev1.record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
     launches = gpu.kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
+    ms = shard.max_over_ranks(ev0.elapsed_time(ev1), device=dev)
     nprob = len(BATCH_GRIDS) * BATCH_SOURCES
     value = nprob * args.steps / (ms / 1e3)
     for s in solvers:
@@ -496,8 +506,12 @@ def run_batched(args):
         plain_its.append(info["iterations"])
         op.close()
     plain_value = nprob / (plain_ms / 1e3)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     out = {
-        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 cycle + f64 Krylov", "data": "synthetic (layered model resampled per grid; tau1 from the library's "
                                                  "travel-time kernel)",
