@@ -35,6 +35,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ADR solves/s to 1e-8 rel. residual at 256^2x128 cells (257x257x129 nodes)"
 UNIT = "solves/s"
+SL_METRIC = ("standard Helmholtz solves/s (shifted-Laplacian cycle) to 1e-8 rel. residual at 256^2x128 cells "
+             "(257x257x129 nodes)")
+
+
+def metric_for(args):
+    return SL_METRIC if args.method == "helmholtz-sl" else METRIC
 WORKLOADS = {
     "layered3d_257x257x129": (257, 257, 129),
     "layered3d_193x193x97": (193, 193, 97),
@@ -48,6 +54,11 @@ BENCH_LEVELS = 3
 # Outer FGMRES restart: 8 was fastest on GB300 at 257x257x129 (458 ms against
 # 505 ms for 20, the same 70 iterations; 5, the paper's, took 73 iterations).
 BENCH_RESTART = 8
+# Shifted-Laplacian comparison (Sec. 3, alpha = 0.2 as in Sec. 4); 4 levels
+# measured fastest for it on the 257x257x129 model (49 iterations, against 75
+# with 3 levels and 47 with 5 at a higher cost per cycle).
+SL_SHIFT = 0.2
+SL_LEVELS = 4
 # The kernel whose roofline is reported, and its algorithmic bytes per node of
 # level 1: the 81-point stencil stored as 27 complex box entries and 54
 # imaginary parts (float32), z and r read, w written (complex float32).
@@ -68,7 +79,13 @@ def parse():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=400)
-    ap.add_argument("--levels", type=int, default=BENCH_LEVELS)
+    ap.add_argument("--levels", type=int, default=None,
+                    help=f"grid levels (default {BENCH_LEVELS} for the ADR solve, {SL_LEVELS} for the shifted Laplacian)")
+    ap.add_argument("--method", default="adr-upwind", choices=["adr-upwind", "helmholtz-sl"],
+                    help="adr-upwind: H_2up a = q with the (1-beta) H_2up + beta H_1up cycle; helmholtz-sl: the "
+                         "standard Helmholtz matrix (tau1 = 0) with the shifted-Laplacian cycle (Eq. shift)")
+    ap.add_argument("--shift", type=float, default=SL_SHIFT)
+    ap.add_argument("--no-comparison", action="store_true")
     ap.add_argument("--restart", type=int, default=None)
     ap.add_argument("--cycle", default=None)
     ap.add_argument("--sweeps", default=None, help="comma-separated relaxations per level")
@@ -91,7 +108,11 @@ def rank_source(n, rank):
 
 def build_params(args):
     from paper_1712_06091_gb300 import adr as gpu
-    kw = {"precision": args.precision, "levels": args.levels, "restart": args.restart or BENCH_RESTART}
+    sl = args.method == "helmholtz-sl"
+    kw = {"precision": args.precision, "levels": args.levels or (SL_LEVELS if sl else BENCH_LEVELS),
+          "restart": args.restart or BENCH_RESTART}
+    if sl:
+        kw["shift"] = args.shift
     if args.cycle:
         kw["cycle"] = args.cycle
     if args.sweeps:
@@ -209,19 +230,22 @@ def measured_traffic_per_node():
 SAMPLE_N = (33, 33, 17)
 
 
-def oracle_sample(pd, tol):
+def oracle_sample(pd, tol, method="adr-upwind"):
     """One oracle solve (setup + FGMRES + cycle + reconstruction) of the layered 3D model
-    resampled to 33 x 33 x 17 nodes.  Returns (seconds, nodes, iterations)."""
+    resampled to 33 x 33 x 17 nodes (helmholtz-sl: tau1 = 0 and the shifted cycle).
+    Returns (seconds, nodes, iterations)."""
+    import numpy as np
     from oracle import adr as oadr
     from oracle import eikonal, krylov
     from oracle import multigrid as omg
     from paper_1712_06091_gb300 import workloads as W
     P = W.layered_3d(SAMPLE_N)
     g = oadr.Grid(P.n, P.h)
-    tau1 = eikonal.factored_fast_marching(g, P.kappa, P.src, order=2)
+    sl = method == "helmholtz-sl"
+    tau1 = np.zeros(g.N) if sl else eikonal.factored_fast_marching(g, P.kappa, P.src, order=2)
     t0 = time.perf_counter()
     A = oadr.assemble_adr(g, P.src, P.omega, P.kappa, P.gamma, tau1, "2up")
-    Ap = oadr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, tau1, pd["beta"])
+    Ap = oadr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, tau1, pd["beta"], shift=pd.get("shift", 0.0))
     hier = omg.build_hierarchy(Ap, P.n, pd["levels"])
     prm = omg.CycleParams(cycle=pd["cycle"], relax=pd["relax"], pre=pd["pre_sweeps"], post=pd["post_sweeps"],
                           weights=pd["jacobi_weight"], coarse_iterations=pd["coarse_iterations"],
@@ -261,6 +285,8 @@ def run_ours(args):
     kappa = torch.from_numpy(P.kappa).to(dev)
     gamma = torch.from_numpy(P.gamma).to(dev)
     tau1, sweeps = gpu.traveltime(P.n, P.h, P.src, kappa)
+    if args.method == "helmholtz-sl":
+        tau1 = torch.zeros_like(tau1)   # tau = 0: H_2up is the standard Helmholtz matrix, u = a
     op = gpu.Operator(P.n, P.h, P.src, P.omega, kappa, tau1, gamma, params=params, device=dev)
     levels = op.info()["levels"]
     a = torch.empty(P.N, dtype=torch.complex128, device=dev)
@@ -341,7 +367,7 @@ def run_ours(args):
     if not args.no_cpu_baseline and rank == 0:
         secs, runs = 0.0, 0
         while secs < 10.0:      # at least ~10 s of oracle work
-            s1, nodes, its_s = oracle_sample(gpu.params_dict(params), args.tol)
+            s1, nodes, its_s = oracle_sample(gpu.params_dict(params), args.tol, args.method)
             secs, runs = secs + s1, runs + 1
         secs /= runs
         cpu = {"value": scale_to_workload(secs, nodes, its_s, P.N, float(np.mean(its))), "unit": UNIT, "cores": 1,
@@ -351,14 +377,19 @@ def run_ours(args):
                          f"iterations in {secs:.1f} s, scaled by unknowns*iterations to {P.N} nodes x "
                          f"{np.mean(its):.1f} iterations (mean of {runs} runs)"}
 
+    comparison = None
+    if not args.no_comparison and rank == 0 and args.method == "adr-upwind":
+        comparison = sl_comparison(P, kappa, gamma, tau1, args, dev)
+
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": metric_for(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 cycle + f64 Krylov" if args.precision == "f32" else "f64",
-            "data": "synthetic (seeded layered-gradient model with Gaussian anomalies; tau1 from the library's "
-                    "travel-time kernel)",
-            "config": {"workload": args.workload, "nodes": P.N, "grid": list(P.n), "spacing_km": P.h[0],
+            "data": "synthetic (seeded layered-gradient model with Gaussian anomalies; " +
+                    ("tau1 = 0: the standard Helmholtz matrix)" if args.method == "helmholtz-sl" else
+                     "tau1 from the library's travel-time kernel)"),
+            "config": {"workload": args.workload, "method": args.method, "nodes": P.N, "grid": list(P.n), "spacing_km": P.h[0],
                        "omega": P.omega, "source": list(src), "tol": args.tol, "params": gpu.params_dict(params),
                        "levels": [lv["n"] for lv in levels], "iterations": its, "max_rel_residual": res,
                        "l2": "no flush: inputs and working set (~9 GB) exceed L2", "wall_s": t_wall,
@@ -369,10 +400,40 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks.summary(),
         }
+        if comparison:
+            out["comparison"] = comparison
         print(json.dumps(out))
     op.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def sl_comparison(P, kappa, gamma, tau1, args, dev):
+    """The paper's comparison system on the same medium and source: the standard
+    Helmholtz matrix (tau1 = 0) solved to the same tolerance with the
+    shifted-Laplacian cycle (Eq. shift, alpha = SL_SHIFT).  One warm-up solve,
+    then one solve timed with CUDA events; the ADR solve's iterations beside it."""
+    import torch
+    from paper_1712_06091_gb300 import adr as gpu
+    params = gpu.default_params(precision=args.precision, levels=SL_LEVELS, restart=args.restart or BENCH_RESTART,
+                                shift=args.shift)
+    zero = torch.zeros_like(tau1)
+    op = gpu.Operator(P.n, P.h, P.src, P.omega, kappa, zero, gamma, params=params, device=dev)
+    a = torch.empty(P.N, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    op.solve(tol=args.tol, maxit=4 * args.maxit, out=a, raise_on_fail=False)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    _, info = op.solve(tol=args.tol, maxit=4 * args.maxit, out=a, raise_on_fail=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    op.close()
+    return {"method": "standard Helmholtz (tau1 = 0), shifted-Laplacian cycle", "shift": args.shift,
+            "levels": SL_LEVELS, "restart": params.restart, "iterations": info["iterations"],
+            "rel_residual": info["rel_residual"], "ms_per_solve": ev0.elapsed_time(ev1),
+            "note": "solve only (operator setup outside the timed solve); same tolerance, medium and source"}
 
 
 def run_reference(args):
@@ -384,18 +445,19 @@ def run_reference(args):
     from paper_1712_06091_gb300.adr import params_dict
     pd = params_dict(build_params(args))
     N = int(np.prod(WORKLOADS[args.workload]))
-    full_its = 70.0   # iterations of the GPU solve at 257x257x129 with this cycle (bench config, measured)
+    # iterations of the GPU solve at 257x257x129 with this cycle (bench config, measured)
+    full_its = 49.0 if args.method == "helmholtz-sl" else 70.0
     for _ in range(min(args.warmup, 1)):
-        oracle_sample(pd, args.tol)
+        oracle_sample(pd, args.tol, args.method)
     secs, its = [], []
     for _ in range(args.steps):
-        s, nodes, k = oracle_sample(pd, args.tol)
+        s, nodes, k = oracle_sample(pd, args.tol, args.method)
         secs.append(s)
         its.append(k)
     value = scale_to_workload(float(np.mean(secs)), nodes, float(np.mean(its)), N, full_its)
     sample = (f"oracle solve per step at {SAMPLE_N} nodes ({nodes} nodes x {np.mean(its):.0f} iterations in "
               f"{np.mean(secs):.1f} s), scaled by unknowns*iterations to {N} nodes x {full_its:.0f} iterations")
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+    out = {"impl": "reference", "metric": metric_for(args), "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "sample": list(SAMPLE_N), "assumed_full_iterations": full_its,

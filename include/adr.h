@@ -111,6 +111,14 @@ typedef struct adr_params {
                                           buffers each; 0: plain loads.  Same per-node
                                           arithmetic; the weight's block sums follow the
                                           kernel's grid.  Default 1 */
+  double shift;                        /* complex shift alpha of the cycle's operator
+                                          (Eq. shift): the multigrid hierarchy is built
+                                          from the preconditioner minus i alpha w^2
+                                          kappa^2 on its diagonal, the outer operator is
+                                          unchanged.  With tau1 = 0 this is the shifted-
+                                          Laplacian preconditioner of the standard
+                                          Helmholtz matrix (Sec. 3, alpha = 0.2 in
+                                          Sec. 4).  0..100, default 0 (no shift) */
 } adr_params_t;
 
 #define ADR_COARSE_AUTO 0      /* cluster up to 32768 nodes, else one block up to 8192, else kernels */

@@ -296,11 +296,16 @@ def assemble_helmholtz(grid, omega, kappa, gamma):
     return _assemble(grid, lambda j: helmholtz_row(grid, omega, kappa, gamma, j))
 
 
-def assemble_preconditioner(grid, src, omega, kappa, gamma, tau1, beta=0.25, near_radius=1):
-    """(1 - beta) H_2up + beta H_1up  (Eq. precADRup)."""
+def assemble_preconditioner(grid, src, omega, kappa, gamma, tau1, beta=0.25, near_radius=1, shift=0.0):
+    """(1 - beta) H_2up + beta H_1up  (Eq. precADRup), minus i shift w^2 kappa^2
+    on the diagonal: the complex shift of Eq. shift (with tau = 0 and
+    shift = alpha this is the shifted-Laplacian preconditioner)."""
     a2 = assemble_adr(grid, src, omega, kappa, gamma, tau1, "2up", near_radius)
     a1 = assemble_adr(grid, src, omega, kappa, gamma, tau1, "1up", near_radius)
-    return ((1.0 - beta) * a2 + beta * a1).tocsr()
+    A = (1.0 - beta) * a2 + beta * a1
+    if shift:
+        A = A - 1j * shift * omega * omega * sp.diags(np.asarray(kappa, dtype=float) ** 2)
+    return A.tocsr()
 
 
 def point_source_rhs(grid, src):

@@ -59,6 +59,7 @@ class Params(ctypes.Structure):
         ("relax_blocks", ctypes.c_int),
         ("coarse_solver", ctypes.c_int),
         ("tma", ctypes.c_int),
+        ("shift", ctypes.c_double),
     ]
 
 

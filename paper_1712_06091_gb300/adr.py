@@ -57,6 +57,7 @@ def params_dict(p: L.Params) -> dict:
         "kcycle_iterations": p.kcycle_iterations, "restart": p.restart,
         "precision": ["f64", "f32"][p.precond_precision], "reorth_eta": p.reorth_eta,
         "relax_blocks": p.relax_blocks, "coarse_solver": p.coarse_solver, "tma": p.tma,
+        "shift": p.shift,
     }
 
 

@@ -261,6 +261,10 @@ void launch_coefficients(const Dims& g, const FineInputs& in, double* const gd[3
                          double2* rho, double* tau, double2* src_row, cudaStream_t st);
 // float64 -> float32 copy of n reals.
 void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+// The cycle's coefficients under the complex shift of Eq. shift: rho_s = rho -
+// i alpha w^2 kappa^2 per node and the source row with the same diagonal change.
+void launch_shift(const Dims& g, const FineInputs& in, double alpha, const double2* rho, const double2* src_row,
+                  double2* rho_s, double2* src_row_s, cudaStream_t st);
 
 // Level-0 operations; x, y, b complex of T.
 template <typename T> void launch_fine_apply(const Dims& g, const FineOp<T>& f, const C<T>* x, C<T>* y, cudaStream_t st);

@@ -132,6 +132,11 @@ struct Op {
   float* gf[3] = {nullptr, nullptr, nullptr};
   float* tf[3] = {nullptr, nullptr, nullptr};
   float* rhof = nullptr;  // float2 view
+  // shifted copies for the cycle (Eq. shift; only when params.shift != 0)
+  double2* rhos = nullptr;
+  float* rhosf = nullptr;
+  double2* srows = nullptr;
+  float* srowsf = nullptr;
   Hier<double> h64;
   Hier<float> h32;
   // outer FGMRES
@@ -303,6 +308,12 @@ static void plan(Op& op, Arena& a) {
   op.tau = a.take<double>(NB);
   op.srow = a.take<double2>(kCross3 * B);
   op.srowf = a.take<float>(2 * kCross3 * B);
+  if (op.p.shift != 0.0) {
+    op.rhos = a.take<double2>(NB);
+    op.rhosf = a.take<float>(2 * NB);
+    op.srows = a.take<double2>(kCross3 * B);
+    op.srowsf = a.take<float>(2 * kCross3 * B);
+  }
   if (op.p.precond_precision == ADR_F64) plan_hierarchy(op, op.h64, a);
   else plan_hierarchy(op, op.h32, a);
   const int m = op.p.restart;
@@ -346,8 +357,14 @@ template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool 
     }
   }
   f.dyn = op.dyn;
-  f.rho = f32 ? (const C<T>*)(const void*)op.rhof : (const C<T>*)(const void*)op.rho;
-  f.src_row = f32 ? (const C<T>*)(const void*)op.srowf : (const C<T>*)(const void*)op.srow;
+  const bool shifted = scheme == ADR_SCHEME_PREC && op.rhos;   // Eq. shift applies to the cycle's operator only
+  if (shifted) {
+    f.rho = f32 ? (const C<T>*)(const void*)op.rhosf : (const C<T>*)(const void*)op.rhos;
+    f.src_row = f32 ? (const C<T>*)(const void*)op.srowsf : (const C<T>*)(const void*)op.srows;
+  } else {
+    f.rho = f32 ? (const C<T>*)(const void*)op.rhof : (const C<T>*)(const void*)op.rho;
+    f.src_row = f32 ? (const C<T>*)(const void*)op.srowf : (const C<T>*)(const void*)op.srow;
+  }
   f.near = op.p.near_source;
   set_scheme(f, scheme, op.p.beta);
   return f;
@@ -591,6 +608,9 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
     double* td[3] = {nullptr, nullptr, nullptr};
     for (int d = 0; d < op.dim; ++d) { gd[d] = op.gd[d] + o; td[d] = op.td[d] + o; }
     launch_coefficients(g1, in, gd, td, op.rho + o, op.tau + o, op.srow + (int64_t)pb * kCross3, op.st);
+    if (op.rhos)
+      launch_shift(g1, in, op.p.shift, op.rho + o, op.srow + (int64_t)pb * kCross3, op.rhos + o,
+                   op.srows + (int64_t)pb * kCross3, op.st);
   }
   for (int d = 0; d < op.dim; ++d) {
     launch_to_f32(op.gd[d], op.gf[d], NB, op.st);
@@ -598,6 +618,10 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
   }
   launch_to_f32((const double*)op.rho, op.rhof, 2 * NB, op.st);
   launch_to_f32((const double*)op.srow, op.srowf, 2 * kCross3 * op.B, op.st);
+  if (op.rhos) {
+    launch_to_f32((const double*)op.rhos, op.rhosf, 2 * NB, op.st);
+    launch_to_f32((const double*)op.srows, op.srowsf, 2 * kCross3 * op.B, op.st);
+  }
   launch_fine_store_rows(op.g0, make_fine<double>(op, ADR_SCHEME_2UP, false), op.rows2up, op.st);
   ADR_TRY(check_launch("coefficients"));
   ADR_TRY(op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32));
@@ -691,6 +715,7 @@ static int validate_params(const adr_params_t& p) {
   if (p.coarse_solver < ADR_COARSE_AUTO || p.coarse_solver > ADR_COARSE_GRID)
     return fail(ADR_ERR_ARG, "unknown coarse_solver");
   if (p.tma < 0 || p.tma > 2) return fail(ADR_ERR_ARG, "tma must be 0, 1 or 2");
+  if (!(p.shift >= 0.0 && p.shift <= 100.0)) return fail(ADR_ERR_ARG, "shift must be in [0, 100]");
   for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
     if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
       return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");

@@ -107,6 +107,29 @@ void launch_coefficients(const Dims& g, const FineInputs& in, double* const gd[3
   count_launches(1), k_source_row<<<1, 32, 0, st>>>(g, in, tau, src_row);
 }
 
+// Eq. shift: the mass term -i alpha w^2 kappa^2 joins the reaction coefficient
+// (the diagonal of every row) and the diagonal of the source row.
+__global__ void k_shift(Dims g, FineInputs in, double alpha, const double2* rho, const double2* srow, double2* rho_s,
+                        double2* srow_s) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  const double m = alpha * in.omega * in.omega;
+  const double2 r = rho[j];
+  rho_s[j] = make_double2(r.x, r.y - m * (in.kappa[j] * in.kappa[j]));
+  if (j < kCross3) {
+    double2 e = srow[j];
+    if (j == 0) {
+      const int64_t js = in.src[0] + g.s1 * in.src[1] + g.s2 * in.src[2];
+      e.y -= m * (in.kappa[js] * in.kappa[js]);
+    }
+    srow_s[j] = e;
+  }
+}
+void launch_shift(const Dims& g, const FineInputs& in, double alpha, const double2* rho, const double2* src_row,
+                  double2* rho_s, double2* src_row_s, cudaStream_t st) {
+  count_launches(1), k_shift<<<blocks_for(g.N, 256), 256, 0, st>>>(g, in, alpha, rho, src_row, rho_s, src_row_s);
+}
+
 __global__ void k_to_f32(const double* s, float* d, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) d[i] = (float)s[i];

@@ -1,5 +1,6 @@
 """Shared GPU-test helpers: seeded problems, their oracle matrices, and the
 conversion of library parameters to the oracle's cycle settings."""
+import copy
 import functools
 
 import numpy as np
@@ -29,15 +30,21 @@ def _with_fm(P):
 
 @functools.lru_cache(maxsize=None)
 def problem(name):
+    """A case by name; the suffix ":helmholtz" gives the same medium and source
+    with tau1 = 0, i.e. the standard Helmholtz matrix (Sec. 1)."""
+    if name.endswith(":helmholtz"):
+        P = copy.copy(problem(name[: -len(":helmholtz")]))
+        P.tau1 = np.zeros_like(P.tau1)
+        return P
     return CASES[name]()
 
 
 @functools.lru_cache(maxsize=None)
-def oracle_matrix(name, scheme, near=1, beta=0.25):
+def oracle_matrix(name, scheme, near=1, beta=0.25, shift=0.0):
     P = problem(name)
     g = adr.Grid(P.n, P.h)
     if scheme == "prec":
-        return adr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, P.tau1, beta, near)
+        return adr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, P.tau1, beta, near, shift)
     return adr.assemble_adr(g, P.src, P.omega, P.kappa, P.gamma, P.tau1, scheme, near)
 
 

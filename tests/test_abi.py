@@ -46,4 +46,9 @@ def test_defaults_and_argument_errors(adrlib):
     p.restart = 0
     rc = adrlib.adr_operator_create(2, n, h, s, 1.0, dummy, dummy, dummy, ctypes.byref(p), None, ctypes.byref(out))
     assert rc == _lib.ADR_ERR_ARG and b"restart" in adrlib.adr_last_error()
+    assert adrlib.adr_params_default(ctypes.byref(p)) == 0 and p.shift == 0.0
+    for bad in (-0.1, float("nan"), 101.0):
+        p.shift = bad
+        rc = adrlib.adr_operator_create(2, n, h, s, 1.0, dummy, dummy, dummy, ctypes.byref(p), None, ctypes.byref(out))
+        assert rc == _lib.ADR_ERR_ARG and b"shift" in adrlib.adr_last_error()
     assert adrlib.adr_version() == b"0.1.0"

@@ -210,3 +210,26 @@ def test_reconstruct_phase():
     tau = adr.travel_time(g, P.src, P.tau1)
     assert np.allclose(np.abs(u), np.abs(a), rtol=0, atol=1e-12)
     assert np.allclose(u * np.exp(1j * P.omega * tau), a, rtol=1e-14, atol=1e-12)
+
+
+def test_shifted_laplacian_preconditioner():
+    """Eq. shift: with tau = 0 the preconditioner is the Helmholtz matrix of
+    Eq. HelmholtzLinSystem minus i alpha w^2 kappa^2 on the diagonal; alpha = 0
+    gives the unshifted operator; the shift moves every Rayleigh quotient down
+    in the complex plane by alpha w^2 <kappa^2> (the damping that makes the
+    multigrid cycle work, Sec. 3)."""
+    P = W.marine_2d((17, 17))
+    g = adr.Grid(P.n, P.h)
+    tau1 = np.zeros(g.N)
+    H = adr.assemble_helmholtz(g, P.omega, P.kappa, P.gamma)
+    A0 = adr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, tau1)
+    A5 = adr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, tau1, shift=0.5)
+    assert abs(A0 - H).max() <= 1e-12 * abs(H).max()
+    D = (A5 - H).tocsr()
+    assert D.nnz == g.N and np.allclose(D.diagonal(), -0.5j * P.omega ** 2 * P.kappa ** 2, rtol=1e-14, atol=0)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)
+    q0 = np.vdot(x, A0 @ x) / np.vdot(x, x)
+    q5 = np.vdot(x, A5 @ x) / np.vdot(x, x)
+    expect = 0.5 * P.omega ** 2 * np.vdot(x, P.kappa ** 2 * x).real / np.vdot(x, x).real
+    assert abs((q0 - q5).imag - expect) <= 1e-10 * expect and abs((q0 - q5).real) <= 1e-10 * abs(q0)
