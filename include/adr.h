@@ -119,6 +119,21 @@ typedef struct adr_params {
                                           Laplacian preconditioner of the standard
                                           Helmholtz matrix (Sec. 3, alpha = 0.2 in
                                           Sec. 4).  0..100, default 0 (no shift) */
+  int scheme;                          /* the solved system (outer FGMRES operator):
+                                          ADR_SCHEME_2UP (Eq. ADRLinSystemUpwind, default),
+                                          ADR_SCHEME_1UP (Eq. 1up) or ADR_SCHEME_CEN
+                                          (Eq. ADRLinSystemCentral) */
+  int prec_scheme;                     /* the cycle's finest-grid operator before the
+                                          shift: ADR_SCHEME_PREC (the blend of
+                                          Eq. precADRup, default; beta = 1 gives H_1up)
+                                          or ADR_SCHEME_2UP / 1UP / CEN */
+  int rescale;                         /* 1: the cycle is built on M A M^{-1}, M =
+                                          diag(exp(-i w tau)) (the system rescaled as
+                                          Helmholtz, Eq. ADRcenRescaled), and applied as
+                                          z = M^{-1} K (M v); the outer iteration stays on
+                                          the amplitude.  Stage 2 of Alg. ADRlong is
+                                          scheme = prec_scheme = ADR_SCHEME_CEN, shift =
+                                          0.2, rescale = 1.  Default 0 */
 } adr_params_t;
 
 #define ADR_COARSE_AUTO 0      /* cluster up to 32768 nodes, else one block up to 8192, else kernels */
@@ -234,7 +249,8 @@ int adr_vcycle(adr_op_t op, const void* r, void* z);
 /* q_hat = delta_{x0} / prod(h) (float64 complex, N entries, Sec. 4.1). */
 int adr_point_source_rhs(adr_op_t op, void* q);
 
-/* Solves H_2up a = rhs by right-preconditioned flexible GMRES(m).
+/* Solves A a = rhs by right-preconditioned flexible GMRES(m), A the system
+ * params.scheme selects (H_2up by default; "H_2up" below stands for it).
  *   rhs: float64 complex device vector, or NULL for the point source.
  *   a: float64 complex device vector; input initial guess if use_x0 != 0,
  *      output solution.
@@ -245,6 +261,22 @@ int adr_point_source_rhs(adr_op_t op, void* q);
  *   return code is ADR_ERR_NOT_CONVERGED if any problem missed the tolerance. */
 int adr_solve(adr_op_t op, const void* rhs, void* a, int use_x0, double tol, int maxit,
               adr_solve_info_t* info);
+
+/* Alg. ADRlong, the two-stage solve: stage 1 runs FGMRES on stage1's system
+ * from a zero guess until its relative residual is <= tol1 or maxit1
+ * iterations have run (Sec. 4.2 uses 1e-2 and 5; ending at maxit1 is not an
+ * error); its iterate starts stage 2, which runs to tol / maxit.  For the
+ * central ADR system, stage1 is scheme = ADR_SCHEME_1UP with the cycle on
+ * H_1up (prec_scheme ADR_SCHEME_PREC, beta = 1) and stage2 is scheme =
+ * prec_scheme = ADR_SCHEME_CEN, shift = 0.2, rescale = 1.
+ *   The two operators must share grid, spacing, problems, sources and
+ *   frequencies (else ADR_ERR_ARG).  rhs: NULL for the point source, else a
+ *   float64 complex device vector of B*N entries.  a: float64 complex, B*N,
+ *   output.  info: NULL or 2*B entries (stage 1's B, then stage 2's B).
+ *   Returns stage 2's status (as adr_solve), or stage 1's error other than
+ *   ADR_ERR_NOT_CONVERGED. */
+int adr_solve_two_stage(adr_op_t stage1, adr_op_t stage2, const void* rhs, void* a, double tol1, int maxit1,
+                        double tol, int maxit, adr_solve_info_t* info);
 
 /* u = a exp(-i w tau) (Eq. new_u), float64 complex device vectors. */
 int adr_reconstruct(adr_op_t op, const void* a, void* u);

@@ -22,6 +22,9 @@ travel time and amplitude":
                  Jacobi-preconditioned GMRES coarsest solve (Sec. 3.1).
 * `krylov`    -- flexible GMRES with classical Gram-Schmidt applied twice.
 * `eikonal`   -- factored-eikonal fast marching (Eq. factoredEikonal).
+* `twostage`  -- the two-stage solve of the central ADR system
+                 (Algorithm ADRlong): a low-accuracy H_1up solve, then the
+                 shifted-Laplacian FGMRES on the system rescaled as Helmholtz.
 * `adjoint`   -- receiver misfit and its slowness gradient by the adjoint
                  state of the assembled system (not in the paper).
 

@@ -32,7 +32,7 @@ EXPORTS = (
     "adr_params_default", "adr_operator_create", "adr_operator_update", "adr_batch_create", "adr_batch_update",
     "adr_operator_destroy", "adr_operator_info",
     "adr_coefficients", "adr_apply", "adr_level_stencil", "adr_vcycle", "adr_point_source_rhs",
-    "adr_solve", "adr_reconstruct", "adr_solve_host", "adr_adjoint_solve", "adr_apply_adjoint", "adr_vcycle_adjoint",
+    "adr_solve", "adr_solve_two_stage", "adr_reconstruct", "adr_solve_host", "adr_adjoint_solve", "adr_apply_adjoint", "adr_vcycle_adjoint",
     "adr_receivers", "adr_kappa_gradient", "adr_traveltime", "adr_traveltime_static", "adr_profile_kernel",
     "adr_profile_read",
     "adr_kernel_launches", "adr_last_error", "adr_version",
@@ -60,6 +60,9 @@ class Params(ctypes.Structure):
         ("coarse_solver", ctypes.c_int),
         ("tma", ctypes.c_int),
         ("shift", ctypes.c_double),
+        ("scheme", ctypes.c_int),
+        ("prec_scheme", ctypes.c_int),
+        ("rescale", ctypes.c_int),
     ]
 
 
@@ -110,6 +113,7 @@ def load():
         "adr_vcycle": [vp, vp, vp],
         "adr_point_source_rhs": [vp, vp],
         "adr_solve": [vp, vp, vp, i, d, i, ctypes.POINTER(SolveInfo)],
+        "adr_solve_two_stage": [vp, vp, vp, vp, d, i, d, i, ctypes.POINTER(SolveInfo)],
         "adr_reconstruct": [vp, vp, vp],
         "adr_solve_host": [i, ip, dp, ip, d, vp, vp, vp, ctypes.POINTER(Params), d, i, vp, vp, vp,
                            ctypes.POINTER(SolveInfo)],

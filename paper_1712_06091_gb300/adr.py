@@ -31,6 +31,8 @@ def default_params(**overrides) -> L.Params:
             p.cycle = L.CYCLES[val] if isinstance(val, str) else int(val)
         elif key == "relax":
             p.relax = L.RELAX[val] if isinstance(val, str) else int(val)
+        elif key in ("scheme", "prec_scheme"):
+            setattr(p, key, L.SCHEMES[val] if isinstance(val, str) else int(val))
         elif key == "coarse_solver":
             p.coarse_solver = L.COARSE_SOLVERS[val] if isinstance(val, str) else int(val)
         elif key in ("precision", "precond_precision"):
@@ -57,8 +59,12 @@ def params_dict(p: L.Params) -> dict:
         "kcycle_iterations": p.kcycle_iterations, "restart": p.restart,
         "precision": ["f64", "f32"][p.precond_precision], "reorth_eta": p.reorth_eta,
         "relax_blocks": p.relax_blocks, "coarse_solver": p.coarse_solver, "tma": p.tma,
-        "shift": p.shift,
+        "shift": p.shift, "scheme": _SCHEME_NAMES[p.scheme], "prec_scheme": _SCHEME_NAMES[p.prec_scheme],
+        "rescale": p.rescale,
     }
+
+
+_SCHEME_NAMES = {v: k for k, v in L.SCHEMES.items()}
 
 
 def _ptr(t):
@@ -281,6 +287,38 @@ def traveltime(n, h, src, kappa, max_sweeps=None, device="cuda", stream=None):
     L.check(lib.adr_traveltime(dim, nn, hh, ss, _ptr(k), _ptr(tau1), int(limit), ctypes.c_void_p(st.cuda_stream),
                                ctypes.byref(sweeps)))
     return tau1, sweeps.value
+
+
+def solve_two_stage(stage1, stage2, rhs=None, tol1=1e-2, maxit1=5, tol=1e-8, maxit=500, out=None,
+                    raise_on_fail=True):
+    """adr_solve_two_stage (Alg. ADRlong): (a, [stage-1 infos], [stage-2 infos]).
+
+    Stage 1 solves stage1's system from zero to tol1 or maxit1 iterations; its
+    iterate starts stage 2's solve to tol.  Both are Operator / BatchOperator
+    objects on the same grid, sources and frequencies."""
+    B = getattr(stage1, "problems", 1)
+    a = out if out is not None else torch.empty(stage2.N, dtype=torch.complex128, device=stage2.device)
+    stage2._vec(a, torch.complex128)
+    rp = ctypes.c_void_p(0) if rhs is None else _ptr(stage2._vec(rhs.reshape(-1), torch.complex128))
+    info = (L.SolveInfo * (2 * B))()
+    rc = stage2._lib.adr_solve_two_stage(stage1._h, stage2._h, rp, _ptr(a), float(tol1), int(maxit1), float(tol),
+                                         int(maxit), info)
+    L.check(rc, () if raise_on_fail else (L.ADR_ERR_NOT_CONVERGED,))
+    d = [{"iterations": s.iterations, "restarts": s.restarts, "rel_residual": s.rel_residual,
+          "rel_estimate": s.rel_estimate, "status": s.status} for s in info]
+    return a, d[:B], d[B:]
+
+
+def central_two_stage_params(**overrides):
+    """Parameters of the two stages of Alg. ADRlong for the central ADR system:
+    stage 1 = H_1up with its own cycle (beta = 1), stage 2 = H_cen with the
+    shifted (alpha = 0.2, Sec. 4.2) cycle on the system rescaled as Helmholtz.
+    `overrides` (cycle shape, precision, levels, restart, ...) apply to both;
+    `shift` only to stage 2."""
+    shift = overrides.pop("shift", 0.2)
+    p1 = default_params(**overrides, scheme="1up", prec_scheme="prec", beta=1.0)
+    p2 = default_params(**overrides, scheme="cen", prec_scheme="cen", shift=shift, rescale=1)
+    return p1, p2
 
 
 def solve_host(n, h, src, omega, kappa, tau1, gamma, params=None, tol=1e-8, maxit=500, stream=None,

@@ -261,6 +261,13 @@ void launch_coefficients(const Dims& g, const FineInputs& in, double* const gd[3
                          double2* rho, double* tau, double2* src_row, cudaStream_t st);
 // float64 -> float32 copy of n reals.
 void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+// diag(M) = exp(-i w tau) per node of every problem (Eq. matrix_rescaling).
+void launch_phase(const double* tau, const FineDyn* dyn, double2* phase, int64_t N, int B, cudaStream_t st);
+// Stored cross rows A -> M A M^{-1}: entry (i, i + o) times m_i conj(m_{i+o}).
+template <typename T> void launch_rows_rescale(const Dims& g, C<T>* rows, const double2* phase, cudaStream_t st);
+// dst = (Td)(src * m) or, with conj, (Td)(src * conj(m)), m = phase (whole arrays of n entries).
+template <typename Ts, typename Td>
+void launch_phase_cast(const C<Ts>* src, const double2* phase, bool conj, C<Td>* dst, int64_t n, cudaStream_t st);
 // The cycle's coefficients under the complex shift of Eq. shift: rho_s = rho -
 // i alpha w^2 kappa^2 per node and the source row with the same diagonal change.
 void launch_shift(const Dims& g, const FineInputs& in, double alpha, const double2* rho, const double2* src_row,

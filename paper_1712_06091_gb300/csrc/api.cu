@@ -104,10 +104,11 @@ static void take_arnoldi(Arena& a, ArnoldiState& s, int m, int B) {
 
 template <typename T> struct Hier {
   int L = 0;
-  T* packed = nullptr;   // packed rows of the level-0 operator (2 + 4 dim reals per node)
+  T* packed = nullptr;   // packed rows of the level-0 operator (2 + 4 dim reals per node); with
+                         // params.rescale its full rows M A M^{-1} (1 + 4 dim complex per node)
   Level<T> lv[ADR_MAX_LEVELS];
   GridScratch gs{};   // persistent coarsest-grid solve (nblk = 0: not planned)
-  FineOp<T> prec{};   // level-0 operator of the cycle: (1 - beta) H_2up + beta H_1up
+  FineOp<T> prec{};   // level-0 operator of the cycle (params.prec_scheme, shift, rescale)
 };
 
 struct Op {
@@ -137,6 +138,8 @@ struct Op {
   float* rhosf = nullptr;
   double2* srows = nullptr;
   float* srowsf = nullptr;
+  // diag(M) = exp(-i w tau) per node (only when params.rescale != 0)
+  double2* phase = nullptr;
   Hier<double> h64;
   Hier<float> h32;
   // outer FGMRES
@@ -144,7 +147,7 @@ struct Op {
   double2* Z = nullptr;
   double2* b = nullptr;  // point-source right-hand side
   double2* r = nullptr;
-  double2* rows2up = nullptr;  // stored float64 rows of H_2up for the outer iteration
+  double2* rows_out = nullptr;  // stored float64 rows of H_2up for the outer iteration
   ArnoldiState ost{};
   KrylovScratch ks{};
   FineDyn* dyn = nullptr;           // omega and the source, read by the fine kernels
@@ -154,7 +157,7 @@ struct Op {
   long long cycle_kernels = 0;
   // conjugate-transposed operator (params.adjoint): H_2up^H rows for the outer
   // iteration and a hierarchy on A^H sharing the forward one's work vectors
-  double2* rows2upT = nullptr;
+  double2* rows_outT = nullptr;
   void* rows0 = nullptr;            // stored rows of the cycle's fine operator (setup scratch)
   void* rows0T = nullptr;           // their conjugate transpose
   Hier<double> a64;
@@ -246,7 +249,8 @@ template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
   }
   const int S = op.dim == 2 ? kPattern2 : kPattern3;
   const size_t B = (size_t)op.B;
-  H.packed = a.take<T>((size_t)(2 + 4 * op.dim) * (size_t)op.g0.N * B);
+  const size_t row_reals = op.p.rescale ? (size_t)2 * (1 + 4 * op.dim) : (size_t)(2 + 4 * op.dim);
+  H.packed = a.take<T>(row_reals * (size_t)op.g0.N * B);
   for (int l = 0; l < H.L; ++l) {
     Level<T>& L = H.lv[l];
     const size_t N = (size_t)L.g.N;
@@ -314,6 +318,7 @@ static void plan(Op& op, Arena& a) {
     op.srows = a.take<double2>(kCross3 * B);
     op.srowsf = a.take<float>(2 * kCross3 * B);
   }
+  if (op.p.rescale) op.phase = a.take<double2>(NB);
   if (op.p.precond_precision == ADR_F64) plan_hierarchy(op, op.h64, a);
   else plan_hierarchy(op, op.h32, a);
   const int m = op.p.restart;
@@ -321,7 +326,7 @@ static void plan(Op& op, Arena& a) {
   op.Z = a.take<double2>((size_t)m * NB);
   op.b = a.take<double2>(NB);
   op.r = a.take<double2>(NB);
-  op.rows2up = a.take<double2>((size_t)(1 + 4 * op.dim) * NB);
+  op.rows_out = a.take<double2>((size_t)(1 + 4 * op.dim) * NB);
   take_arnoldi(a, op.ost, m, op.B);
   op.ks.partial = a.take<double2>((size_t)kPartialStride * B);
   op.ks.ticket = a.take<unsigned>(B);
@@ -334,7 +339,7 @@ static void plan(Op& op, Arena& a) {
   if (op.p.adjoint) {
     const size_t cross = (size_t)(1 + 4 * op.dim) * N;
     const size_t cbytes = op.p.precond_precision == ADR_F64 ? sizeof(double2) : sizeof(float2);
-    op.rows2upT = a.take<double2>(cross);
+    op.rows_outT = a.take<double2>(cross);
     op.rows0 = a.take<char>(cross * cbytes);
     op.rows0T = a.take<char>(cross * cbytes);
     if (op.p.precond_precision == ADR_F64) plan_adjoint(op.h64, op.a64, a, op.dim);
@@ -342,7 +347,9 @@ static void plan(Op& op, Arena& a) {
   }
 }
 
-template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool f32) {
+// The finest-grid operator of `scheme`; cycle = true gives the cycle's version
+// (Eq. shift applied when params.shift != 0).
+template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool f32, bool cycle = false) {
   FineOp<T> f{};
   for (int d = 0; d < 3; ++d) {
     if (d < op.dim) {
@@ -357,7 +364,7 @@ template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool 
     }
   }
   f.dyn = op.dyn;
-  const bool shifted = scheme == ADR_SCHEME_PREC && op.rhos;   // Eq. shift applies to the cycle's operator only
+  const bool shifted = cycle && op.rhos;   // Eq. shift applies to the cycle's operator only
   if (shifted) {
     f.rho = f32 ? (const C<T>*)(const void*)op.rhosf : (const C<T>*)(const void*)op.rhos;
     f.src_row = f32 ? (const C<T>*)(const void*)op.srowsf : (const C<T>*)(const void*)op.srows;
@@ -558,9 +565,17 @@ template <typename T> struct Cycle {
 
 template <typename T> static int build_hierarchy(Op& op, Hier<T>& H) {
   const bool f32 = sizeof(T) == 4;
-  H.prec = make_fine<T>(op, ADR_SCHEME_PREC, f32);
-  launch_fine_pack<T>(H.lv[0].g, H.prec, H.packed, op.st);   // the cycle reads the packed rows from here on
-  H.prec.packed = H.packed;
+  H.prec = make_fine<T>(op, op.p.prec_scheme, f32, true);
+  if (op.p.rescale) {
+    // Alg. ADRlong, stage 2: the cycle acts on M A M^{-1}, stored as rows
+    C<T>* rows = (C<T>*)(void*)H.packed;
+    launch_fine_store_rows(H.lv[0].g, H.prec, rows, op.st);
+    launch_rows_rescale<T>(H.lv[0].g, rows, op.phase, op.st);
+    H.prec.rows = rows;
+  } else {
+    launch_fine_pack<T>(H.lv[0].g, H.prec, H.packed, op.st);   // the cycle reads the packed rows from here on
+    H.prec.packed = H.packed;
+  }
   Level<T>& L0 = H.lv[0];
   launch_fine_dinv<T>(L0.g, H.prec, nullptr, L0.dinv, op.st);
   for (int l = 1; l < H.L; ++l) {
@@ -622,11 +637,12 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
     launch_to_f32((const double*)op.rhos, op.rhosf, 2 * NB, op.st);
     launch_to_f32((const double*)op.srows, op.srowsf, 2 * kCross3 * op.B, op.st);
   }
-  launch_fine_store_rows(op.g0, make_fine<double>(op, ADR_SCHEME_2UP, false), op.rows2up, op.st);
+  if (op.phase) launch_phase(op.tau, op.dyn, op.phase, N, op.B, op.st);
+  launch_fine_store_rows(op.g0, make_fine<double>(op, op.p.scheme, false), op.rows_out, op.st);
   ADR_TRY(check_launch("coefficients"));
   ADR_TRY(op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32));
   if (!op.p.adjoint) return ADR_OK;
-  launch_rows_adjoint<double>(op.g0, op.rows2up, op.rows2upT, op.st);
+  launch_rows_adjoint<double>(op.g0, op.rows_out, op.rows_outT, op.st);
   return op.p.precond_precision == ADR_F64 ? build_adjoint(op, op.h64, op.a64) : build_adjoint(op, op.h32, op.a32);
 }
 
@@ -675,17 +691,25 @@ template <typename T> static int run_cycle(Op& op, Hier<T>& H, bool adj = false)
 
 // One preconditioner application on float64 vectors (casting for a float32
 // cycle); adj selects the cycle on A^H.
+// z = K v with K the cycle; with params.rescale, z = M^{-1} K (M v) (the
+// cycle works on the rescaled variables, Alg. ADRlong; the same form for the
+// adjoint since M is unitary).
 static int precondition(Op& op, const double2* v, double2* z, bool adj = false) {
+  const int64_t NB = op.g0.N * op.B;
   if (op.p.precond_precision == ADR_F64) {
     Hier<double>& H = adj ? op.a64 : op.h64;
-    launch_copy<double>(v, H.lv[0].b, op.g0.N * op.B, op.st);
+    if (op.phase) launch_phase_cast<double, double>(v, op.phase, false, H.lv[0].b, NB, op.st);
+    else launch_copy<double>(v, H.lv[0].b, NB, op.st);
     ADR_TRY(run_cycle(op, H, adj));
-    launch_copy<double>(H.lv[0].x, z, op.g0.N * op.B, op.st);
+    if (op.phase) launch_phase_cast<double, double>(H.lv[0].x, op.phase, true, z, NB, op.st);
+    else launch_copy<double>(H.lv[0].x, z, NB, op.st);
   } else {
     Hier<float>& H = adj ? op.a32 : op.h32;
-    launch_ccast<double, float>(v, H.lv[0].b, op.g0.N * op.B, op.st);
+    if (op.phase) launch_phase_cast<double, float>(v, op.phase, false, H.lv[0].b, NB, op.st);
+    else launch_ccast<double, float>(v, H.lv[0].b, NB, op.st);
     ADR_TRY(run_cycle(op, H, adj));
-    launch_ccast<float, double>(H.lv[0].x, z, op.g0.N * op.B, op.st);
+    if (op.phase) launch_phase_cast<float, double>(H.lv[0].x, op.phase, true, z, NB, op.st);
+    else launch_ccast<float, double>(H.lv[0].x, z, NB, op.st);
   }
   return ADR_OK;
 }
@@ -716,6 +740,10 @@ static int validate_params(const adr_params_t& p) {
     return fail(ADR_ERR_ARG, "unknown coarse_solver");
   if (p.tma < 0 || p.tma > 2) return fail(ADR_ERR_ARG, "tma must be 0, 1 or 2");
   if (!(p.shift >= 0.0 && p.shift <= 100.0)) return fail(ADR_ERR_ARG, "shift must be in [0, 100]");
+  if (p.scheme != ADR_SCHEME_2UP && p.scheme != ADR_SCHEME_1UP && p.scheme != ADR_SCHEME_CEN)
+    return fail(ADR_ERR_ARG, "scheme must be ADR_SCHEME_2UP, ADR_SCHEME_1UP or ADR_SCHEME_CEN");
+  if (p.prec_scheme < ADR_SCHEME_2UP || p.prec_scheme > ADR_SCHEME_PREC) return fail(ADR_ERR_ARG, "unknown prec_scheme");
+  if (p.rescale != 0 && p.rescale != 1) return fail(ADR_ERR_ARG, "rescale must be 0 or 1");
   for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
     if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
       return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");
@@ -756,6 +784,8 @@ int adr_params_default(adr_params_t* p) {
   p->near_source = 1;
   p->reorth_eta = 0.1;
   p->tma = 1;
+  p->scheme = ADR_SCHEME_2UP;
+  p->prec_scheme = ADR_SCHEME_PREC;
   return ADR_OK;
 }
 
@@ -981,16 +1011,29 @@ int adr_apply(adr_op_t h, int scheme, int precision, const void* x, void* y) {
   if (!h || !x || !y) return fail(ADR_ERR_ARG, "null argument");
   if (scheme < ADR_SCHEME_2UP || scheme > ADR_SCHEME_PREC) return fail(ADR_ERR_ARG, "unknown scheme");
   Op& op = h->op;
-  if (precision == ADR_F64 && scheme == ADR_SCHEME_2UP) {
-    launch_rows_apply(op.g0, op.rows2up, (const double2*)x, (double2*)y, op.st);   // the outer iteration's operator
+  if (precision != ADR_F64 && precision != ADR_F32) return fail(ADR_ERR_ARG, "unknown precision");
+  if (scheme == ADR_SCHEME_PREC && precision == op.p.precond_precision) {
+    // the cycle's finest-grid operator exactly as the cycle applies it
+    if (precision == ADR_F64) launch_fine_apply<double>(op.g0, op.h64.prec, (const double2*)x, (double2*)y, op.st);
+    else launch_fine_apply<float>(op.g0, op.h32.prec, (const float2*)x, (float2*)y, op.st);
+  } else if (scheme == ADR_SCHEME_PREC && op.p.rescale) {
+    return fail(ADR_ERR_ARG, "with rescale the cycle's operator exists in the cycle's precision only");
+  } else if (scheme == ADR_SCHEME_PREC) {
+    if (precision == ADR_F64) {
+      FineOp<double> f = make_fine<double>(op, op.p.prec_scheme, false, true);
+      launch_fine_apply<double>(op.g0, f, (const double2*)x, (double2*)y, op.st);
+    } else {
+      FineOp<float> f = make_fine<float>(op, op.p.prec_scheme, true, true);
+      launch_fine_apply<float>(op.g0, f, (const float2*)x, (float2*)y, op.st);
+    }
+  } else if (precision == ADR_F64 && scheme == op.p.scheme) {
+    launch_rows_apply(op.g0, op.rows_out, (const double2*)x, (double2*)y, op.st);   // the outer iteration's operator
   } else if (precision == ADR_F64) {
     FineOp<double> f = make_fine<double>(op, scheme, false);
     launch_fine_apply<double>(op.g0, f, (const double2*)x, (double2*)y, op.st);
   } else if (precision == ADR_F32) {
     FineOp<float> f = make_fine<float>(op, scheme, true);
     launch_fine_apply<float>(op.g0, f, (const float2*)x, (float2*)y, op.st);
-  } else {
-    return fail(ADR_ERR_ARG, "unknown precision");
   }
   return check_launch("adr_apply");
 }
@@ -1055,7 +1098,7 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
   const int64_t N = op.g0.N;
   const int64_t NB = N * B;
   const int m = op.p.restart;
-  const double2* rows = adj ? op.rows2upT : op.rows2up;
+  const double2* rows = adj ? op.rows_outT : op.rows_out;
   const double* hs = op.host_scal;
 
   launch_norm_start<double>(b, N, op.ks, nullptr, st, B);
@@ -1164,6 +1207,23 @@ int adr_solve(adr_op_t h, const void* rhs_in, void* a_out, int use_x0, double to
   return fgmres(op, false, b, (double2*)a_out, use_x0, tol, maxit, info);
 }
 
+int adr_solve_two_stage(adr_op_t s1, adr_op_t s2, const void* rhs, void* a, double tol1, int maxit1, double tol,
+                        int maxit, adr_solve_info_t* info) {
+  if (!s1 || !s2 || !a) return fail(ADR_ERR_ARG, "null argument");
+  if (s1 == s2) return fail(ADR_ERR_ARG, "the two stages need their own operators");
+  if (!(tol1 >= 0.0) || maxit1 < 0 || !(tol >= 0.0) || maxit < 0)
+    return fail(ADR_ERR_ARG, "tolerances must be >= 0 and iteration counts >= 0");
+  const Op& o1 = s1->op;
+  const Op& o2 = s2->op;
+  bool same = o1.dim == o2.dim && o1.B == o2.B && o1.omegas == o2.omegas && o1.srcs == o2.srcs;
+  for (int d = 0; d < 3; ++d) same = same && o1.g0.n[d] == o2.g0.n[d] && o1.h[d] == o2.h[d];
+  if (!same) return fail(ADR_ERR_ARG, "the two stages must share grid, spacing, problems, sources and frequencies");
+  const int rc1 = adr_solve(s1, rhs, a, 0, tol1, maxit1, info);
+  if (rc1 != ADR_OK && rc1 != ADR_ERR_NOT_CONVERGED) return rc1;
+  if (o1.st != o2.st) ADR_CUDA(cudaStreamSynchronize(o1.st));   // stage 2 reads stage 1's iterate
+  return adr_solve(s2, rhs, a, 1, tol, maxit, info ? info + o1.B : nullptr);
+}
+
 int adr_adjoint_solve(adr_op_t h, const void* rhs, void* lambda, int use_x0, double tol, int maxit,
                       adr_solve_info_t* info) {
   if (!h || !rhs || !lambda) return fail(ADR_ERR_ARG, "null argument");
@@ -1178,7 +1238,7 @@ int adr_apply_adjoint(adr_op_t h, const void* x, void* y) {
   if (!h || !x || !y) return fail(ADR_ERR_ARG, "null argument");
   Op& op = h->op;
   if (!op.p.adjoint) return fail(ADR_ERR_STATE, "operator created without params.adjoint");
-  launch_rows_apply(op.g0, op.rows2upT, (const double2*)x, (double2*)y, op.st);
+  launch_rows_apply(op.g0, op.rows_outT, (const double2*)x, (double2*)y, op.st);
   return check_launch("adr_apply_adjoint");
 }
 

@@ -475,6 +475,37 @@ void launch_reconstruct(const double2* a, const double* tau, const FineDyn* dyn,
   count_launches(1), k_reconstruct<<<dim3(blocks_for(N, 256), B), 256, 0, st>>>(a, tau, dyn, u, N);
 }
 
+__global__ void k_phase(const double* tau, const FineDyn* dyn, double2* phase, int64_t N) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  batch_shift(N, tau, phase);
+  double s, c;
+  sincos(-dyn[blockIdx.y].omega * tau[i], &s, &c);
+  phase[i] = make_double2(c, s);
+}
+void launch_phase(const double* tau, const FineDyn* dyn, double2* phase, int64_t N, int B, cudaStream_t st) {
+  count_launches(1), k_phase<<<dim3(blocks_for(N, 256), B), 256, 0, st>>>(tau, dyn, phase, N);
+}
+
+template <typename Ts, typename Td>
+__global__ void k_phase_cast(const C<Ts>* __restrict__ src, const double2* __restrict__ phase, bool conj,
+                             C<Td>* __restrict__ dst, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const C<Ts> v = src[i];
+  double2 m = phase[i];
+  if (conj) m.y = -m.y;
+  const double2 r = cmul(make_double2((double)v.x, (double)v.y), m);
+  dst[i] = mk<Td>((Td)r.x, (Td)r.y);
+}
+template <typename Ts, typename Td>
+void launch_phase_cast(const C<Ts>* src, const double2* phase, bool conj, C<Td>* dst, int64_t n, cudaStream_t st) {
+  count_launches(1), k_phase_cast<Ts, Td><<<blocks_for(n, 256), 256, 0, st>>>(src, phase, conj, dst, n);
+}
+template void launch_phase_cast<double, double>(const double2*, const double2*, bool, double2*, int64_t, cudaStream_t);
+template void launch_phase_cast<double, float>(const double2*, const double2*, bool, float2*, int64_t, cudaStream_t);
+template void launch_phase_cast<float, double>(const float2*, const double2*, bool, double2*, int64_t, cudaStream_t);
+
 __global__ void k_pack(Dims g, const double* g0, const double* g1, const double* g2, const double* t0, const double* t1,
                        const double* t2, const double2* rho, const double* tau, double* out) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -699,6 +730,42 @@ void launch_rows_adjoint(const Dims& g, const C<T>* rows, C<T>* rowsT, cudaStrea
   else count_launches(1), k_rows_adjoint<3, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, rowsT);
 }
 template void launch_rows_adjoint<double>(const Dims&, const double2*, double2*, cudaStream_t);
+
+// M A M^{-1} for stored cross rows: the entry of row i at offset o is scaled
+// by m_i conj(m_{i+o}) = exp(-i w (tau_i - tau_{i+o})) (|m| = 1); the centre
+// and the zero slots of off-grid neighbours are unchanged.
+template <int DIM, typename T>
+__global__ void k_rows_rescale(Dims g, C<T>* __restrict__ rows, const double2* __restrict__ phase) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  batch_shift((1 + 4 * DIM) * g.N, rows);
+  batch_shift(g.N, phase);
+  int ii[3];
+  unravel(g, i, ii[0], ii[1], ii[2]);
+  const double2 mi = phase[i];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int64_t stride = d == 0 ? 1 : (d == 1 ? g.s1 : g.s2);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int o = (s & 2) ? ((s & 1) ? 2 : -2) : ((s & 1) ? 1 : -1);   // slots -1, +1, -2, +2
+      const int k = ii[d] + o;
+      if (k < 0 || k >= g.n[d]) continue;
+      double2 mn = phase[i + o * stride];
+      mn.y = -mn.y;
+      const double2 f = cmul(mi, mn);
+      C<T>& e = rows[(int64_t)(1 + 4 * d + s) * g.N + i];
+      const double2 r = cmul(make_double2((double)e.x, (double)e.y), f);
+      e = mk<T>((T)r.x, (T)r.y);
+    }
+  }
+}
+template <typename T> void launch_rows_rescale(const Dims& g, C<T>* rows, const double2* phase, cudaStream_t st) {
+  if (g.dim == 2) count_launches(1), k_rows_rescale<2, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, phase);
+  else count_launches(1), k_rows_rescale<3, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, phase);
+}
+template void launch_rows_rescale<double>(const Dims&, double2*, const double2*, cudaStream_t);
+template void launch_rows_rescale<float>(const Dims&, float2*, const double2*, cudaStream_t);
 template void launch_rows_adjoint<float>(const Dims&, const float2*, float2*, cudaStream_t);
 void launch_rows_apply(const Dims& g, const double2* rows, const double2* x, double2* y, cudaStream_t st) {
   if (g.dim == 2) count_launches(1), k_rows_apply<2, double><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, rows, x, y);
