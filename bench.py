@@ -37,10 +37,13 @@ METRIC = "ADR solves/s to 1e-8 rel. residual at 256^2x128 cells (257x257x129 nod
 UNIT = "solves/s"
 SL_METRIC = ("standard Helmholtz solves/s (shifted-Laplacian cycle) to 1e-8 rel. residual at 256^2x128 cells "
              "(257x257x129 nodes)")
+CEN_METRIC = ("central ADR solves/s (two-stage, Alg. ADRlong) to 1e-8 rel. residual at 256^2x128 cells "
+              "(257x257x129 nodes)")
+METHODS = ("adr-upwind", "helmholtz-sl", "adr-central")
 
 
 def metric_for(args):
-    return SL_METRIC if args.method == "helmholtz-sl" else METRIC
+    return {"helmholtz-sl": SL_METRIC, "adr-central": CEN_METRIC}.get(args.method, METRIC)
 WORKLOADS = {
     "layered3d_257x257x129": (257, 257, 129),
     "layered3d_193x193x97": (193, 193, 97),
@@ -59,13 +62,20 @@ BENCH_RESTART = 8
 # with 3 levels and 47 with 5 at a higher cost per cycle).
 SL_SHIFT = 0.2
 SL_LEVELS = 4
+# Two-stage central solve (Alg. ADRlong): stage 1 to 1e-2 or 5 iterations
+# (Sec. 4.2), stage 2 with the shifted cycle on the rescaled system.
+CEN_LEVELS = 4
+CEN_TOL1 = 1e-2
+CEN_MAXIT1 = 5
+CEN_FULL_ITERATIONS = 60.0   # stage 1 + stage 2 iterations of the GPU solve at 257x257x129 (measured)
 # The kernel whose roofline is reported, and its algorithmic bytes per node of
 # level 1: the 81-point stencil stored as 27 complex box entries and 54
 # imaginary parts (float32), z and r read, w written (complex float32).
-ROOFLINE_KERNEL = "k_stencil_mr_apply<3,float> on level 1 (minimal-residual relaxation apply, 81-point Galerkin stencil)"
+ROOFLINE_KERNEL = ("k_stencil_tma<3,float,false,16,1,kTmaMr> on level 1 (minimal-residual relaxation apply, "
+                   "81-point Galerkin stencil streamed into shared memory by bulk copies)")
 ROOFLINE_BYTES_PER_NODE = 27 * 8 + 54 * 4 + 3 * 8
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_stencil_mr_apply_level1_traffic.txt")
-TRAFFIC_SOURCES = ["paper_1712_06091_gb300/csrc/coarse.cu", "paper_1712_06091_gb300/csrc/coarse_stencil.cuh",
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_stencil_tma_mr_level1_traffic.txt")
+TRAFFIC_SOURCES = ["paper_1712_06091_gb300/csrc/coarse_tma.cu", "paper_1712_06091_gb300/csrc/coarse_stencil.cuh",
                    "paper_1712_06091_gb300/csrc/reduce.cuh"]
 
 
@@ -81,9 +91,10 @@ def parse():
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--levels", type=int, default=None,
                     help=f"grid levels (default {BENCH_LEVELS} for the ADR solve, {SL_LEVELS} for the shifted Laplacian)")
-    ap.add_argument("--method", default="adr-upwind", choices=["adr-upwind", "helmholtz-sl"],
+    ap.add_argument("--method", default="adr-upwind", choices=list(METHODS),
                     help="adr-upwind: H_2up a = q with the (1-beta) H_2up + beta H_1up cycle; helmholtz-sl: the "
-                         "standard Helmholtz matrix (tau1 = 0) with the shifted-Laplacian cycle (Eq. shift)")
+                         "standard Helmholtz matrix (tau1 = 0) with the shifted-Laplacian cycle (Eq. shift); "
+                         "adr-central: H_cen a = q by the two-stage solve (Alg. ADRlong)")
     ap.add_argument("--shift", type=float, default=SL_SHIFT)
     ap.add_argument("--no-comparison", action="store_true")
     ap.add_argument("--restart", type=int, default=None)
@@ -106,18 +117,57 @@ def rank_source(n, rank):
     return (c0 + off[0], c1 + off[1], min(2, n[2] - 1))
 
 
-def build_params(args):
+def build_params(args, method=None):
+    """Parameters of the method's operators: [params] or, for the two-stage
+    central solve, [stage 1, stage 2]."""
     from paper_1712_06091_gb300 import adr as gpu
-    sl = args.method == "helmholtz-sl"
-    kw = {"precision": args.precision, "levels": args.levels or (SL_LEVELS if sl else BENCH_LEVELS),
-          "restart": args.restart or BENCH_RESTART}
-    if sl:
-        kw["shift"] = args.shift
+    method = method or args.method
+    levels = {"helmholtz-sl": SL_LEVELS, "adr-central": CEN_LEVELS}.get(method, BENCH_LEVELS)
+    kw = {"precision": args.precision, "levels": args.levels or levels, "restart": args.restart or BENCH_RESTART}
     if args.cycle:
         kw["cycle"] = args.cycle
     if args.sweeps:
         kw["sweeps"] = [int(v) for v in args.sweeps.split(",")]
-    return gpu.default_params(**kw)
+    if method == "helmholtz-sl":
+        return [gpu.default_params(shift=args.shift, **kw)]
+    if method == "adr-central":
+        return list(gpu.central_two_stage_params(shift=args.shift, **kw))
+    return [gpu.default_params(**kw)]
+
+
+class MethodSolver:
+    """One step of a method on the bench medium and source: set up the
+    operator(s) (coefficients and hierarchy), solve from zero to the
+    tolerance, reconstruct u."""
+
+    def __init__(self, method, P, kappa, tau1, gamma, args, dev):
+        import torch
+        from paper_1712_06091_gb300 import adr as gpu
+        self.gpu, self.method, self.P, self.args = gpu, method, P, args
+        self.kappa, self.gamma = kappa, gamma
+        self.tau1 = torch.zeros_like(tau1) if method == "helmholtz-sl" else tau1   # tau = 0: u = a
+        self.params = build_params(args, method)
+        self.ops = [gpu.Operator(P.n, P.h, P.src, P.omega, kappa, self.tau1, gamma, params=p, device=dev)
+                    for p in self.params]
+        self.op = self.ops[-1]
+
+    def step(self, out):
+        for op in self.ops:
+            op.update(self.P.src, self.P.omega, self.kappa, self.tau1, self.gamma)
+        if len(self.ops) == 1:
+            _, info = self.op.solve(tol=self.args.tol, maxit=self.args.maxit, out=out)
+        else:
+            _, i1, i2 = self.gpu.solve_two_stage(self.ops[0], self.ops[1], tol1=CEN_TOL1, maxit1=CEN_MAXIT1,
+                                                 tol=self.args.tol, maxit=self.args.maxit, out=out)
+            info = dict(i2[0])
+            info["stage1_iterations"] = i1[0]["iterations"]
+            info["stage2_iterations"] = i2[0]["iterations"]
+            info["iterations"] = i1[0]["iterations"] + i2[0]["iterations"]
+        return info, self.op.reconstruct(out)
+
+    def close(self):
+        for op in self.ops:
+            op.close()
 
 
 class ClockSampler:
@@ -243,13 +293,20 @@ def oracle_sample(pd, tol, method="adr-upwind"):
     g = oadr.Grid(P.n, P.h)
     sl = method == "helmholtz-sl"
     tau1 = np.zeros(g.N) if sl else eikonal.factored_fast_marching(g, P.kappa, P.src, order=2)
-    t0 = time.perf_counter()
-    A = oadr.assemble_adr(g, P.src, P.omega, P.kappa, P.gamma, tau1, "2up")
-    Ap = oadr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, tau1, pd["beta"], shift=pd.get("shift", 0.0))
-    hier = omg.build_hierarchy(Ap, P.n, pd["levels"])
     prm = omg.CycleParams(cycle=pd["cycle"], relax=pd["relax"], pre=pd["pre_sweeps"], post=pd["post_sweeps"],
                           weights=pd["jacobi_weight"], coarse_iterations=pd["coarse_iterations"],
                           kcycle_iterations=pd["kcycle_iterations"])
+    t0 = time.perf_counter()
+    if method == "adr-central":
+        from oracle import twostage
+        _, a, (its1, _), (its2, _) = twostage.two_stage_central(
+            g, P.src, P.omega, P.kappa, P.gamma, tau1, prm, pd["levels"], alpha=pd["shift"], stage1_tol=CEN_TOL1,
+            stage1_maxit=CEN_MAXIT1, tol=tol, restart=pd["restart"], maxit=400, reorth_eta=pd["reorth_eta"])
+        oadr.reconstruct(g, P.src, P.omega, tau1, a)
+        return time.perf_counter() - t0, g.N, its1 + its2
+    A = oadr.assemble_adr(g, P.src, P.omega, P.kappa, P.gamma, tau1, "2up")
+    Ap = oadr.assemble_preconditioner(g, P.src, P.omega, P.kappa, P.gamma, tau1, pd["beta"], shift=pd.get("shift", 0.0))
+    hier = omg.build_hierarchy(Ap, P.n, pd["levels"])
     q = oadr.point_source_rhs(g, P.src)
     a, its, res, _ = krylov.fgmres(A, q, lambda v: omg.cycle(hier, v, prm), tol=tol, restart=pd["restart"], maxit=400,
                                    reorth_eta=pd["reorth_eta"])
@@ -280,22 +337,18 @@ def run_ours(args):
     n = WORKLOADS[args.workload]
     src = rank_source(n, rank)
     P = W.layered_3d(n, src=src)
-    params = build_params(args)
     stream = torch.cuda.current_stream(dev)
     kappa = torch.from_numpy(P.kappa).to(dev)
     gamma = torch.from_numpy(P.gamma).to(dev)
     tau1, sweeps = gpu.traveltime(P.n, P.h, P.src, kappa)
-    if args.method == "helmholtz-sl":
-        tau1 = torch.zeros_like(tau1)   # tau = 0: H_2up is the standard Helmholtz matrix, u = a
-    op = gpu.Operator(P.n, P.h, P.src, P.omega, kappa, tau1, gamma, params=params, device=dev)
+    solver = MethodSolver(args.method, P, kappa, tau1, gamma, args, dev)
+    params = solver.params[-1]
+    op = solver.op
     levels = op.info()["levels"]
     a = torch.empty(P.N, dtype=torch.complex128, device=dev)
 
     def step():
-        op.update(P.src, P.omega, kappa, tau1, gamma)
-        _, info = op.solve(tol=args.tol, maxit=args.maxit, out=a)
-        u = op.reconstruct(a)
-        return info, u
+        return solver.step(a)
 
     # CUDA events around every launch of the roofline kernel (captured into the
     # cycle's graph, so enable before the warm-up; re-enabling resets the totals).
@@ -345,9 +398,9 @@ def run_ours(args):
                 "avg_launch_ms": per_launch_ms}
 
     e2e = None
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e and rank == 0 and len(solver.ops) == 1:
         kh = torch.from_numpy(P.kappa).pin_memory().numpy()
-        th = tau1.cpu().pin_memory().numpy()
+        th = solver.tau1.cpu().pin_memory().numpy()
         gh = torch.from_numpy(P.gamma).pin_memory().numpy()
         uh = torch.empty(P.N, dtype=torch.complex128).pin_memory().numpy()
         torch.cuda.synchronize()
@@ -378,8 +431,8 @@ def run_ours(args):
                          f"{np.mean(its):.1f} iterations (mean of {runs} runs)"}
 
     comparison = None
-    if not args.no_comparison and rank == 0 and args.method == "adr-upwind":
-        comparison = sl_comparison(P, kappa, gamma, tau1, args, dev)
+    if not args.no_comparison and rank == 0:
+        comparison = [method_comparison(m, P, kappa, gamma, tau1, args, dev) for m in METHODS if m != args.method]
 
     if rank == 0:
         out = {
@@ -389,9 +442,11 @@ def run_ours(args):
             "data": "synthetic (seeded layered-gradient model with Gaussian anomalies; " +
                     ("tau1 = 0: the standard Helmholtz matrix)" if args.method == "helmholtz-sl" else
                      "tau1 from the library's travel-time kernel)"),
+            "method": args.method,
             "config": {"workload": args.workload, "method": args.method, "nodes": P.N, "grid": list(P.n), "spacing_km": P.h[0],
                        "omega": P.omega, "source": list(src), "tol": args.tol, "params": gpu.params_dict(params),
                        "levels": [lv["n"] for lv in levels], "iterations": its, "max_rel_residual": res,
+                       "stage1_iterations": [i.get("stage1_iterations") for i in infos] if len(solver.ops) > 1 else None,
                        "l2": "no flush: inputs and working set (~9 GB) exceed L2", "wall_s": t_wall,
                        "traveltime_sweeps": sweeps},
             "roofline": roofline,
@@ -403,37 +458,36 @@ def run_ours(args):
         if comparison:
             out["comparison"] = comparison
         print(json.dumps(out))
-    op.close()
+    solver.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def sl_comparison(P, kappa, gamma, tau1, args, dev):
-    """The paper's comparison system on the same medium and source: the standard
-    Helmholtz matrix (tau1 = 0) solved to the same tolerance with the
-    shifted-Laplacian cycle (Eq. shift, alpha = SL_SHIFT).  One warm-up solve,
-    then one solve timed with CUDA events; the ADR solve's iterations beside it."""
+def method_comparison(method, P, kappa, gamma, tau1, args, dev):
+    """Another method on the same medium, source and tolerance (the paper's
+    comparison of Sec. 4): one warm-up step, then one step (operator setup,
+    solve, reconstruction) timed with CUDA events."""
     import torch
     from paper_1712_06091_gb300 import adr as gpu
-    params = gpu.default_params(precision=args.precision, levels=SL_LEVELS, restart=args.restart or BENCH_RESTART,
-                                shift=args.shift)
-    zero = torch.zeros_like(tau1)
-    op = gpu.Operator(P.n, P.h, P.src, P.omega, kappa, zero, gamma, params=params, device=dev)
+    solver = MethodSolver(method, P, kappa, tau1, gamma, args, dev)
     a = torch.empty(P.N, dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream(dev)
-    op.solve(tol=args.tol, maxit=4 * args.maxit, out=a, raise_on_fail=False)
+    solver.step(a)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    _, info = op.solve(tol=args.tol, maxit=4 * args.maxit, out=a, raise_on_fail=False)
+    info, _ = solver.step(a)
     ev1.record(stream)
     torch.cuda.synchronize()
-    op.close()
-    return {"method": "standard Helmholtz (tau1 = 0), shifted-Laplacian cycle", "shift": args.shift,
-            "levels": SL_LEVELS, "restart": params.restart, "iterations": info["iterations"],
-            "rel_residual": info["rel_residual"], "ms_per_solve": ev0.elapsed_time(ev1),
-            "note": "solve only (operator setup outside the timed solve); same tolerance, medium and source"}
+    out = {"method": method, "metric": {"helmholtz-sl": SL_METRIC, "adr-central": CEN_METRIC}.get(method, METRIC),
+           "value": 1e3 / ev0.elapsed_time(ev1), "unit": UNIT, "ms_per_step": ev0.elapsed_time(ev1),
+           "iterations": info["iterations"], "rel_residual": info["rel_residual"],
+           "params": [gpu.params_dict(p) for p in solver.params]}
+    if "stage1_iterations" in info:
+        out["stage1_iterations"] = info["stage1_iterations"]
+    solver.close()
+    return out
 
 
 def run_reference(args):
@@ -443,10 +497,10 @@ def run_reference(args):
         return
     import numpy as np
     from paper_1712_06091_gb300.adr import params_dict
-    pd = params_dict(build_params(args))
+    pd = params_dict(build_params(args)[-1])
     N = int(np.prod(WORKLOADS[args.workload]))
     # iterations of the GPU solve at 257x257x129 with this cycle (bench config, measured)
-    full_its = 49.0 if args.method == "helmholtz-sl" else 70.0
+    full_its = {"helmholtz-sl": 49.0, "adr-central": CEN_FULL_ITERATIONS}.get(args.method, 70.0)
     for _ in range(min(args.warmup, 1)):
         oracle_sample(pd, args.tol, args.method)
     secs, its = [], []
