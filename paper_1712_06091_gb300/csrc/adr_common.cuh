@@ -296,6 +296,10 @@ template <typename T> void launch_fine_pack(const Dims& g, const FineOp<T>& f, T
 template <typename T> void launch_rows_adjoint(const Dims& g, const C<T>* rows, C<T>* rowsT, cudaStream_t st);
 void launch_rows_apply(const Dims& g, const double2* rows, const double2* x, double2* y, cudaStream_t st);
 void launch_rows_residual(const Dims& g, const double2* rows, const double2* b, const double2* x, double2* r, cudaStream_t st);
+// the outer float64 operator from packed rows (f.packed set; see k_fine_pack)
+void launch_packed_apply(const Dims& g, const FineOp<double>& f, const double2* x, double2* y, cudaStream_t st);
+void launch_packed_residual(const Dims& g, const FineOp<double>& f, const double2* b, const double2* x, double2* r,
+                            cudaStream_t st);
 // Writes the per-source values read by the fine kernels.
 void launch_set_dyn(FineDyn* d, const FineDyn& v, cudaStream_t st);
 // Galerkin product of the fine operator into the stored stencil of level 1.

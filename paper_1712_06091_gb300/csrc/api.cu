@@ -147,7 +147,8 @@ struct Op {
   double2* Z = nullptr;
   double2* b = nullptr;  // point-source right-hand side
   double2* r = nullptr;
-  double2* rows_out = nullptr;  // stored float64 rows of H_2up for the outer iteration
+  double* packed_out = nullptr; // packed float64 rows of the outer system (k_fine_pack layout)
+  double2* rows_out = nullptr;  // stored float64 rows of the outer system (adjoint operators only)
   ArnoldiState ost{};
   KrylovScratch ks{};
   FineDyn* dyn = nullptr;           // omega and the source, read by the fine kernels
@@ -326,7 +327,7 @@ static void plan(Op& op, Arena& a) {
   op.Z = a.take<double2>((size_t)m * NB);
   op.b = a.take<double2>(NB);
   op.r = a.take<double2>(NB);
-  op.rows_out = a.take<double2>((size_t)(1 + 4 * op.dim) * NB);
+  op.packed_out = a.take<double>((size_t)(2 + 4 * op.dim) * NB);
   take_arnoldi(a, op.ost, m, op.B);
   op.ks.partial = a.take<double2>((size_t)kPartialStride * B);
   op.ks.ticket = a.take<unsigned>(B);
@@ -339,6 +340,7 @@ static void plan(Op& op, Arena& a) {
   if (op.p.adjoint) {
     const size_t cross = (size_t)(1 + 4 * op.dim) * N;
     const size_t cbytes = op.p.precond_precision == ADR_F64 ? sizeof(double2) : sizeof(float2);
+    op.rows_out = a.take<double2>(cross);
     op.rows_outT = a.take<double2>(cross);
     op.rows0 = a.take<char>(cross * cbytes);
     op.rows0T = a.take<char>(cross * cbytes);
@@ -374,6 +376,14 @@ template <typename T> static FineOp<T> make_fine(const Op& op, int scheme, bool 
   }
   f.near = op.p.near_source;
   set_scheme(f, scheme, op.p.beta);
+  return f;
+}
+
+// The outer iteration's float64 operator (params.scheme, unshifted), read
+// from the packed rows written at setup.
+static FineOp<double> outer_op(const Op& op) {
+  FineOp<double> f = make_fine<double>(op, op.p.scheme, false);
+  f.packed = op.packed_out;
   return f;
 }
 
@@ -638,10 +648,11 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
     launch_to_f32((const double*)op.srows, op.srowsf, 2 * kCross3 * op.B, op.st);
   }
   if (op.phase) launch_phase(op.tau, op.dyn, op.phase, N, op.B, op.st);
-  launch_fine_store_rows(op.g0, make_fine<double>(op, op.p.scheme, false), op.rows_out, op.st);
+  launch_fine_pack<double>(op.g0, make_fine<double>(op, op.p.scheme, false), op.packed_out, op.st);
   ADR_TRY(check_launch("coefficients"));
   ADR_TRY(op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32));
   if (!op.p.adjoint) return ADR_OK;
+  launch_fine_store_rows(op.g0, make_fine<double>(op, op.p.scheme, false), op.rows_out, op.st);
   launch_rows_adjoint<double>(op.g0, op.rows_out, op.rows_outT, op.st);
   return op.p.precond_precision == ADR_F64 ? build_adjoint(op, op.h64, op.a64) : build_adjoint(op, op.h32, op.a32);
 }
@@ -1027,7 +1038,7 @@ int adr_apply(adr_op_t h, int scheme, int precision, const void* x, void* y) {
       launch_fine_apply<float>(op.g0, f, (const float2*)x, (float2*)y, op.st);
     }
   } else if (precision == ADR_F64 && scheme == op.p.scheme) {
-    launch_rows_apply(op.g0, op.rows_out, (const double2*)x, (double2*)y, op.st);   // the outer iteration's operator
+    launch_packed_apply(op.g0, outer_op(op), (const double2*)x, (double2*)y, op.st);   // the outer iteration's operator
   } else if (precision == ADR_F64) {
     FineOp<double> f = make_fine<double>(op, scheme, false);
     launch_fine_apply<double>(op.g0, f, (const double2*)x, (double2*)y, op.st);
@@ -1098,7 +1109,16 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
   const int64_t N = op.g0.N;
   const int64_t NB = N * B;
   const int m = op.p.restart;
-  const double2* rows = adj ? op.rows_outT : op.rows_out;
+  // the outer operator: packed rows, or the stored conjugate-transposed rows
+  const FineOp<double> fo = outer_op(op);
+  auto outer_apply = [&](const double2* x, double2* y) {
+    if (adj) launch_rows_apply(op.g0, op.rows_outT, x, y, st);
+    else launch_packed_apply(op.g0, fo, x, y, st);
+  };
+  auto outer_residual = [&](const double2* bb, const double2* x, double2* r) {
+    if (adj) launch_rows_residual(op.g0, op.rows_outT, bb, x, r, st);
+    else launch_packed_residual(op.g0, fo, bb, x, r, st);
+  };
   const double* hs = op.host_scal;
 
   launch_norm_start<double>(b, N, op.ks, nullptr, st, B);
@@ -1108,7 +1128,7 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
   std::vector<int> its_p(B, 0), status(B, ADR_OK), done(B, 0);
   for (int pb = 0; pb < B; ++pb) bnorm[pb] = sqrt(hs[2 * pb]);
   if (use_x0) {
-    launch_rows_residual(op.g0, rows, b, a, op.r, st);
+    outer_residual(b, a, op.r);
   } else {
     launch_zero<double>(a, NB, st);
     launch_copy<double>(b, op.r, NB, st);
@@ -1137,7 +1157,7 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
       ADR_TRY(precondition(op, vj, zj, adj));
       {
         const int pk = adj ? -1 : prof_begin(op, ADR_PROF_OUTER_APPLY, st);
-        launch_rows_apply(op.g0, rows, zj, w, st);
+        outer_apply(zj, w);
         prof_end(op, pk, st);
       }
       launch_cgs_selective<double>(op.V, NB, j + 1, w, N, op.ks, op.ost, j, op.p.reorth_eta, st, B);
@@ -1161,7 +1181,7 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
     if (nan) break;
     launch_backsolve(op.ost, k, st, B);
     launch_combine<double>(a, op.Z, NB, k, op.ost, false, N, st, B);
-    launch_rows_residual(op.g0, rows, b, a, op.r, st);
+    outer_residual(b, a, op.r);
     launch_norm_start<double>(op.r, N, op.ks, &op.ost, st, B);
     ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2 * B));
     ++cycles;
