@@ -76,7 +76,7 @@ ROOFLINE_KERNEL = ("k_stencil_tma<3,float,false,16,1,kTmaMr> on level 1 (minimal
 ROOFLINE_BYTES_PER_NODE = 27 * 8 + 54 * 4 + 3 * 8
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_stencil_tma_mr_level1_traffic.txt")
 TRAFFIC_SOURCES = ["paper_1712_06091_gb300/csrc/coarse_tma.cu", "paper_1712_06091_gb300/csrc/coarse_stencil.cuh",
-                   "paper_1712_06091_gb300/csrc/reduce.cuh"]
+                   "paper_1712_06091_gb300/csrc/reduce.cuh", "paper_1712_06091_gb300/csrc/adr_common.cuh"]
 
 
 def parse():

@@ -77,7 +77,36 @@ struct Dims {
   int64_t s1, s2;  // strides of axes 1 and 2
   int B;           // problems sharing this grid in a batched launch (grid.y)
   int mrcap;       // largest grid of the relaxation applies (0: kMaxMrBlocks)
+  unsigned mul0, mul1;  // division by n[0], n[1] as a multiply and a shift (fast_div_params)
+  int shr0, shr1;
 };
+
+// Division of a 31-bit unsigned x by an invariant d >= 1 without a divide
+// instruction (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, round-up method): with l = ceil(log2 d),
+// m = ceil(2^(31+l) / d) < 2^32 and x < 2^31,
+//   floor(x / d) = floor(x m / 2^(31+l)) = umulhi(x, m) >> (l - 1),
+// because x m / 2^(31+l) = x / d + delta with 0 <= delta < 2^-l <= 1/d.
+// d = 1 is the identity (shr = -1).
+inline void fast_div_params(unsigned d, unsigned& mul, int& shr) {
+  if (d <= 1u) {
+    mul = 0u;
+    shr = -1;
+    return;
+  }
+  int l = 0;
+  while ((1ull << l) < (unsigned long long)d) ++l;
+  mul = (unsigned)(((1ull << (31 + l)) + d - 1) / d);
+  shr = l - 1;
+}
+__host__ __device__ __forceinline__ unsigned fast_div(unsigned x, unsigned mul, int shr) {
+#ifdef __CUDA_ARCH__
+  const unsigned hi = __umulhi(x, mul);
+#else
+  const unsigned hi = (unsigned)(((unsigned long long)x * mul) >> 32);
+#endif
+  return shr < 0 ? x : (hi >> shr);
+}
 
 inline Dims make_dims(int dim, const int* n) {
   Dims g;
@@ -90,6 +119,8 @@ inline Dims make_dims(int dim, const int* n) {
   g.N = g.s2 * g.n[2];
   g.B = 1;
   g.mrcap = 0;
+  fast_div_params((unsigned)g.n[0], g.mul0, g.shr0);
+  fast_div_params((unsigned)g.n[1], g.mul1, g.shr1);
   return g;
 }
 
@@ -111,6 +142,15 @@ __device__ __forceinline__ void batch_shift_opt(int64_t stride, P&... p) {
 constexpr int64_t kPartialStride = 20480;
 
 __device__ __forceinline__ void unravel(const Dims& g, int64_t j, int& i0, int& i1, int& i2) {
+  if (j >= 0 && j <= 0x7fffffffLL) {   // every grid of the solver: two multiply-shift divisions
+    const unsigned u = (unsigned)j;
+    const unsigned q = fast_div(u, g.mul0, g.shr0);
+    i0 = (int)(u - q * (unsigned)g.n[0]);
+    const unsigned q2 = fast_div(q, g.mul1, g.shr1);
+    i1 = (int)(q - q2 * (unsigned)g.n[1]);
+    i2 = (int)q2;
+    return;
+  }
   i0 = (int)(j % g.n[0]);
   int64_t q = j / g.n[0];
   i1 = (int)(q % g.n[1]);

@@ -1,0 +1,23 @@
+"""Host logic of the CUDA path that needs no GPU: the multiply-shift division
+every kernel uses to turn a linear node index into grid coordinates (axis 0
+fastest).  The check program includes the library's own header, so it tests
+the code the kernels compile, on the host."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+def test_fast_division_matches_integer_division(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "fast_div_check")
+    subprocess.run([nvcc, "-std=c++17", "-I" + os.path.join(ROOT, "include"), "-o", exe,
+                    os.path.join(HERE, "native", "fast_div_check.cu")], check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
