@@ -97,6 +97,8 @@ def parse():
                          "adr-central: H_cen a = q by the two-stage solve (Alg. ADRlong)")
     ap.add_argument("--shift", type=float, default=SL_SHIFT)
     ap.add_argument("--no-comparison", action="store_true")
+    ap.add_argument("--breakdown", action="store_true",
+                    help="after the timed steps, time each instrumented kernel class live (one extra step per class)")
     ap.add_argument("--restart", type=int, default=None)
     ap.add_argument("--cycle", default=None)
     ap.add_argument("--sweeps", default=None, help="comma-separated relaxations per level")
@@ -430,6 +432,8 @@ def run_ours(args):
                          f"iterations in {secs:.1f} s, scaled by unknowns*iterations to {P.N} nodes x "
                          f"{np.mean(its):.1f} iterations (mean of {runs} runs)"}
 
+    breakdown = kernel_breakdown(solver, a) if args.breakdown and rank == 0 else None
+
     comparison = None
     if not args.no_comparison and rank == 0:
         comparison = [method_comparison(m, P, kappa, gamma, tau1, args, dev) for m in METHODS if m != args.method]
@@ -457,10 +461,32 @@ def run_ours(args):
         }
         if comparison:
             out["comparison"] = comparison
+        if breakdown:
+            out["breakdown"] = breakdown
         print(json.dumps(out))
     solver.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def kernel_breakdown(solver, a):
+    """Live time of each instrumented kernel class inside a step: CUDA events
+    around every launch of the class (event-record nodes in the captured
+    cycle), one warm step to capture the instrumented graph, then one timed
+    step per class.  Outside the bench's timed region."""
+    import torch
+    op = solver.op
+    out = {}
+    for cls in ("level1_relax", "fine_relax", "outer_apply", "coarsest"):
+        op.profile(cls)
+        solver.step(a)
+        op.profile(cls)
+        solver.step(a)
+        torch.cuda.synchronize()
+        cnt, ms = op.profile_read()
+        out[cls] = {"launches_per_step": cnt, "ms_per_step": ms, "us_per_launch": 1e3 * ms / cnt if cnt else None}
+    op.profile("none")
+    return out
 
 
 def method_comparison(method, P, kappa, gamma, tau1, args, dev):
