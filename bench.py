@@ -57,6 +57,20 @@ BENCH_LEVELS = 3
 # Outer FGMRES restart: 8 was fastest on GB300 at 257x257x129 (458 ms against
 # 505 ms for 20, the same 70 iterations; 5, the paper's, took 73 iterations).
 BENCH_RESTART = 8
+# Grid of the finest-level relaxation applies: one resident wave (four blocks of
+# 256 threads per SM), walked by grid-stride loops.  Measured at 257x257x129:
+# 161 us per apply and 404 ms per solve against 176 us and 410 ms with the
+# library default of 2432 blocks.
+RELAX_BLOCKS_PER_SM = 4
+
+
+def bench_relax_blocks():
+    import torch
+    if not torch.cuda.is_available():   # the oracle arm: the value only shapes GPU launches
+        return 0
+    return RELAX_BLOCKS_PER_SM * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 # Shifted-Laplacian comparison (Sec. 3, alpha = 0.2 as in Sec. 4); 4 levels
 # measured fastest for it on the 257x257x129 model (49 iterations, against 75
 # with 3 levels and 47 with 5 at a higher cost per cycle).
@@ -125,7 +139,8 @@ def build_params(args, method=None):
     from paper_1712_06091_gb300 import adr as gpu
     method = method or args.method
     levels = {"helmholtz-sl": SL_LEVELS, "adr-central": CEN_LEVELS}.get(method, BENCH_LEVELS)
-    kw = {"precision": args.precision, "levels": args.levels or levels, "restart": args.restart or BENCH_RESTART}
+    kw = {"precision": args.precision, "levels": args.levels or levels, "restart": args.restart or BENCH_RESTART,
+          "relax_blocks": bench_relax_blocks()}
     if args.cycle:
         kw["cycle"] = args.cycle
     if args.sweeps:

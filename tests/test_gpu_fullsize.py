@@ -1,6 +1,6 @@
 """Parity at the full benchmark size (257 x 257 x 129 nodes, 25 m spacing),
 in the configuration bench.py times: float32 K-cycle preconditioner on 3
-levels, float64 FGMRES(8) to 1e-8.
+levels, float64 FGMRES(8) to 1e-8, relaxation grid of four blocks per SM.
 
 The oracle cannot assemble or solve an 8.5 M-node system, so it computes
 sampled outputs one by one: coefficients (Eq. travel_time_coeff) and rows of
@@ -39,7 +39,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 N_FULL = (257, 257, 129)
-BENCH_PARAMS = dict(precision="f32", levels=3, restart=8)   # bench.py's default solve configuration
+# bench.py's default solve configuration (its relaxation grid: four blocks per SM)
+BENCH_PARAMS = dict(precision="f32", levels=3, restart=8)
+RELAX_BLOCKS_PER_SM = 4
 BETA = 0.25
 
 
@@ -71,7 +73,8 @@ def sample_nodes(n, src, count, seed):
 def full(adrlib, cuda):
     from paper_1712_06091_gb300 import adr as gpu
     P = problem()
-    params = gpu.default_params(**BENCH_PARAMS)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    params = gpu.default_params(relax_blocks=RELAX_BLOCKS_PER_SM * sms, **BENCH_PARAMS)
     op = gpu.Operator(P.n, P.h, P.src, P.omega, torch.from_numpy(P.kappa), torch.from_numpy(P.tau1),
                       torch.from_numpy(P.gamma), params=params)
     yield P, op
