@@ -615,9 +615,10 @@ template void launch_fine_residual_dinv<float>(const Dims&, const FineOp<float>&
 }  // namespace adr
 
 // ===========================================================================
-// Stored cross rows: the fine operator of the float64 outer iteration, written
-// once per setup so that each outer apply costs a plain 9/13-point complex
-// stencil (about 40 float64 FMAs per node instead of rebuilding the row).
+// Stored rows of a finest-grid operator, written once per setup: full complex
+// cross rows (the adjoint operators' rows and their conjugate transpose, the
+// rescaled cycle operator M A M^{-1}) and the packed rows (the cycle's
+// operator and the float64 outer operator), so that no apply rebuilds a row.
 // ===========================================================================
 namespace adr {
 
