@@ -362,8 +362,7 @@ int adr_traveltime(int dim, const int* n, const double* h, const int* src, const
  * ADR_TRAVELTIME_STATIC_MAX_SWEEPS ints (32 KiB) inside the library; the call
  * zeroes the first max_sweeps of them on `stream` before its first sweep, so
  * nothing needs to be zero beforehand.  The host reads the flags into stack
- * memory every 16 sweeps (a synchronisation of `stream`), so the call can not
- * be captured into a CUDA graph.
+ * memory every 16 sweeps (a synchronisation of `stream`).
  *
  * - max_sweeps above ADR_TRAVELTIME_STATIC_MAX_SWEEPS is rejected with
  *   ADR_ERR_ARG before any device work.
