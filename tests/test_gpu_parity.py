@@ -189,6 +189,24 @@ def test_solve_mixed_precision(adrlib, cuda, name):
     assert rel(a, xe) <= 1e-5
 
 
+@pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17"])
+def test_solve_mixed_precision_refined(adrlib, cuda, name):
+    """float32 cycle, float64 FGMRES continued to a 1e-12 residual (the outer
+    loop refines the float32 preconditioner's output): the solution matches
+    the direct solve of the oracle's H_2up to 1e-8 relative L2."""
+    P, params, op = make_operator(name, precision="f32")
+    A = oracle_matrix(name, "2up")
+    q = adr.point_source_rhs(adr.Grid(P.n, P.h), P.src)
+    a, info = op.solve(tol=1e-12, maxit=800)
+    a = a.cpu().numpy()
+    assert info["rel_residual"] <= 1e-12
+    xe = spla.spsolve(A.tocsc(), q)
+    err = rel(a, xe)
+    print(f"mixed-precision refined {name}: {info['iterations']} iterations, residual {info['rel_residual']:.2e}, "
+          f"error {err:.2e}")
+    assert err <= 1e-8
+
+
 def test_point_source_and_reconstruct(adrlib, cuda):
     P, _, op = make_operator("marine2d_65")
     g = adr.Grid(P.n, P.h)
