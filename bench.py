@@ -88,6 +88,8 @@ CEN_FULL_ITERATIONS = 60.0   # stage 1 + stage 2 iterations of the GPU solve at 
 ROOFLINE_KERNEL = ("k_stencil_tma<3,float,false,16,1,kTmaMr> on level 1 (minimal-residual relaxation apply, "
                    "81-point Galerkin stencil streamed into shared memory by bulk copies)")
 ROOFLINE_BYTES_PER_NODE = 27 * 8 + 54 * 4 + 3 * 8
+# The finest-grid relaxation apply: packed rows (14 floats) plus z, r read and w written (complex float32).
+FINE_RELAX_BYTES_PER_NODE = 14 * 4 + 3 * 8
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_stencil_tma_mr_level1_traffic.txt")
 TRAFFIC_SOURCES = ["paper_1712_06091_gb300/csrc/coarse_tma.cu", "paper_1712_06091_gb300/csrc/coarse_stencil.cuh",
                    "paper_1712_06091_gb300/csrc/reduce.cuh", "paper_1712_06091_gb300/csrc/adr_common.cuh"]
@@ -465,6 +467,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "method": args.method, "nodes": P.N, "grid": list(P.n), "spacing_km": P.h[0],
                        "omega": P.omega, "source": list(src), "tol": args.tol, "params": gpu.params_dict(params),
                        "levels": [lv["n"] for lv in levels], "iterations": its, "max_rel_residual": res,
+                       "unknown_iterations_per_s": unknown_iterations_per_s(value, P.N, its),
                        "stage1_iterations": [i.get("stage1_iterations") for i in infos] if len(solver.ops) > 1 else None,
                        "l2": "no flush: inputs and working set (~9 GB) exceed L2", "wall_s": t_wall,
                        "traveltime_sweeps": sweeps},
@@ -484,6 +487,25 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def unknown_iterations_per_s(solves_per_s, nodes, iterations):
+    """Unknowns times outer iterations per second (the mean iteration count of the timed steps)."""
+    return solves_per_s * nodes * (sum(iterations) / len(iterations))
+
+
+def class_bandwidth(cls, us_per_launch, levels):
+    """Algorithmic GB/s of a kernel class whose bytes per launch are fixed by its level's size (the two
+    relaxation applies), else None."""
+    if not us_per_launch:
+        return None
+    if cls == "level1_relax" and len(levels) > 1:
+        bytes_per_launch = ROOFLINE_BYTES_PER_NODE * levels[1]["nodes"]
+    elif cls == "fine_relax":
+        bytes_per_launch = FINE_RELAX_BYTES_PER_NODE * levels[0]["nodes"]
+    else:
+        return None
+    return bytes_per_launch / (us_per_launch * 1e-6) / 1e9
+
+
 def kernel_breakdown(solver, a):
     """Live time of each instrumented kernel class inside a step: CUDA events
     around every launch of the class (event-record nodes in the captured
@@ -491,6 +513,7 @@ def kernel_breakdown(solver, a):
     step per class.  Outside the bench's timed region."""
     import torch
     op = solver.op
+    levels = op.info()["levels"]
     out = {}
     for cls in ("level1_relax", "fine_relax", "outer_apply", "coarsest"):
         op.profile(cls)
@@ -499,7 +522,9 @@ def kernel_breakdown(solver, a):
         solver.step(a)
         torch.cuda.synchronize()
         cnt, ms = op.profile_read()
-        out[cls] = {"launches_per_step": cnt, "ms_per_step": ms, "us_per_launch": 1e3 * ms / cnt if cnt else None}
+        us = 1e3 * ms / cnt if cnt else None
+        out[cls] = {"launches_per_step": cnt, "ms_per_step": ms, "us_per_launch": us,
+                    "algorithmic_gbs": class_bandwidth(cls, us, levels)}
     op.profile("none")
     return out
 
