@@ -82,3 +82,14 @@ def test_static_traveltime_limit_rejected(adrlib):
     assert rc == _lib.ADR_ERR_ARG and b"max_sweeps" in adrlib.adr_last_error()
     rc = adrlib.adr_traveltime_static(2, n, h, s, DUMMY, DUMMY, 0, None, ctypes.byref(done))
     assert rc == _lib.ADR_ERR_ARG
+
+
+def test_grid_beyond_31_bit_indices_rejected(adrlib):
+    """Node indices are 31-bit: a grid of 2^31 nodes or more is refused before any allocation."""
+    from paper_1712_06091_gb300 import _lib
+    n = (ctypes.c_int * 3)(2048, 2048, 513)
+    h = (ctypes.c_double * 3)(0.01, 0.01, 0.01)
+    s = (ctypes.c_int * 3)(1024, 1024, 2)
+    out = ctypes.c_void_p()
+    rc = adrlib.adr_operator_create(3, n, h, s, 1.0, DUMMY, DUMMY, DUMMY, None, None, ctypes.byref(out))
+    assert rc == _lib.ADR_ERR_ARG and b"too large" in adrlib.adr_last_error()
