@@ -120,7 +120,11 @@ def parse():
     ap.add_argument("--sweeps", default=None, help="comma-separated relaxations per level")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--oracle-sample", default="x".join(str(v) for v in SAMPLE_N),
+                    help="grid of the oracle's bounded sample (cpu_baseline and --impl reference), e.g. 33x33x17")
+    args = ap.parse_args()
+    args.oracle_sample = tuple(int(v) for v in args.oracle_sample.split("x"))
+    return args
 
 
 def dist_env():
@@ -296,19 +300,35 @@ def measured_traffic_per_node():
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (the cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-SAMPLE_N = (33, 33, 17)
+SAMPLE_N = (49, 49, 25)
 
 
-def oracle_sample(pd, tol, method="adr-upwind"):
+def oracle_params(args, method=None):
+    """The cycle and Krylov settings of the bench, as a plain dict for the
+    oracle: the paper's K-cycle (Alg. Kcycle, FGMRES(2) inner steps), one
+    Jacobi-GMRES step per relaxation with l+1 sweeps on level l (Sec. 4.2),
+    10 coarsest GMRES steps, beta = 0.25 (Eq. precADRup), the bench's restart
+    and level count.  The reference arm builds its oracle from this alone."""
+    method = method or args.method
+    levels = {"helmholtz-sl": SL_LEVELS, "adr-central": CEN_LEVELS}.get(method, BENCH_LEVELS)
+    sweeps = [int(v) for v in args.sweeps.split(",")] if args.sweeps else [l + 2 for l in range(8)]
+    sweeps = (sweeps + [sweeps[-1]] * 8)[:8]
+    return {"levels": args.levels or levels, "beta": 0.25, "cycle": args.cycle or "K", "relax": "mr",
+            "pre_sweeps": sweeps, "post_sweeps": list(sweeps), "jacobi_weight": [0.5] * 8,
+            "coarse_iterations": 10, "kcycle_iterations": 2, "restart": args.restart or BENCH_RESTART,
+            "reorth_eta": 0.1, "shift": args.shift if method in ("helmholtz-sl", "adr-central") else 0.0}
+
+
+def oracle_sample(pd, tol, method="adr-upwind", n=None):
     """One oracle solve (setup + FGMRES + cycle + reconstruction) of the layered 3D model
-    resampled to 33 x 33 x 17 nodes (helmholtz-sl: tau1 = 0 and the shifted cycle).
+    resampled to n nodes (default SAMPLE_N; helmholtz-sl: tau1 = 0 and the shifted cycle).
     Returns (seconds, nodes, iterations)."""
     import numpy as np
     from oracle import adr as oadr
     from oracle import eikonal, krylov
     from oracle import multigrid as omg
     from paper_1712_06091_gb300 import workloads as W
-    P = W.layered_3d(SAMPLE_N)
+    P = W.layered_3d(tuple(n or SAMPLE_N))
     g = oadr.Grid(P.n, P.h)
     sl = method == "helmholtz-sl"
     tau1 = np.zeros(g.N) if sl else eikonal.factored_fast_marching(g, P.kappa, P.src, order=2)
@@ -439,15 +459,17 @@ def run_ours(args):
     if not args.no_cpu_baseline and rank == 0:
         secs, runs = 0.0, 0
         while secs < 10.0:      # at least ~10 s of oracle work
-            s1, nodes, its_s = oracle_sample(gpu.params_dict(params), args.tol, args.method)
+            s1, nodes, its_s = oracle_sample(oracle_params(args), args.tol, args.method, args.oracle_sample)
             secs, runs = secs + s1, runs + 1
         secs /= runs
+        sn = "x".join(str(v) for v in args.oracle_sample)
         cpu = {"value": scale_to_workload(secs, nodes, its_s, P.N, float(np.mean(its))), "unit": UNIT, "cores": 1,
                "kind": "oracle",
+               "extrapolated": f"by unknowns x iterations from {nodes} to {P.N} nodes",
                "sample": f"one oracle solve (setup + FGMRES + cycle + reconstruction, tol {args.tol:g}) of the same "
-                         f"model family at {SAMPLE_N[0]}x{SAMPLE_N[1]}x{SAMPLE_N[2]} nodes: {nodes} nodes x {its_s} "
-                         f"iterations in {secs:.1f} s, scaled by unknowns*iterations to {P.N} nodes x "
-                         f"{np.mean(its):.1f} iterations (mean of {runs} runs)"}
+                         f"model family at {sn} nodes: {nodes} nodes x {its_s} iterations in {secs:.1f} s "
+                         f"({nodes * its_s / secs:.3g} unknowns x iterations/s, one thread), scaled by "
+                         f"unknowns*iterations to {P.N} nodes x {np.mean(its):.1f} iterations (mean of {runs} runs)"}
 
     breakdown = kernel_breakdown(solver, a) if args.breakdown and rank == 0 else None
 
@@ -557,32 +579,35 @@ def method_comparison(method, P, kappa, gamma, tau1, args, dev):
 
 
 def run_reference(args):
-    """The CPU oracle as the reference arm (rank 0 only)."""
+    """The CPU oracle as the reference arm (rank 0 only).  Nothing here loads
+    the CUDA library: the oracle's settings come from oracle_params."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import numpy as np
-    from paper_1712_06091_gb300.adr import params_dict
-    pd = params_dict(build_params(args)[-1])
+    pd = oracle_params(args)
     N = int(np.prod(WORKLOADS[args.workload]))
     # iterations of the GPU solve at 257x257x129 with this cycle (bench config, measured)
     full_its = {"helmholtz-sl": 49.0, "adr-central": CEN_FULL_ITERATIONS}.get(args.method, 70.0)
     for _ in range(min(args.warmup, 1)):
-        oracle_sample(pd, args.tol, args.method)
+        oracle_sample(pd, args.tol, args.method, args.oracle_sample)
     secs, its = [], []
     for _ in range(args.steps):
-        s, nodes, k = oracle_sample(pd, args.tol, args.method)
+        s, nodes, k = oracle_sample(pd, args.tol, args.method, args.oracle_sample)
         secs.append(s)
         its.append(k)
     value = scale_to_workload(float(np.mean(secs)), nodes, float(np.mean(its)), N, full_its)
-    sample = (f"oracle solve per step at {SAMPLE_N} nodes ({nodes} nodes x {np.mean(its):.0f} iterations in "
-              f"{np.mean(secs):.1f} s), scaled by unknowns*iterations to {N} nodes x {full_its:.0f} iterations")
+    sn = "x".join(str(v) for v in args.oracle_sample)
+    sample = (f"oracle solve per step at {sn} nodes ({nodes} nodes x {np.mean(its):.0f} iterations in "
+              f"{np.mean(secs):.1f} s, one thread), scaled by unknowns*iterations to {N} nodes x {full_its:.0f} "
+              f"iterations")
     out = {"impl": "reference", "metric": metric_for(args), "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "sample": list(SAMPLE_N), "assumed_full_iterations": full_its,
-                      "params": pd},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": args.workload, "sample": list(args.oracle_sample),
+                      "assumed_full_iterations": full_its, "params": pd},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "extrapolated": f"by unknowns x iterations from {nodes} to {N} nodes"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
