@@ -298,6 +298,11 @@ void launch_coarse_gmres_grid(const Dims& g, const C<T>* A, const C<T>* dinv, co
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // A barrier that timed out in an earlier solve may have left its arrival
+  // count part-filled and raised the error word: every solve starts from zero
+  // (memset nodes when captured).
+  cudaMemsetAsync(gs.bar, 0, sizeof(unsigned) * 2 * (size_t)g.B, st);
+  cudaMemsetAsync(gs.err, 0, sizeof(int) * (size_t)g.B, st);
   count_launches(1);
   if (g.dim == 2) cudaLaunchKernelEx(&cfg, k_coarse_gmres_grid<2, T>, g, A, dinv, b, x, V, z, k, gs);
   else cudaLaunchKernelEx(&cfg, k_coarse_gmres_grid<3, T>, g, A, dinv, b, x, V, z, k, gs);

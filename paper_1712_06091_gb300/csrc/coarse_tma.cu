@@ -132,10 +132,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   const int64_t ntiles = (g.N + 31) >> 5;
   const int64_t stride = (int64_t)gridDim.x * WARPS;
   const int64_t t0 = (int64_t)blockIdx.x * WARPS + warp;
+  unsigned pending = 0u;   // bit s: stage s has a copy issued and not yet consumed (warp-uniform)
   auto issue = [&](int64_t t, int s) {
-    if (lane == 0 && t < ntiles) {
-      mbar_expect_tx(&mbar[warp][s], kTileBytes);
-      bulk_load(s ? buf1 : buf0, A + t * (int64_t)W * 32, kTileBytes, &mbar[warp][s]);
+    if (t < ntiles) {
+      if (lane == 0) {
+        mbar_expect_tx(&mbar[warp][s], kTileBytes);
+        bulk_load(s ? buf1 : buf0, A + t * (int64_t)W * 32, kTileBytes, &mbar[warp][s]);
+      }
+      pending |= 1u << s;
     }
   };
   issue(t0, 0);
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     fail = __any_sync(0xffffffffu, fail);
     if (fail) break;
     phase ^= 1u << s;
+    pending &= ~(1u << s);
     const int64_t j = t * 32 + lane;
     if (j < g.N) {
       int i0, i1, i2;
@@ -177,9 +182,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     issue(t + STAGES * stride, s);
   }
   if (fail) {
-    // wait (bounded) for this warp's copies still in flight, mark the failure:
-    // the weight (kTmaMr) or the tiles this warp did not compute become NaN
-    for (int q = 0; q < STAGES; ++q) mbar_wait(&mbar[warp][q], (phase >> q) & 1u);
+    // wait (bounded) for this warp's copies still in flight (only stages with
+    // an issued, unconsumed copy), mark the failure: the weight (kTmaMr) or the
+    // tiles this warp did not compute become NaN.  A copy can still be
+    // outstanding when the warp leaves only if this second wait also runs out.
+    for (int q = 0; q < STAGES; ++q)
+      if ((pending >> q) & 1u) mbar_wait(&mbar[warp][q], (phase >> q) & 1u);
     if (lane == 0) {
       atomicExch(err, 1);
       s_fail = 1;

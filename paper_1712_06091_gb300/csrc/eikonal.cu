@@ -109,9 +109,10 @@ using namespace adr;
 
 extern "C" int adr_traveltime(int dim, const int* n, const double* h, const int* src, const double* kappa, double* tau1,
                               int max_sweeps, void* stream, int* sweeps_done) {
-  if ((dim != 2 && dim != 3) || !n || !h || !src || !kappa || !tau1 || max_sweeps < 1) return ADR_ERR_ARG;
+  if ((dim != 2 && dim != 3) || !n || !h || !src || !kappa || !tau1 || max_sweeps < 1)
+    return set_last_error(ADR_ERR_ARG, "invalid argument");
   for (int d = 0; d < dim; ++d)
-    if (n[d] < 2 || !(h[d] > 0.0) || src[d] < 0 || src[d] >= n[d]) return ADR_ERR_ARG;
+    if (n[d] < 2 || !(h[d] > 0.0) || src[d] < 0 || src[d] >= n[d]) return set_last_error(ADR_ERR_ARG, "invalid grid or source");
   cudaStream_t st = (cudaStream_t)stream;
   Dims g = make_dims(dim, n);
   EikParams P{};
@@ -122,34 +123,38 @@ extern "C" int adr_traveltime(int dim, const int* n, const double* h, const int*
   P.js = P.src[0] + g.s1 * P.src[1] + g.s2 * P.src[2];
   int* flag = nullptr;
   int* host_flag = nullptr;
-  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return ADR_ERR_OOM;
-  if (cudaMallocHost(&host_flag, sizeof(int)) != cudaSuccess) {
+  cudaError_t e = cudaMalloc(&flag, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_last_error(ADR_ERR_OOM, (std::string("cudaMalloc of the sweep flag: ") + cudaGetErrorString(e)).c_str());
+  }
+  e = cudaMallocHost(&host_flag, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
     cudaFree(flag);
-    return ADR_ERR_OOM;
+    return set_last_error(ADR_ERR_OOM, (std::string("cudaMallocHost of the sweep flag: ") + cudaGetErrorString(e)).c_str());
   }
   count_launches(1), k_eik_init<<<blocks_for(g.N, 256), 256, 0, st>>>(tau1, g.N, P.js, kappa);
   int done = 0;
-  int rc = ADR_OK;
   const int check_every = 16;
-  while (done < max_sweeps) {
-    cudaMemsetAsync(flag, 0, sizeof(int), st);
-    for (int k = 0; k < check_every && done < max_sweeps; ++k, ++done) {
+  e = cudaGetLastError();
+  while (e == cudaSuccess && done < max_sweeps) {
+    e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    for (int k = 0; e == cudaSuccess && k < check_every && done < max_sweeps; ++k, ++done) {
       if (dim == 2) count_launches(1), k_eik_sweep<2><<<blocks_for(g.N, 256), 256, 0, st>>>(g, P, kappa, tau1, flag);
       else count_launches(1), k_eik_sweep<3><<<blocks_for(g.N, 256), 256, 0, st>>>(g, P, kappa, tau1, flag);
+      e = cudaGetLastError();
     }
-    if (cudaMemcpyAsync(host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-      rc = ADR_ERR_CUDA;
-      break;
-    }
-    if (*host_flag == 0) break;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && *host_flag == 0) break;
   }
-  if (rc == ADR_OK && cudaGetLastError() != cudaSuccess) rc = ADR_ERR_CUDA;
   cudaFree(flag);
   cudaFreeHost(host_flag);
   if (sweeps_done) *sweeps_done = done;
-  if (rc == ADR_OK && done >= max_sweeps) rc = ADR_ERR_NOT_CONVERGED;
-  return rc;
+  if (e != cudaSuccess) return set_last_error(ADR_ERR_CUDA, (std::string("travel-time sweeps: ") + cudaGetErrorString(e)).c_str());
+  if (done >= max_sweeps) return set_last_error(ADR_ERR_NOT_CONVERGED, "max_sweeps reached while tau1 still changed");
+  return ADR_OK;
 }
 
 // ---------------------------------------------------------------------------

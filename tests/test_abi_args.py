@@ -93,3 +93,16 @@ def test_grid_beyond_31_bit_indices_rejected(adrlib):
     out = ctypes.c_void_p()
     rc = adrlib.adr_operator_create(3, n, h, s, 1.0, DUMMY, DUMMY, DUMMY, None, None, ctypes.byref(out))
     assert rc == _lib.ADR_ERR_ARG and b"too large" in adrlib.adr_last_error()
+
+
+def test_traveltime_invalid_arguments_set_the_error_text(adrlib):
+    """Both travel-time entry points report an invalid argument through adr_last_error (no device work)."""
+    from paper_1712_06091_gb300 import _lib
+    n, h, s = _grid()
+    adrlib.adr_params_default(None)                      # leaves an unrelated message behind
+    for fn in (adrlib.adr_traveltime, adrlib.adr_traveltime_static):
+        rc = fn(2, n, h, s, DUMMY, DUMMY, 0, None, None)
+        assert rc == _lib.ADR_ERR_ARG and b"invalid argument" in adrlib.adr_last_error()
+        bad = (ctypes.c_int * 3)(99, 99, 0)
+        rc = fn(2, n, h, bad, DUMMY, DUMMY, 10, None, None)
+        assert rc == _lib.ADR_ERR_ARG and b"invalid grid or source" in adrlib.adr_last_error()
