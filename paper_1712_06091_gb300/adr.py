@@ -354,17 +354,22 @@ def solve_host(n, h, src, omega, kappa, tau1, gamma, params=None, tol=1e-8, maxi
 
 
 def misfit_gradient(n, h, omega, kappa, gamma, sources, tau1s, receivers, data, params=None, tol=1e-10, maxit=500,
-                    device="cuda"):
+                    device="cuda", rank=None, world=None):
     """Receiver misfit J(kappa) = sum_s 1/2 |R u_s - d_s|^2 and dJ/dkappa (tau1 held fixed).
 
     Per source: adr_operator_update, adr_solve, adr_reconstruct, adr_receivers,
-    adr_adjoint_solve, adr_kappa_gradient; one operator (params.adjoint = 1) is
-    reused over the sources.  Returns (J, grad) with grad a float64 tensor.
+    adr_adjoint_solve, adr_kappa_gradient; one operator (a copy of params with
+    adjoint = 1; the caller's params are not modified) is reused over the
+    sources.  Under torch.distributed (or with rank / world given) every rank
+    solves its `shard.partition` share of the sources and the misfit and
+    gradient are summed over the ranks by one all-reduce, so every rank
+    returns the full (J, grad).  Returns (J, grad) with grad a float64 tensor.
     """
+    from . import shard
     device = torch.device(device)
     if device.type == "cuda" and device.index is None:
         device = torch.device("cuda", torch.cuda.current_device())
-    p = params if params is not None else default_params()
+    p = L.Params.from_buffer_copy(params) if params is not None else default_params()
     p.adjoint = 1
     N = int(np.prod(n))
     k = _dev_real(kappa, N, device)
@@ -372,20 +377,24 @@ def misfit_gradient(n, h, omega, kappa, gamma, sources, tau1s, receivers, data, 
     grad = torch.zeros(N, dtype=torch.float64, device=device)
     a = torch.empty(N, dtype=torch.complex128, device=device)
     lam = torch.empty(N, dtype=torch.complex128, device=device)
-    J = 0.0
     op = None
+
+    def one_source(i):
+        nonlocal op
+        src, t1, d = sources[i], tau1s[i], data[i]
+        if op is None:
+            op = Operator(n, h, src, omega, k, t1, g, params=p, device=device)
+        else:
+            op.update(src, omega, k, t1, g)
+        op.solve(tol=tol, maxit=maxit, out=a)
+        u = op.reconstruct(a)
+        Js, _, rhs = op.receivers(receivers, d, u)
+        op.adjoint_solve(rhs, tol=tol, maxit=maxit, out=lam)
+        op.kappa_gradient(k, g, a, lam, grad)    # accumulates into grad
+        return Js, grad
+
     try:
-        for src, t1, d in zip(sources, tau1s, data):
-            if op is None:
-                op = Operator(n, h, src, omega, k, t1, g, params=p, device=device)
-            else:
-                op.update(src, omega, k, t1, g)
-            op.solve(tol=tol, maxit=maxit, out=a)
-            u = op.reconstruct(a)
-            Js, _, rhs = op.receivers(receivers, d, u)
-            op.adjoint_solve(rhs, tol=tol, maxit=maxit, out=lam)
-            op.kappa_gradient(k, g, a, lam, grad)
-            J += Js
+        J, grad = shard.sharded_sum(len(sources), one_source, rank, world, out=grad)
     finally:
         if op is not None:
             op.close()

@@ -1,10 +1,11 @@
 """Problem sharding across ranks (one process per GPU).
 
 Independent point-source problems (sources, frequencies) need no exchange: each
-rank solves its own share, and the only collective is the timing reduction
-(max over ranks) that reports the whole job's time.  A single solve is not
-split across GPUs (it would need a halo exchange per stencil apply and an
-all-reduce per Krylov dot).
+rank solves its own share.  The collectives are the timing reduction (max
+over ranks) that reports the whole job's time and, for the receiver-misfit
+gradient, one all-reduce sum of the per-rank misfit and slowness gradient
+(`sharded_sum`).  A single solve is not split across GPUs (it would need a
+halo exchange per stencil apply and an all-reduce per Krylov dot).
 """
 from __future__ import annotations
 
@@ -62,3 +63,39 @@ def sum_over_ranks(value, device=None):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return t.item()
+
+
+def sharded_sum(count, per_item, rank=None, world=None, weights=None, out=None):
+    """Sum of per_item(i) -> (scalar, tensor) over i in [0, count), each rank
+    evaluating its `partition` share, then one all-reduce sum over the ranks.
+
+    The gradient of a multi-source misfit is a sum over sources, so ranks
+    that solve disjoint sources only exchange their partial sums once, at the
+    end: the scalar rides in the last entry of one all-reduce buffer with the
+    tensor.  rank / world default to the initialised process group (else 0
+    and 1); `out` (a tensor shaped like per_item's) receives this rank's sum
+    before the reduction, and the total after it.  Returns (scalar, tensor).
+    """
+    import torch
+    import torch.distributed as dist
+    grouped = dist.is_available() and dist.is_initialized()
+    if rank is None or world is None:
+        rank, world = (dist.get_rank(), dist.get_world_size()) if grouped else (0, 1)
+    mine = partition(count, rank, world, weights)
+    scalar, total = 0.0, out
+    for i in mine:
+        s, t = per_item(i)
+        scalar += float(s)
+        if total is None:
+            total = t.clone()
+        elif t is not total:
+            total += t
+    if total is None:
+        raise ValueError("no item on this rank and no `out` tensor to shape the reduction")
+    if world == 1 or not grouped:
+        return scalar, total
+    buf = torch.cat([total.reshape(-1).to(torch.float64), torch.tensor([scalar], dtype=torch.float64,
+                                                                        device=total.device)])
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM)
+    total.copy_(buf[:-1].reshape(total.shape).to(total.dtype))
+    return float(buf[-1].item()), total

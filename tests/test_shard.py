@@ -63,3 +63,64 @@ def test_two_rank_gloo_sharding():
     assert [r[1] for r in results] == [[0, 1, 2, 3, 4], [5, 6, 7, 8, 9]]
     assert all(r[2] == 2.5 for r in results)
     assert all(r[3] == 10 for r in results)
+
+
+def _item(i, n=64):
+    """A source's misfit and gradient stand-in: deterministic per index."""
+    import torch
+    g = torch.Generator().manual_seed(1000 + i)
+    return float(i * i + 0.5), torch.randn(n, dtype=torch.float64, generator=g)
+
+
+def _gradient_worker(rank, world, port, count, out):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        seen = []
+
+        def accumulate(i, acc=torch.zeros(64, dtype=torch.float64)):
+            # the misfit_gradient pattern: every source adds into one buffer
+            seen.append(i)
+            J, g = _item(i)
+            acc += g
+            return J, acc
+
+        buf = torch.zeros(64, dtype=torch.float64)
+        J, grad = shard.sharded_sum(count, lambda i: accumulate(i, buf), out=buf)
+        out.put((rank, seen, J, grad.numpy().tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("count,world", [(16, 2), (2, 3)])
+def test_sharded_gradient_allreduce_gloo(count, world):
+    """The sharded misfit gradient: each rank sums its partition's sources and
+    one all-reduce gives every rank the single-rank total (a rank without a
+    source contributes zeros)."""
+    import numpy as np
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gradient_worker, args=(r, world, port, count, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = sorted((out.get(timeout=120) for _ in procs), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert sorted(i for r in results for i in r[1]) == list(range(count))   # every source once
+    J_ref = sum(_item(i)[0] for i in range(count))
+    g_ref = sum(_item(i)[1].numpy() for i in range(count))
+    for _, _, J, g in results:
+        assert abs(J - J_ref) <= 1e-12 * J_ref
+        assert np.allclose(np.array(g), g_ref, rtol=1e-13, atol=1e-13)
+
+
+def test_sharded_sum_single_process():
+    import torch
+    J, g = shard.sharded_sum(5, _item, rank=0, world=1)
+    assert abs(J - sum(_item(i)[0] for i in range(5))) < 1e-12
+    assert torch.allclose(g, sum(_item(i)[1] for i in range(5)))
