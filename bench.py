@@ -113,12 +113,19 @@ def parse():
                          "adr-central: H_cen a = q by the two-stage solve (Alg. ADRlong)")
     ap.add_argument("--shift", type=float, default=SL_SHIFT)
     ap.add_argument("--no-comparison", action="store_true")
-    ap.add_argument("--breakdown", action="store_true",
-                    help="after the timed steps, time each instrumented kernel class live (one extra step per class)")
+    ap.add_argument("--no-breakdown", action="store_true",
+                    help="skip the per-class live timing after the timed steps (one extra step per class) and the "
+                         "whole-cycle roofline derived from it")
     ap.add_argument("--restart", type=int, default=None)
+    ap.add_argument("--coarse-solver", default=None, choices=["auto", "kernels", "cta", "cluster", "grid"],
+                    help="form of the coarsest-grid GMRES (same arithmetic; default: the library's choice)")
     ap.add_argument("--cycle", default=None)
     ap.add_argument("--sweeps", default=None, help="comma-separated relaxations per level")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--paper-table", action="store_true",
+                    help="probe only: the paper's solver configuration on two models at two resolutions each")
+    ap.add_argument("--fp-rates", action="store_true",
+                    help="probe only: float64 / float32 GEMM throughput of this GPU (no solve)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", default="x".join(str(v) for v in SAMPLE_N),
                     help="grid of the oracle's bounded sample (cpu_baseline and --impl reference), e.g. 33x33x17")
@@ -149,6 +156,8 @@ def build_params(args, method=None):
           "relax_blocks": bench_relax_blocks()}
     if args.cycle:
         kw["cycle"] = args.cycle
+    if args.coarse_solver:
+        kw["coarse_solver"] = args.coarse_solver
     if args.sweeps:
         kw["sweeps"] = [int(v) for v in args.sweeps.split(",")]
     if method == "helmholtz-sl":
@@ -174,9 +183,13 @@ class MethodSolver:
                     for p in self.params]
         self.op = self.ops[-1]
 
-    def step(self, out):
+    def step(self, out, marks=None):
+        """One step; marks: optional [event, event] recorded after the setup and after the whole step (the
+        caller records the start), on the operator's stream."""
         for op in self.ops:
             op.update(self.P.src, self.P.omega, self.kappa, self.tau1, self.gamma)
+        if marks:
+            marks[0].record(self.op.stream)
         if len(self.ops) == 1:
             _, info = self.op.solve(tol=self.args.tol, maxit=self.args.maxit, out=out)
         else:
@@ -186,7 +199,10 @@ class MethodSolver:
             info["stage1_iterations"] = i1[0]["iterations"]
             info["stage2_iterations"] = i2[0]["iterations"]
             info["iterations"] = i1[0]["iterations"] + i2[0]["iterations"]
-        return info, self.op.reconstruct(out)
+        u = self.op.reconstruct(out)
+        if marks:
+            marks[1].record(self.op.stream)
+        return info, u
 
     def close(self):
         for op in self.ops:
@@ -334,7 +350,8 @@ def oracle_sample(pd, tol, method="adr-upwind", n=None):
     tau1 = np.zeros(g.N) if sl else eikonal.factored_fast_marching(g, P.kappa, P.src, order=2)
     prm = omg.CycleParams(cycle=pd["cycle"], relax=pd["relax"], pre=pd["pre_sweeps"], post=pd["post_sweeps"],
                           weights=pd["jacobi_weight"], coarse_iterations=pd["coarse_iterations"],
-                          kcycle_iterations=pd["kcycle_iterations"])
+                          kcycle_iterations=pd["kcycle_iterations"],
+                          coarse_reorth_eta=pd["reorth_eta"] if pd["reorth_eta"] < 1.0 else None)
     t0 = time.perf_counter()
     if method == "adr-central":
         from oracle import twostage
@@ -379,7 +396,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     kappa = torch.from_numpy(P.kappa).to(dev)
     gamma = torch.from_numpy(P.gamma).to(dev)
-    tau1, sweeps = gpu.traveltime(P.n, P.h, P.src, kappa)
+    # tau1 by the second-order factored eikonal on the device (input preparation, outside the timed region;
+    # its own time is reported)
+    gpu.traveltime(P.n, P.h, P.src, kappa, order=2)
+    torch.cuda.synchronize()
+    t_eik = time.perf_counter()
+    tau1, sweeps = gpu.traveltime(P.n, P.h, P.src, kappa, order=2)
+    torch.cuda.synchronize()
+    t_eik = time.perf_counter() - t_eik
     solver = MethodSolver(args.method, P, kappa, tau1, gamma, args, dev)
     params = solver.params[-1]
     op = solver.op
@@ -400,14 +424,17 @@ def run_ours(args):
         dist.barrier()
     launches0 = gpu.kernel_launches()
     infos = []
+    # per step: start, end of setup, end of step (events on the same stream, inside the timed region)
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     with ClockSampler(local) as clocks:
         t_wall = time.perf_counter()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         nvtx_push("timed")
         ev0.record(stream)
-        for _ in range(args.steps):
-            info, _ = step()
+        for k in range(args.steps):
+            marks[k][0].record(stream)
+            info, _ = solver.step(a, marks[k][1:])
             infos.append(info)
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -416,6 +443,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
     launches = gpu.kernel_launches() - launches0
+    setup_ms = sum(m[0].elapsed_time(m[1]) for m in marks) / args.steps
+    solve_ms = sum(m[1].elapsed_time(m[2]) for m in marks) / args.steps
     k_count, k_ms = op.profile_read()
     op.profile("none")
     from paper_1712_06091_gb300 import shard
@@ -471,11 +500,15 @@ def run_ours(args):
                          f"({nodes * its_s / secs:.3g} unknowns x iterations/s, one thread), scaled by "
                          f"unknowns*iterations to {P.N} nodes x {np.mean(its):.1f} iterations (mean of {runs} runs)"}
 
-    breakdown = kernel_breakdown(solver, a) if args.breakdown and rank == 0 else None
+    breakdown = kernel_breakdown(solver, a) if not args.no_breakdown and rank == 0 else None
+
+    cyc_roof = cycle_roofline(breakdown, levels, gpu.params_dict(params), peak, peak_kind)
 
     comparison = None
     if not args.no_comparison and rank == 0:
         comparison = [method_comparison(m, P, kappa, gamma, tau1, args, dev) for m in METHODS if m != args.method]
+        if args.precision == "f32":     # the same method with the float64 cycle (the plain float64 solve)
+            comparison.append(method_comparison(args.method, P, kappa, gamma, tau1, args, dev, precision="f64"))
 
     if rank == 0:
         out = {
@@ -484,7 +517,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32 cycle + f64 Krylov" if args.precision == "f32" else "f64",
             "data": "synthetic (seeded layered-gradient model with Gaussian anomalies; " +
                     ("tau1 = 0: the standard Helmholtz matrix)" if args.method == "helmholtz-sl" else
-                     "tau1 from the library's travel-time kernel)"),
+                     "tau1 from the library's second-order travel-time kernel)"),
             "method": args.method,
             "config": {"workload": args.workload, "method": args.method, "nodes": P.N, "grid": list(P.n), "spacing_km": P.h[0],
                        "omega": P.omega, "source": list(src), "tol": args.tol, "params": gpu.params_dict(params),
@@ -492,8 +525,11 @@ def run_ours(args):
                        "unknown_iterations_per_s": unknown_iterations_per_s(value, P.N, its),
                        "stage1_iterations": [i.get("stage1_iterations") for i in infos] if len(solver.ops) > 1 else None,
                        "l2": "no flush: inputs and working set (~9 GB) exceed L2", "wall_s": t_wall,
-                       "traveltime_sweeps": sweeps},
+                       "traveltime_sweeps": sweeps, "traveltime_order": 2, "traveltime_ms": 1e3 * t_eik},
             "roofline": roofline,
+            "cycle_roofline": cyc_roof,
+            "setup_ms_per_step": setup_ms,
+            "solve_ms_per_step": solve_ms,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -528,6 +564,68 @@ def class_bandwidth(cls, us_per_launch, levels):
     return bytes_per_launch / (us_per_launch * 1e-6) / 1e9
 
 
+def cycle_bytes(levels, pd, dim=3):
+    """Algorithmic bytes of one float32 preconditioner application (the K- or
+    V-cycle with minimal-residual relaxation the bench runs), summed over the
+    launches of the cycle in their order: every array a launch reads or
+    writes counted once per launch (8 B per complex float32 entry, the packed
+    finest-grid rows 4 (2 + 4 dim) B per node, the split Galerkin stencils
+    (27 complex + 54 imaginary-only floats in 3D, 9 + 12 in 2D), no reuse
+    between launches assumed).  The coarsest grid's bytes are counted the
+    same way although its working set is L2-resident."""
+    C = 8
+    fine_rows = 4 * (2 + 4 * dim)
+    stencil = (27 * 8 + 54 * 4) if dim == 3 else (9 * 8 + 12 * 4)
+    N = [lv["nodes"] for lv in levels]
+    L = len(N)
+
+    def update(x_zero, has_next):       # x += alpha z ; r -= alpha w ; z_next = dinv r
+        return (0 if x_zero else C) + C + 4 * C + (2 * C if has_next else 0)
+
+    def relax(l, sweeps, x_zero):
+        row = fine_rows if l == 0 else stencil
+        b = 3 * C if x_zero else row + 5 * C                # D^{-1} b, or the residual with D^{-1}
+        for s in range(sweeps):
+            b += row + 3 * C + update(x_zero and s == 0, s + 1 < sweeps)
+        return b * N[l]
+
+    def coarse(l):
+        k = pd["coarse_iterations"]
+        n = N[l]
+        b = C * n + 4 * C * n                                # |b|, V_0 and z = D^{-1} V_0
+        for j in range(k):
+            b += (stencil + 2 * C + (j + 1) * C) * n         # w = A z with the first pass's dots
+            b += (2 * C + 2 * (j + 1) * C) * n               # w -= V ha, hb = V^H w, |w|^2
+            if j + 1 < k:
+                b += ((j + 1) * C + 5 * C) * n               # V_{j+1}, z
+        return b + (k * C + 2 * C) * n                       # x = D^{-1} V y
+
+    def cgs2(k, n):                                          # three passes over k basis vectors
+        return (k * C + C + (2 * k * C + 2 * C) + (k * C + 2 * C)) * n
+
+    def kcycle(l):
+        k = pd["kcycle_iterations"]
+        n = N[l]
+        b = C * n + 2 * C * n                                # |b| and V_0
+        for j in range(k):
+            b += cycle(l)
+            b += (stencil + 2 * C) * n + cgs2(j + 1, n)      # A z_j and its orthogonalisation
+            if j + 1 < k:
+                b += 2 * C * n
+        return b + (k * C + C) * n                           # x = Z y
+
+    def cycle(l):
+        if l == L - 1:
+            return coarse(l)
+        b = relax(l, pd["pre_sweeps"][l], True)
+        b += C * N[l] + C * N[l + 1]                         # restriction
+        b += kcycle(l + 1) if pd["cycle"] == "K" and l + 1 < L - 1 else cycle(l + 1)
+        b += C * N[l + 1] + 2 * C * N[l]                     # prolongation and correction
+        return b + relax(l, pd["post_sweeps"][l], False)
+
+    return cycle(0)
+
+
 def kernel_breakdown(solver, a):
     """Live time of each instrumented kernel class inside a step: CUDA events
     around every launch of the class (event-record nodes in the captured
@@ -537,7 +635,7 @@ def kernel_breakdown(solver, a):
     op = solver.op
     levels = op.info()["levels"]
     out = {}
-    for cls in ("level1_relax", "fine_relax", "outer_apply", "coarsest"):
+    for cls in ("level1_relax", "fine_relax", "outer_apply", "coarsest", "cycle"):
         op.profile(cls)
         solver.step(a)
         op.profile(cls)
@@ -551,12 +649,33 @@ def kernel_breakdown(solver, a):
     return out
 
 
-def method_comparison(method, P, kappa, gamma, tau1, args, dev):
-    """Another method on the same medium, source and tolerance (the paper's
-    comparison of Sec. 4): one warm-up step, then one step (operator setup,
-    solve, reconstruction) timed with CUDA events."""
+def cycle_roofline(breakdown, levels, pd, peak, peak_kind):
+    """The whole cycle against the HBM roofline: its algorithmic bytes (cycle_bytes)
+    over the live duration of one cycle (CUDA events around each replay of the
+    captured cycle inside a step)."""
+    cyc = breakdown.get("cycle") if breakdown else None
+    if not cyc or not cyc.get("us_per_launch") or pd["precision"] != "f32":
+        return None
+    b = cycle_bytes(levels, pd, len(levels[0]["n"]))
+    gbs = b / (cyc["us_per_launch"] * 1e-6) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_cycle": b, "cycles_per_step": cyc["launches_per_step"],
+            "avg_cycle_ms": cyc["us_per_launch"] / 1e3,
+            "note": "sum of the algorithmic bytes of every launch of one preconditioner application (model in "
+                    "bench.cycle_bytes) over its live event time"}
+
+
+def method_comparison(method, P, kappa, gamma, tau1, args, dev, precision=None):
+    """Another method (or the same one in another cycle precision) on the same
+    medium, source and tolerance (the paper's comparison of Sec. 4): one
+    warm-up step, then one step (operator setup, solve, reconstruction) timed
+    with CUDA events."""
+    import copy
     import torch
     from paper_1712_06091_gb300 import adr as gpu
+    if precision:
+        args = copy.copy(args)
+        args.precision = precision
     solver = MethodSolver(method, P, kappa, tau1, gamma, args, dev)
     a = torch.empty(P.N, dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -568,7 +687,8 @@ def method_comparison(method, P, kappa, gamma, tau1, args, dev):
     info, _ = solver.step(a)
     ev1.record(stream)
     torch.cuda.synchronize()
-    out = {"method": method, "metric": {"helmholtz-sl": SL_METRIC, "adr-central": CEN_METRIC}.get(method, METRIC),
+    out = {"method": method, "precision": args.precision,
+           "metric": {"helmholtz-sl": SL_METRIC, "adr-central": CEN_METRIC}.get(method, METRIC),
            "value": 1e3 / ev0.elapsed_time(ev1), "unit": UNIT, "ms_per_step": ev0.elapsed_time(ev1),
            "iterations": info["iterations"], "rel_residual": info["rel_residual"],
            "params": [gpu.params_dict(p) for p in solver.params]}
@@ -636,7 +756,7 @@ def batch_problems(n, count, seed=3):
     out = []
     for (i0, i1), i2 in zip(lateral, depth):
         src = (int(i0), int(i1), int(i2))
-        tau1, _ = gpu.traveltime(P.n, P.h, src, kappa)
+        tau1, _ = gpu.traveltime(P.n, P.h, src, kappa, order=2)
         out.append((src, P.omega, kappa, tau1, torch.from_numpy(P.gamma).cuda()))
     return P, out
 
@@ -788,9 +908,86 @@ def run_gradient(args):
     print(json.dumps(out))
 
 
+PAPER_TABLE = (("marine2d", (257, 257)), ("marine2d", (513, 513)), ("layered3d", (129, 129, 65)),
+               ("layered3d", (257, 257, 129)))
+
+
+def run_paper_table(args):
+    """The paper's own solver configuration (Sec. 4.2): flexible GMRES(5) to a
+    1e-5 relative residual from zero, 5 levels of K-cycles (Alg. Kcycle, the
+    0.1 coarse threshold, FGMRES(2) inner steps), Jacobi-GMRES relaxation with
+    l+1 sweeps, 10 coarsest GMRES steps, beta = 0.25; the standard Helmholtz
+    matrix with the shifted-Laplacian cycle (alpha = 0.2) beside it.  Runs the
+    2D marine and 3D layered models at two resolutions each (10 points per
+    wavelength, so the frequency doubles with the resolution) and prints the
+    iteration counts and solve times (the trends of the paper's tables)."""
+    import torch
+    from paper_1712_06091_gb300 import adr as gpu
+    from paper_1712_06091_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    rows = []
+    for model, n in PAPER_TABLE:
+        P = W.marine_2d(n) if model == "marine2d" else W.layered_3d(n)
+        kappa = torch.from_numpy(P.kappa).to(dev)
+        gamma = torch.from_numpy(P.gamma).to(dev)
+        tau1, _ = gpu.traveltime(P.n, P.h, P.src, kappa, order=2)
+        for method, tau, shift in (("adr-upwind", tau1, 0.0), ("helmholtz-sl", torch.zeros_like(tau1), 0.2)):
+            prm = gpu.default_params(precision="f32", levels=5, restart=5, kcycle_threshold=0.1, shift=shift,
+                                     relax_blocks=bench_relax_blocks())
+            with gpu.Operator(P.n, P.h, P.src, P.omega, kappa, tau, gamma, params=prm, device=dev) as op:
+                op.solve(tol=1e-5, maxit=1000)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(op.stream)
+                a, info = op.solve(tol=1e-5, maxit=1000)
+                e1.record(op.stream)
+                torch.cuda.synchronize()
+                rows.append({"model": model, "grid": list(P.n), "nodes": P.N, "method": method,
+                             "ppw": P.meta.get("ppw"), "omega": P.omega, "iterations": info["iterations"],
+                             "rel_residual": info["rel_residual"], "solve_ms": e0.elapsed_time(e1),
+                             "levels": len(op.info()["levels"])})
+    print(json.dumps({"probe": "paper_table", "config": "FGMRES(5), 5 levels, K-cycle (threshold 0.1), 1e-5, float32 "
+                      "cycle", "rows": rows}))
+
+
+def run_fp_rates(args):
+    """Machine probe: float64 and float32 (TF32 off) throughput of square
+    cuBLAS GEMMs through torch, best of several timed runs with CUDA events.
+    The float64 figure bounds the library's float64 outer apply and
+    Gram-Schmidt passes, which are arithmetic-bound on this GPU; the float32
+    figure shows how far the float32 cycle is from its own ALU bound."""
+    import torch
+    torch.cuda.set_device(0)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {"probe": "fp_rates", "unit": "TFLOP/s", "device": torch.cuda.get_device_name(0)}
+    for name, dt, n in (("fp64", torch.float64, 8192), ("fp32", torch.float32, 8192)):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        for _ in range(2):
+            torch.matmul(a, b)
+        best = None
+        with ClockSampler(0) as clocks:
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+        out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+        out[name + "_clocks"] = clocks.summary()
+        del a, b
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.fp_rates:
+        run_fp_rates(args)
+    elif args.paper_table:
+        run_paper_table(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched3d_3x32":
         run_batched(args)

@@ -88,18 +88,24 @@ typedef struct adr_params {
   int near_source;                     /* rows within this Chebyshev distance of the
                                           source use central advection (Sec. 2.2 says
                                           "distance of one node"; 1..4, default 1) */
-  double reorth_eta;                   /* outer Gram-Schmidt: the second classical pass
-                                          runs only when the first left less than
+  double reorth_eta;                   /* Gram-Schmidt of the outer FGMRES and of the
+                                          coarsest-grid GMRES (one launch per step, or
+                                          the cooperative form): the second classical
+                                          pass runs only when the first left less than
                                           reorth_eta |w| (Daniel-Gragg-Kaufman-Stewart
-                                          test); >= 1: always (CGS2).  Default 0.1 */
+                                          test); >= 1: always (CGS2).  The single-block
+                                          and cluster coarsest forms always run it.
+                                          Default 0.1 */
   int adjoint;                         /* 1: also build the conjugate-transposed
                                           operator and its hierarchy (adr_adjoint_solve,
                                           adr_apply_adjoint, adr_vcycle_adjoint); about
                                           doubles the operator's memory.  Default 0 */
   int relax_blocks;                    /* grid of the fused relaxation applies (blocks
                                           per problem, grid-stride beyond); 0 selects
-                                          2432 (16 per SM).  A launch shape, not
-                                          arithmetic: results do not depend on it
+                                          2432 (16 per SM).  The bulk-copy applies
+                                          (tma) run one block per SM, or relax_blocks
+                                          blocks when that is smaller.  A launch shape,
+                                          not arithmetic: results do not depend on it
                                           beyond rounding order.  0..10240 */
   int coarse_solver;                   /* form of the coarsest-grid GMRES (same arithmetic):
                                           ADR_COARSE_AUTO picks by size; the others force
@@ -134,6 +140,13 @@ typedef struct adr_params {
                                           the amplitude.  Stage 2 of Alg. ADRlong is
                                           scheme = prec_scheme = ADR_SCHEME_CEN, shift =
                                           0.2, rescale = 1.  Default 0 */
+  double kcycle_threshold;             /* early exit of the K-cycle's inner FGMRES
+                                          (Alg. Kcycle; Sec. 4.2 uses 0.1 on the coarse
+                                          grids): an inner solve whose residual falls to
+                                          this fraction of the restricted residual stops
+                                          and its later steps do not enter the result.
+                                          0 (default): the fixed kcycle_iterations steps.
+                                          0..1e6 */
 } adr_params_t;
 
 #define ADR_COARSE_AUTO 0      /* cluster up to 32768 nodes, else one block up to 8192, else kernels */
@@ -187,6 +200,22 @@ int adr_params_default(adr_params_t* p);
 int adr_operator_create(int dim, const int* n, const double* h, const int* src, double omega,
                         const double* kappa, const double* tau1, const double* gamma,
                         const adr_params_t* params, void* stream, adr_op_t* out);
+
+/* adr_operator_create for a travel time given as plain nodal values tau
+ * (device float64[N]) instead of the factor tau1 of tau = |x - x0| tau1: the
+ * coefficients of Eq. travel_time_coeff take d_d tau and d_dd tau by finite
+ * differences of tau itself (central inside, first-order / second-order
+ * one-sided on the boundary), the source row (Eq. helmADR2) and the
+ * reconstruction use tau directly.  tau must be the travel time from the
+ * source (zero at src).  Next to the source, where tau has its conical kink,
+ * the differences are only first-order accurate: the factored form of
+ * adr_operator_create is the more accurate input (Sec. 2.1).  Everything
+ * else (arguments, ownership, errors) as adr_operator_create;
+ * adr_operator_update on this operator takes plain tau in its tau1
+ * argument. */
+int adr_operator_create_tau(int dim, const int* n, const double* h, const int* src, double omega,
+                            const double* kappa, const double* tau, const double* gamma,
+                            const adr_params_t* params, void* stream, adr_op_t* out);
 
 /* Rebuilds the coefficients and the whole Galerkin hierarchy of an existing
  * operator for a new source, frequency and medium on the same grid, inside
@@ -349,6 +378,21 @@ int adr_kappa_gradient(adr_op_t op, const double* kappa, const double* gamma, co
 int adr_traveltime(int dim, const int* n, const double* h, const int* src, const double* kappa, double* tau1,
                    int max_sweeps, void* stream, int* sweeps_done);
 
+/* adr_traveltime with a choice of order.  order 1 is adr_traveltime.  order 2
+ * continues from that first-order fixed point with the second-order
+ * one-sided differences of the factored fast marching (Sec. 2.1): along each
+ * axis (3 t_j - 4 t_nb + t_nb2) / 2h where the node two steps out on the
+ * upwind side has the smaller travel time, first order at Chebyshev distance
+ * 1 from the source, the larger root of the local quadratic, axes dropped
+ * while the root would fall below a neighbour's travel time.  That phase
+ * iterates Jacobi sweeps (deterministic) until no node moves by more than a
+ * relative 1e-12, at most max_sweeps more sweeps; *sweeps_done counts both
+ * phases.  Allocates one int, one pinned int and (order 2) N float64 of
+ * device memory for the call.  Errors as adr_traveltime; ADR_ERR_ARG for
+ * another order. */
+int adr_traveltime_order(int dim, const int* n, const double* h, const int* src, const double* kappa, double* tau1,
+                         int order, int max_sweeps, void* stream, int* sweeps_done);
+
 /* adr_traveltime without any allocation.  The paper has no counterpart: this
  * is a deployment variant of the same computation, with the same arguments,
  * result and error codes as adr_traveltime.
@@ -382,6 +426,8 @@ int adr_traveltime_static(int dim, const int* n, const double* h, const int* src
 #define ADR_PROF_FINE_RELAX 2     /* minimal-residual apply on the finest level */
 #define ADR_PROF_OUTER_APPLY 3    /* float64 H_2up apply of the outer iteration */
 #define ADR_PROF_COARSEST 4       /* coarsest-grid solve */
+#define ADR_PROF_CYCLE 5          /* one whole preconditioner application (the
+                                     captured cycle, every level's kernels) */
 
 /* Instrumentation: brackets every launch of one kernel class of op with CUDA
  * events on the stream it runs on (inside the captured cycle as well) and

@@ -83,6 +83,20 @@ class Grid:
 # Travel-time coefficients (Eq. travel_time_coeff)
 # ---------------------------------------------------------------------------
 
+class PlainTau:
+    """A travel time given as plain nodal values tau instead of the factor
+    tau1 of tau = tau0 tau1.  Wherever a function below takes `tau1`, a
+    PlainTau may be passed: the coefficients then take d_d tau and d_dd tau by
+    the same finite differences of tau itself (central inside, one-sided on
+    the boundary) that the factored form applies to tau1, instead of
+    Eq. travel_time_coeff's product rule with the analytic tau0.  Next to the
+    source, where tau has its conical kink, these differences are only first
+    order accurate; the factored form avoids that (Sec. 2.1)."""
+
+    def __init__(self, values):
+        self.values = np.asarray(values, dtype=np.float64)
+
+
 def tau0_derivatives(grid, src, i):
     """tau0 = |x - x0| and its analytic first and second derivatives per axis."""
     dx = [(i[d] - src[d]) * grid.h[d] for d in range(grid.dim)]
@@ -132,6 +146,13 @@ def node_coefficients(grid, src, omega, kappa, gamma, tau1, j):
     - i w gamma kappa^2.
     """
     i = grid.coords(j)
+    if isinstance(tau1, PlainTau):                  # d tau and d^2 tau by differences of tau itself
+        tv = tau1.values
+        g = [tau1_first_derivative(grid, tv, i, d) for d in range(grid.dim)]
+        t = [tau1_second_derivative(grid, tv, i, d) for d in range(grid.dim)]
+        k2 = kappa[j] * kappa[j]
+        grad2 = sum(v * v for v in g)
+        return tv[j], g, t, omega * omega * (k2 - grad2) - 1j * omega * gamma[j] * k2
     r, d0, dd0 = tau0_derivatives(grid, src, i)
     t1 = tau1[j]
     g = []
@@ -148,7 +169,9 @@ def node_coefficients(grid, src, omega, kappa, gamma, tau1, j):
 
 
 def travel_time(grid, src, tau1):
-    """tau = tau0 * tau1 at every node."""
+    """tau = tau0 * tau1 at every node (a PlainTau: its values)."""
+    if isinstance(tau1, PlainTau):
+        return tau1.values.copy()
     out = np.empty(grid.N)
     for j in range(grid.N):
         r, _, _ = tau0_derivatives(grid, src, grid.coords(j))
@@ -203,10 +226,12 @@ def source_row(grid, src, omega, kappa, gamma, tau1):
     row = defaultdict(complex)
 
     def tau_at(i):
+        if isinstance(tau1, PlainTau):
+            return tau1.values[grid.index(i)]
         r, _, _ = tau0_derivatives(grid, src, i)
         return r * tau1[grid.index(i)]
 
-    tau_s = 0.0
+    tau_s = tau_at(src)          # 0 for the factored form (tau0 vanishes at the source)
     for d in range(grid.dim):
         h2 = grid.h[d] ** 2
         for s in (+1, -1):

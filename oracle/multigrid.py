@@ -20,7 +20,9 @@ Readings (also in the design notes):
       the coarse grid keeps every other node.
   M2  The coarsest GMRES is right-preconditioned by D = diag(A), uses
       classical Gram-Schmidt applied twice and stops early only on an exact
-      breakdown (h_{j+1,j} == 0).
+      breakdown (h_{j+1,j} == 0).  With coarse_reorth_eta < 1 the second
+      pass runs only when the first one left less than that fraction of |w|
+      (the selective test of the outer iteration, reading K4 of krylov).
 """
 from __future__ import annotations
 
@@ -98,8 +100,10 @@ def cgs2(V, w):
     return h + h2, w
 
 
-def coarse_gmres(A, dinv, b, iterations):
-    """Fixed-count GMRES from x = 0, right-preconditioned by Jacobi (reading M2)."""
+def coarse_gmres(A, dinv, b, iterations, reorth_eta=None):
+    """Fixed-count GMRES from x = 0, right-preconditioned by Jacobi (reading M2);
+    reorth_eta < 1: the selective second Gram-Schmidt pass."""
+    from .krylov import cgs_selective
     n = b.shape[0]
     beta = np.linalg.norm(b)
     if beta == 0.0:
@@ -114,7 +118,10 @@ def coarse_gmres(A, dinv, b, iterations):
     k = 0
     for j in range(iterations):
         w = A @ (dinv * V[:, j])
-        hcol, w = cgs2(V[:, : j + 1], w)
+        if reorth_eta is None or reorth_eta >= 1.0:
+            hcol, w = cgs2(V[:, : j + 1], w)
+        else:
+            hcol, w = cgs_selective(V[:, : j + 1], w, reorth_eta)
         H[: j + 1, j] = hcol
         H[j + 1, j] = np.linalg.norm(w)
         for i in range(j):                         # earlier rotations
@@ -172,11 +179,17 @@ class CycleParams:
     Jacobi-preconditioned GMRES, i.e. Jacobi with the complex weight that
     minimises the residual, Sec. 3.1); pre/post: sweeps per level;
     coarse_iterations: fixed GMRES steps on the coarsest grid;
-    kcycle_iterations: inner FGMRES steps of the K-cycle.
+    kcycle_iterations: inner FGMRES steps of the K-cycle;
+    kcycle_threshold: the inner FGMRES stops early once its residual is at
+    most this fraction of the restricted residual it started from (Sec. 4.2
+    uses 0.1 for the coarse grids: some cycles then make one recursive call
+    instead of two); 0 runs the fixed count;
+    coarse_reorth_eta: None (classical Gram-Schmidt twice in the coarsest
+    GMRES) or the selective second pass's threshold (reading M2).
     """
 
     def __init__(self, cycle="K", relax="mr", pre=None, post=None, weights=None,
-                 coarse_iterations=10, kcycle_iterations=2):
+                 coarse_iterations=10, kcycle_iterations=2, kcycle_threshold=0.0, coarse_reorth_eta=None):
         self.cycle = cycle
         self.relax = relax
         self.pre = list(pre) if pre is not None else [l + 2 for l in range(8)]
@@ -184,6 +197,8 @@ class CycleParams:
         self.weights = list(weights) if weights is not None else [0.5] * 8
         self.coarse_iterations = coarse_iterations
         self.kcycle_iterations = kcycle_iterations
+        self.kcycle_threshold = kcycle_threshold
+        self.coarse_reorth_eta = coarse_reorth_eta
 
 
 def relax_mr(A, dinv, x, b):
@@ -213,18 +228,63 @@ def fixed_fgmres(A, b, precond, iterations):
     return x
 
 
+def kcycle_fgmres(A, b, precond, iterations, threshold):
+    """The inner solve of Alg. Kcycle: flexible GMRES from zero (one Arnoldi
+    cycle, classical Gram-Schmidt applied twice, Givens rotations) that stops
+    after step j when the least-squares residual |g_{j+1}| is at most
+    threshold * |b|, and after `iterations` steps otherwise (Sec. 4.2: the
+    threshold 0.1 lets some cycles skip their second recursive call).
+    Returns (x, steps taken)."""
+    n = b.shape[0]
+    beta = np.linalg.norm(b)
+    if beta == 0.0:
+        return np.zeros(n, dtype=np.complex128), 0
+    V = np.zeros((n, iterations + 1), dtype=np.complex128)
+    Z = np.zeros((n, iterations), dtype=np.complex128)
+    H = np.zeros((iterations + 1, iterations), dtype=np.complex128)
+    cs = np.zeros(iterations)
+    sn = np.zeros(iterations, dtype=np.complex128)
+    g = np.zeros(iterations + 1, dtype=np.complex128)
+    V[:, 0] = b / beta
+    g[0] = beta
+    k = 0
+    for j in range(iterations):
+        Z[:, j] = precond(V[:, j])
+        hcol, w = cgs2(V[:, : j + 1], A @ Z[:, j])
+        H[: j + 1, j] = hcol
+        H[j + 1, j] = np.linalg.norm(w)
+        for i in range(j):
+            a, bb = H[i, j], H[i + 1, j]
+            H[i, j] = cs[i] * a + sn[i] * bb
+            H[i + 1, j] = -np.conj(sn[i]) * a + cs[i] * bb
+        hn = H[j + 1, j].real
+        cs[j], sn[j], H[j, j] = givens(H[j, j], H[j + 1, j])
+        H[j + 1, j] = 0.0
+        g[j + 1] = -np.conj(sn[j]) * g[j]
+        g[j] = cs[j] * g[j]
+        k = j + 1
+        if hn == 0.0 or abs(g[j + 1]) <= threshold * beta:
+            break
+        V[:, j + 1] = w / hn
+    y = back_substitution(H[:k, :k], g[:k])
+    return Z[:, :k] @ y, k
+
+
 def cycle(hier, b, params, level=0):
     """x = B_l^{-1} b from a zero guess with the cycle selected by `params`."""
     lv = hier[level]
     A, dinv = lv["A"], lv["dinv"]
     if level == len(hier) - 1:
-        return coarse_gmres(A, dinv, b, params.coarse_iterations)
+        return coarse_gmres(A, dinv, b, params.coarse_iterations, params.coarse_reorth_eta)
     x = np.zeros_like(b)
     for _ in range(params.pre[level]):
         x = _relax(lv, x, b, params, level)
     bc = lv["P"].T @ (b - A @ x)
     nxt = level + 1
-    if params.cycle == "K" and nxt < len(hier) - 1:
+    if params.cycle == "K" and nxt < len(hier) - 1 and params.kcycle_threshold > 0.0:
+        xc, _ = kcycle_fgmres(hier[nxt]["A"], bc, lambda v: cycle(hier, v, params, nxt), params.kcycle_iterations,
+                              params.kcycle_threshold)
+    elif params.cycle == "K" and nxt < len(hier) - 1:
         xc = fixed_fgmres(hier[nxt]["A"], bc, lambda v: cycle(hier, v, params, nxt), params.kcycle_iterations)
     else:
         xc = cycle(hier, bc, params, nxt)

@@ -29,15 +29,17 @@ TRAVELTIME_STATIC_MAX_SWEEPS = 8192
 
 # The exported entry points, in the order include/adr.h declares them.
 EXPORTS = (
-    "adr_params_default", "adr_operator_create", "adr_operator_update", "adr_batch_create", "adr_batch_update",
+    "adr_params_default", "adr_operator_create", "adr_operator_create_tau", "adr_operator_update", "adr_batch_create",
+    "adr_batch_update",
     "adr_operator_destroy", "adr_operator_info",
     "adr_coefficients", "adr_apply", "adr_level_stencil", "adr_vcycle", "adr_point_source_rhs",
     "adr_solve", "adr_solve_two_stage", "adr_reconstruct", "adr_solve_host", "adr_adjoint_solve", "adr_apply_adjoint", "adr_vcycle_adjoint",
-    "adr_receivers", "adr_kappa_gradient", "adr_traveltime", "adr_traveltime_static", "adr_profile_kernel",
+    "adr_receivers", "adr_kappa_gradient", "adr_traveltime", "adr_traveltime_order", "adr_traveltime_static",
+    "adr_profile_kernel",
     "adr_profile_read",
     "adr_kernel_launches", "adr_last_error", "adr_version",
 )
-PROFILE_CLASSES = {"none": 0, "level1_relax": 1, "fine_relax": 2, "outer_apply": 3, "coarsest": 4}
+PROFILE_CLASSES = {"none": 0, "level1_relax": 1, "fine_relax": 2, "outer_apply": 3, "coarsest": 4, "cycle": 5}
 
 
 class Params(ctypes.Structure):
@@ -63,6 +65,7 @@ class Params(ctypes.Structure):
         ("scheme", ctypes.c_int),
         ("prec_scheme", ctypes.c_int),
         ("rescale", ctypes.c_int),
+        ("kcycle_threshold", ctypes.c_double),
     ]
 
 
@@ -102,6 +105,7 @@ def load():
     sig = {
         "adr_params_default": [ctypes.POINTER(Params)],
         "adr_operator_create": [i, ip, dp, ip, d, vp, vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
+        "adr_operator_create_tau": [i, ip, dp, ip, d, vp, vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
         "adr_operator_update": [vp, ip, d, vp, vp, vp],
         "adr_batch_create": [i, ip, dp, i, ip, dp, vp, vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
         "adr_batch_update": [vp, ip, dp, vp, vp, vp],
@@ -123,6 +127,7 @@ def load():
         "adr_receivers": [vp, i, vp, vp, vp, vp, vp, dp],
         "adr_kappa_gradient": [vp, vp, vp, vp, vp, vp],
         "adr_traveltime": [i, ip, dp, ip, vp, vp, i, vp, ip],
+        "adr_traveltime_order": [i, ip, dp, ip, vp, vp, i, i, vp, ip],
         "adr_traveltime_static": [i, ip, dp, ip, vp, vp, i, vp, ip],
         "adr_profile_kernel": [vp, i],
         "adr_profile_read": [vp, ctypes.POINTER(ctypes.c_longlong), dp],

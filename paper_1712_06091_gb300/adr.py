@@ -60,7 +60,7 @@ def params_dict(p: L.Params) -> dict:
         "precision": ["f64", "f32"][p.precond_precision], "reorth_eta": p.reorth_eta,
         "relax_blocks": p.relax_blocks, "coarse_solver": p.coarse_solver, "tma": p.tma,
         "shift": p.shift, "scheme": _SCHEME_NAMES[p.scheme], "prec_scheme": _SCHEME_NAMES[p.prec_scheme],
-        "rescale": p.rescale,
+        "rescale": p.rescale, "kcycle_threshold": p.kcycle_threshold,
     }
 
 
@@ -79,9 +79,14 @@ def _dev_real(x, N, device):
 
 
 class Operator:
-    """H_2up and its multigrid hierarchy for one point source (adr_operator_create)."""
+    """H_2up and its multigrid hierarchy for one point source (adr_operator_create).
 
-    def __init__(self, n, h, src, omega, kappa, tau1, gamma, params=None, device="cuda", stream=None):
+    tau_kind="factored" (default): `tau1` is the factor of tau = |x - x0| tau1;
+    tau_kind="plain": `tau1` holds tau itself, differentiated by finite
+    differences (adr_operator_create_tau; less accurate next to the source)."""
+
+    def __init__(self, n, h, src, omega, kappa, tau1, gamma, params=None, device="cuda", stream=None,
+                 tau_kind="factored"):
         self._lib = L.load()
         self.dim = len(n)
         self.n = tuple(int(v) for v in n)
@@ -101,9 +106,11 @@ class Operator:
         hh = (ctypes.c_double * 3)(*self.h, *([1.0] * (3 - self.dim)))
         ss = (ctypes.c_int * 3)(*self.src, *([0] * (3 - self.dim)))
         handle = ctypes.c_void_p()
-        L.check(self._lib.adr_operator_create(self.dim, nn, hh, ss, self.omega, _ptr(k), _ptr(t), _ptr(g),
-                                              ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream),
-                                              ctypes.byref(handle)))
+        if tau_kind not in ("factored", "plain"):
+            raise ValueError("tau_kind must be 'factored' or 'plain'")
+        create = self._lib.adr_operator_create_tau if tau_kind == "plain" else self._lib.adr_operator_create
+        L.check(create(self.dim, nn, hh, ss, self.omega, _ptr(k), _ptr(t), _ptr(g), ctypes.byref(self.params),
+                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)))
         self._h = handle
         self.cycle_dtype = torch.complex128 if self.params.precond_precision == L.ADR_F64 else torch.complex64
 
@@ -271,8 +278,10 @@ def kernel_launches() -> int:
     return int(L.load().adr_kernel_launches())
 
 
-def traveltime(n, h, src, kappa, max_sweeps=None, device="cuda", stream=None):
-    """adr_traveltime: device float64 tau1 for slowness `kappa` (first-order factored eikonal)."""
+def traveltime(n, h, src, kappa, max_sweeps=None, device="cuda", stream=None, order=1):
+    """adr_traveltime / adr_traveltime_order: device float64 tau1 for slowness
+    `kappa` (factored eikonal, first- or second-order differences).  Returns
+    (tau1, sweeps)."""
     lib = L.load()
     dim = len(n)
     N = int(np.prod(n))
@@ -284,8 +293,12 @@ def traveltime(n, h, src, kappa, max_sweeps=None, device="cuda", stream=None):
     st = stream if stream is not None else torch.cuda.current_stream(k.device)
     sweeps = ctypes.c_int(0)
     limit = max_sweeps if max_sweeps is not None else 8 * sum(n) + 64
-    L.check(lib.adr_traveltime(dim, nn, hh, ss, _ptr(k), _ptr(tau1), int(limit), ctypes.c_void_p(st.cuda_stream),
-                               ctypes.byref(sweeps)))
+    if order == 1:
+        L.check(lib.adr_traveltime(dim, nn, hh, ss, _ptr(k), _ptr(tau1), int(limit), ctypes.c_void_p(st.cuda_stream),
+                                   ctypes.byref(sweeps)))
+    else:
+        L.check(lib.adr_traveltime_order(dim, nn, hh, ss, _ptr(k), _ptr(tau1), int(order), int(limit),
+                                         ctypes.c_void_p(st.cuda_stream), ctypes.byref(sweeps)))
     return tau1, sweeps.value
 
 

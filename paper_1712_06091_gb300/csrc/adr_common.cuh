@@ -140,6 +140,8 @@ __device__ __forceinline__ void batch_shift_opt(int64_t stride, P&... p) {
 
 // Per-problem partial sums of the last-block reductions.
 constexpr int64_t kPartialStride = 20480;
+// Per-problem stride of the Gram-Schmidt coefficient arrays (KrylovScratch ha / hb).
+constexpr int kMaxArnoldiDots = 66;
 
 __device__ __forceinline__ void unravel(const Dims& g, int64_t j, int& i0, int& i1, int& i2) {
   if (j >= 0 && j <= 0x7fffffffLL) {   // every grid of the solver: two multiply-shift divisions
@@ -288,12 +290,13 @@ template <typename T> inline void set_scheme(FineOp<T>& f, int scheme, double be
 // ---------------------------------------------------------------------------
 struct FineInputs {
   const double* kappa;
-  const double* tau1;
+  const double* tau1;   // tau1 of tau = |x - x0| tau1, or tau itself when plain != 0
   const double* gamma;
   int src[3];
   double omega;
   double h[3];
   double ih[3];   // 1 / h
+  int plain;      // 1: tau1 holds plain tau, differentiated by finite differences
 };
 
 // Fine coefficients in float64 (g, t, rho, tau) and the source row.
@@ -368,6 +371,7 @@ void launch_stencil_apply_tma(const Dims& g, const float2* A, const float2* x, f
 void launch_stencil_residual_dinv_tma(const Dims& g, const float2* A, const float2* b, const float2* x,
                                       const float2* dinv, float2* r, float2* z, int* err, int blocks, int variant,
                                       cudaStream_t st);
+
 template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, int B, cudaStream_t st);
 template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st);
 

@@ -171,6 +171,7 @@ struct Op {
   int grid_coresident = 0;          // co-resident blocks of the persistent coarsest solve (0: not available)
   bool tma_ok = false;              // bulk-copy relaxation apply available (and enabled by params.tma)
   int num_sms = 0;
+  int plain_tau = 0;                // 1: the travel-time input is plain tau (adr_operator_create_tau)
   int* tma_err = nullptr;           // per problem: error words of the bulk-copy kernels
   // instrumentation (adr_profile_kernel): event pairs 2k, 2k+1 of prof_pool
   int prof_class = ADR_PROF_NONE;
@@ -278,7 +279,7 @@ template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
   if (H.L > 1 && per_problem > 0 && Lc.kdim <= kGridMaxK) {
     const int64_t want = (Lc.g.N + 1023) / 1024;
     H.gs.nblk = (int)(want < per_problem ? want : per_problem);
-    H.gs.part = a.take<double2>((size_t)2 * H.gs.nblk * kGridMaxK * B);
+    H.gs.part = a.take<double2>((size_t)2 * H.gs.nblk * (kGridMaxK + 1) * B);
     H.gs.bar = a.take<unsigned>(2 * B);
     H.gs.err = a.take<int>(B);
   }
@@ -387,6 +388,13 @@ static FineOp<double> outer_op(const Op& op) {
   return f;
 }
 
+// Grid of the bulk-copy relaxation applies: one block per SM, or
+// params.relax_blocks when that is smaller (every warp then walks several
+// tiles; a launch shape only).
+static int tma_blocks(const Op& op) {
+  return op.p.relax_blocks > 0 && op.p.relax_blocks < op.num_sms ? op.p.relax_blocks : op.num_sms;
+}
+
 // ---------------------------------------------------------------------------
 // Level operations
 // ---------------------------------------------------------------------------
@@ -399,7 +407,7 @@ template <typename T> struct Cycle {
     if (l == 0) {
       launch_fine_apply<T>(H.lv[0].g, H.prec, x, y, st);
     } else if constexpr (sizeof(T) == 4) {
-      if (op.tma_ok) launch_stencil_apply_tma(H.lv[l].g, H.lv[l].A, x, y, op.tma_err, op.num_sms, op.p.tma, st);
+      if (op.tma_ok) launch_stencil_apply_tma(H.lv[l].g, H.lv[l].A, x, y, op.tma_err, tma_blocks(op), op.p.tma, st);
       else launch_stencil_apply<T>(H.lv[l].g, H.lv[l].A, x, y, st);
     } else {
       launch_stencil_apply<T>(H.lv[l].g, H.lv[l].A, x, y, st);
@@ -418,7 +426,7 @@ template <typename T> struct Cycle {
       launch_fine_residual_dinv<T>(H.lv[0].g, H.prec, b, x, H.lv[0].dinv, r, z, st);
     } else if constexpr (sizeof(T) == 4) {
       if (op.tma_ok)
-        launch_stencil_residual_dinv_tma(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, op.tma_err, op.num_sms,
+        launch_stencil_residual_dinv_tma(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, op.tma_err, tma_blocks(op),
                                          op.p.tma, st);
       else
         launch_stencil_residual_dinv<T>(H.lv[l].g, H.lv[l].A, b, x, H.lv[l].dinv, r, z, st);
@@ -433,7 +441,7 @@ template <typename T> struct Cycle {
     } else if constexpr (sizeof(T) == 4) {
       if (op.tma_ok)
         launch_stencil_mr_apply_tma(H.lv[l].g, H.lv[l].A, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, op.tma_err,
-                                    op.num_sms, op.p.tma, st);
+                                    tma_blocks(op), op.p.tma, st);
       else
         launch_stencil_mr_apply<T>(H.lv[l].g, H.lv[l].A, z, r, w, op.ks.partial, op.ks.ticket, op.ks.alpha, st);
     } else {
@@ -516,31 +524,50 @@ template <typename T> struct Cycle {
     // for the per-step launches (four grid barriers per GMRES step; the whole
     // ADR solve 455 against 409 ms).
     if (grid_ok && form == ADR_COARSE_GRID) {
-      launch_coarse_gmres_grid<T>(L.g, L.A, L.dinv, b, x, L.KV, L.z, k, H.gs, st);
+      launch_coarse_gmres_grid<T>(L.g, L.A, L.dinv, b, x, L.KV, L.z, k, H.gs, op.p.reorth_eta, st);
       return;
     }
+    // Per step: the apply fused with the first Gram-Schmidt pass and the
+    // selective decision (or the two launches), the second pass where the
+    // first cancelled (reading M2, eta = params.reorth_eta; it returns at once
+    // otherwise), and the next basis vector with its Jacobi-scaled direction;
+    // the last step's column also solves the least-squares problem.
     const int B = L.g.B;
     const int64_t ld = n * B;
+    const double eta = op.p.reorth_eta;
     launch_norm_start<T>(b, n, op.ks, &L.ks, st, B);
     launch_scale_dinv<T>(b, L.KV, L.dinv, L.z, op.ks.nrm2, n, st, B);   // V_0 and z = D^{-1} V_0
     for (int j = 0; j < k; ++j) {
-      apply(l, L.z, L.t);
-      launch_cgs2<T>(L.KV, ld, j + 1, L.t, n, op.ks, L.ks, j, st, B);
-      if (j + 1 < k) launch_scale_dinv<T>(L.t, L.KV + (int64_t)(j + 1) * ld, L.dinv, L.z, op.ks.nrm2, n, st, B);
+      const int finish = j + 1 == k ? k : 0;
+      bool fused = false;
+      if constexpr (sizeof(T) == 4) {
+        if (op.tma_ok && k < kMaxArnoldiDots - 2) {
+          launch_stencil_arnoldi_tma(L.g, L.A, L.z, L.t, L.KV, ld, j + 1, op.ks, L.ks, j, finish, eta, op.tma_err,
+                                     tma_blocks(op), op.p.tma, st);
+          fused = true;
+        }
+      }
+      if (!fused) {
+        apply(l, L.z, L.t);
+        launch_cgs_dots_sel<T>(L.KV, ld, j + 1, L.t, n, op.ks, L.ks, j, finish, eta, st, B);
+      }
+      launch_cgs_reorth<T>(L.KV, ld, j + 1, L.t, n, op.ks, L.ks, j, finish, st, B);
+      if (j + 1 < k) launch_cgs_next<T>(L.KV, ld, j + 1, L.t, n, op.ks, L.KV + (int64_t)(j + 1) * ld, L.dinv, L.z, st, B);
     }
-    launch_backsolve(L.ks, k, st, B);
-    launch_combine<T>(L.t, L.KV, ld, k, L.ks, true, n, st, B);
-    launch_cmul_vec<T>(L.dinv, L.t, x, ld, st);
+    launch_combine_dinv<T>(x, L.KV, ld, k, L.ks, L.dinv, n, st, B);
   }
 
-  // Inner flexible GMRES of the K-cycle on level l, from zero, fixed count.
+  // Inner flexible GMRES of the K-cycle on level l, from zero: kdim steps,
+  // or fewer when params.kcycle_threshold > 0 (Alg. Kcycle's early exit:
+  // the instance's convergence target is that fraction of |b|, and the back
+  // substitution stops at the column that met it).
   void kcycle(int l, const C<T>* b, C<T>* x) {
     Level<T>& L = H.lv[l];
     const int64_t n = L.g.N;
     const int k = L.kdim;
     const int B = L.g.B;
     const int64_t ld = n * B;
-    launch_norm_start<T>(b, n, op.ks, &L.ks, st, B);
+    launch_norm_start<T>(b, n, op.ks, &L.ks, st, B, op.p.kcycle_threshold);
     launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st, B);
     for (int j = 0; j < k; ++j) {
       C<T>* zj = L.KZ + (int64_t)j * ld;
@@ -630,6 +657,7 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
     in.kappa = kappa + o; in.tau1 = tau1 + o; in.gamma = gamma + o;
     for (int d = 0; d < 3; ++d) { in.src[d] = dyn.src[d]; in.h[d] = op.h[d]; in.ih[d] = 1.0 / op.h[d]; }
     in.omega = dyn.omega;
+    in.plain = op.plain_tau;
     double* gd[3] = {nullptr, nullptr, nullptr};
     double* td[3] = {nullptr, nullptr, nullptr};
     for (int d = 0; d < op.dim; ++d) { gd[d] = op.gd[d] + o; td[d] = op.td[d] + o; }
@@ -666,8 +694,10 @@ template <typename T> static int run_cycle(Op& op, Hier<T>& H, bool adj = false)
   Level<T>& L0 = H.lv[0];
   op.prof_off = adj;
   if (!op.use_graph) {
+    const int pk = adj ? -1 : prof_begin(op, ADR_PROF_CYCLE, op.st);
     Cycle<T> c{op, H, op.st};
     c.cycle(0, L0.b, L0.x);
+    prof_end(op, pk, op.st);
     op.prof_off = false;
     return check_launch("cycle");
   }
@@ -695,7 +725,9 @@ template <typename T> static int run_cycle(Op& op, Hier<T>& H, bool adj = false)
     count_launches((int)-kernels);  // capture launched nothing; replays are counted below
   }
   op.prof_off = false;
+  const int pk = adj ? -1 : prof_begin(op, ADR_PROF_CYCLE, op.st);
   ADR_CUDA(cudaGraphLaunch(exec, op.st));
+  prof_end(op, pk, op.st);
   count_launches((int)kernels);
   if (!adj) op.prof_graph_fresh = true;
   return ADR_OK;
@@ -756,6 +788,8 @@ static int validate_params(const adr_params_t& p) {
     return fail(ADR_ERR_ARG, "scheme must be ADR_SCHEME_2UP, ADR_SCHEME_1UP or ADR_SCHEME_CEN");
   if (p.prec_scheme < ADR_SCHEME_2UP || p.prec_scheme > ADR_SCHEME_PREC) return fail(ADR_ERR_ARG, "unknown prec_scheme");
   if (p.rescale != 0 && p.rescale != 1) return fail(ADR_ERR_ARG, "rescale must be 0 or 1");
+  if (!(p.kcycle_threshold >= 0.0 && p.kcycle_threshold <= 1e6))
+    return fail(ADR_ERR_ARG, "kcycle_threshold must be in [0, 1e6]");
   for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
     if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
       return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");
@@ -803,7 +837,7 @@ int adr_params_default(adr_params_t* p) {
 
 static int create_impl(int dim, const int* n, const double* h, int B, const int* src, const double* omega,
                        const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
-                       void* stream, adr_op_t* out) {
+                       void* stream, adr_op_t* out, int plain_tau = 0) {
   if (!out) return fail(ADR_ERR_ARG, "out is null");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(ADR_ERR_ARG, "dim must be 2 or 3");
@@ -831,6 +865,7 @@ static int create_impl(int dim, const int* n, const double* h, int B, const int*
   Op& op = h_->op;
   op.dim = dim;
   op.B = B;
+  op.plain_tau = plain_tau;
   op.g0 = make_dims(dim, n);
   op.g0.B = B;
   op.g0.mrcap = p.relax_blocks;
@@ -905,6 +940,14 @@ int adr_operator_create(int dim, const int* n, const double* h, const int* src, 
   return create_impl(dim, n, h, 1, s3, &omega, kappa, tau1, gamma, params, stream, out);
 }
 
+int adr_operator_create_tau(int dim, const int* n, const double* h, const int* src, double omega, const double* kappa,
+                            const double* tau, const double* gamma, const adr_params_t* params, void* stream,
+                            adr_op_t* out) {
+  if (!src) return fail(ADR_ERR_ARG, "null argument");
+  const int s3[3] = {src[0], dim > 1 ? src[1] : 0, dim > 2 ? src[2] : 0};
+  return create_impl(dim, n, h, 1, s3, &omega, kappa, tau, gamma, params, stream, out, 1);
+}
+
 int adr_batch_create(int dim, const int* n, const double* h, int problems, const int* src, const double* omega,
                      const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
                      void* stream, adr_op_t* out) {
@@ -948,7 +991,7 @@ long long adr_kernel_launches(void) { return g_launches.load(std::memory_order_r
 
 int adr_profile_kernel(adr_op_t h, int kernel_class) {
   if (!h) return fail(ADR_ERR_ARG, "null argument");
-  if (kernel_class < ADR_PROF_NONE || kernel_class > ADR_PROF_COARSEST) return fail(ADR_ERR_ARG, "unknown kernel class");
+  if (kernel_class < ADR_PROF_NONE || kernel_class > ADR_PROF_CYCLE) return fail(ADR_ERR_ARG, "unknown kernel class");
   Op& op = h->op;
   ADR_CUDA(cudaStreamSynchronize(op.st));
   if (kernel_class != ADR_PROF_NONE && op.prof_pool.empty()) {

@@ -23,6 +23,7 @@
 #include <cstdint>
 
 #include "coarse_stencil.cuh"
+#include "krylov_dev.cuh"
 #include "reduce.cuh"
 
 namespace adr {
@@ -91,7 +92,26 @@ __device__ __forceinline__ C<T> tile_dot_seq(const C<T>* __restrict__ tb, const 
 }
 
 // Modes of the streamed stencil kernel.
-enum { kTmaMr = 0, kTmaApply = 1, kTmaResid = 2 };
+enum { kTmaMr = 0, kTmaApply = 1, kTmaResid = 2, kTmaArnoldi = 3 };
+
+// What the kTmaArnoldi mode's last block needs for the Arnoldi column.
+struct ArnoldiTail {
+  ArnoldiState st;
+  double2* hb;
+  double2* nrm2;
+  int j, finish;
+  double eta2;
+};
+
+// All lanes receive the warp's sum of v (butterfly; float for a float cycle).
+template <typename T> __device__ __forceinline__ C<T> warp_allsum(C<T> v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
 
 // One pass over the level with the coefficient tiles streamed into shared
 // memory.  WARPS warps per block, each with STAGES tile buffers (1: the other
@@ -100,11 +120,19 @@ enum { kTmaMr = 0, kTmaApply = 1, kTmaResid = 2 };
 //              block writes the minimal-residual weight to alpha
 //   kTmaApply: out = A x
 //   kTmaResid: out = aux - A x, out2 = dinv .* out
+//   kTmaArnoldi: out = A x and the first Gram-Schmidt pass of an Arnoldi step,
+//              ha[i] = sum_e conj(V_i[e]) out[e] for i < kd and ha[kd] =
+//              |out|^2 (kd <= 63): each tile's products are summed over the
+//              warp, lane i (and i - 32) keeps value i's running sum in
+//              float64, the warps add theirs in warp order, the last block
+//              adds the blocks' in block order (deterministic for a given
+//              grid) and takes the selective decision (coarse_select_dev)
 template <int DIM, typename T, bool BT, int WARPS, int STAGES, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, 1)
     k_stencil_tma(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ x, const C<T>* __restrict__ aux,
                   C<T>* __restrict__ out, const C<T>* __restrict__ dinv, C<T>* __restrict__ out2, double2* partial,
-                  unsigned* ticket, double2* alpha, int* err) {
+                  unsigned* ticket, double2* alpha, int* err, const C<T>* __restrict__ V, int64_t ld, int kd,
+                  ArnoldiTail tail) {
   constexpr int W = Split<DIM>::W, NB = Split<DIM>::NB, S = PatternSize<DIM>::value;
   constexpr unsigned kTileBytes = W * 32 * sizeof(C<T>);
   extern __shared__ __align__(128) unsigned char tma_smem[];
@@ -114,9 +142,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   if (BT) {
     batch_shift(stencil_entries(g.N, S), A);
     batch_shift(g.N, x, aux, out);
-    batch_shift_opt(g.N, dinv, out2);
+    batch_shift_opt(g.N, dinv, out2, V);
     batch_shift_opt(kPartialStride, partial);
-    batch_shift_opt(1, ticket, alpha);
+    batch_shift_opt(1, ticket);
+    batch_shift_opt(MODE == kTmaArnoldi ? kMaxArnoldiDots : 1, alpha);
+    if constexpr (MODE == kTmaArnoldi) {
+      tail.hb += (int64_t)blockIdx.y * kMaxArnoldiDots;
+      tail.nrm2 += blockIdx.y;
+    }
     batch_shift(1, err);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -147,6 +180,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   unsigned phase = 0u;   // bit s: parity of stage s's next completion
   bool fail = false;
   C<T> sacc[2] = {czero<T>(), czero<T>()};
+  double2 dacc0 = make_double2(0.0, 0.0), dacc1 = make_double2(0.0, 0.0);   // kTmaArnoldi: bases lane, lane + 32
   int s = 0;
   int64_t t = t0;
   for (; t < ntiles; t += stride, s = STAGES > 1 ? s ^ 1 : 0) {
@@ -156,6 +190,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     phase ^= 1u << s;
     pending &= ~(1u << s);
     const int64_t j = t * 32 + lane;
+    C<T> axw = czero<T>();
     if (j < g.N) {
       int i0, i1, i2;
       unravel(g, j, i0, i1, i2);
@@ -164,7 +199,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       const C<T>* tb = bs + lane;
       const T* tr = reinterpret_cast<const T*>(bs + NB * 32) + lane;
       const C<T> ax = tile_dot_seq<DIM, T>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
-      if constexpr (MODE == kTmaMr) {
+      axw = ax;
+      if constexpr (MODE == kTmaArnoldi) {
+        out[j] = ax;
+      } else if constexpr (MODE == kTmaMr) {
         out[j] = ax;
         sacc[0] = cfma_conj(ax, aux[j], sacc[0]);
         sacc[1] = cfma_conj(ax, ax, sacc[1]);
@@ -174,6 +212,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         const C<T> rj = csub(aux[j], ax);
         out[j] = rj;
         out2[j] = cmul(dinv[j], rj);
+      }
+    }
+    if constexpr (MODE == kTmaArnoldi) {
+      for (int i = 0; i <= kd; ++i) {   // value kd: |A x|^2
+        const C<T> vi = i == kd ? axw : (j < g.N ? V[(int64_t)i * ld + j] : czero<T>());
+        const C<T> p = warp_allsum<T>(cfma_conj(vi, axw, czero<T>()));
+        if (lane == (i & 31)) {
+          double2& d = i < 32 ? dacc0 : dacc1;
+          d.x += (double)p.x;
+          d.y += (double)p.y;
+        }
       }
     }
     __syncwarp();
@@ -203,6 +252,24 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       }
     }
   }
+  if constexpr (MODE == kTmaArnoldi) {
+    const int nv = kd + 1;
+    __shared__ double2 s_dots[kMaxArnoldiDots];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) s_dots[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int w = 0; w < WARPS; ++w) {   // warps in order
+      if (warp == w) {
+        if (lane < nv) s_dots[lane] = cadd(s_dots[lane], dacc0);
+        if (lane + 32 < nv) s_dots[lane + 32] = cadd(s_dots[lane + 32], dacc1);
+      }
+      __syncthreads();
+    }
+    if (last_block_rt(nv, s_dots, partial, ticket, alpha, sh) && threadIdx.x == 0) {
+      if (*(volatile int*)err != 0 || s_fail)
+        for (int i = 0; i < nv; ++i) alpha[i] = make_double2(NAN, NAN);
+      coarse_select_dev(alpha, tail.hb, kd, tail.eta2, arnoldi_at(tail.st, blockIdx.y), tail.j, tail.finish, tail.nrm2);
+    }
+  }
   if constexpr (MODE == kTmaMr) {
     double2 mine[2], tot[2];
     block_sum_t<T, 2>(sacc, sh, mine);
@@ -227,7 +294,7 @@ template <int DIM, int WARPS, int STAGES, int MODE> static bool tma_attr_mode() 
 }
 template <int DIM, int WARPS, int STAGES> static bool tma_attr() {
   return tma_attr_mode<DIM, WARPS, STAGES, kTmaMr>() && tma_attr_mode<DIM, WARPS, STAGES, kTmaApply>() &&
-         tma_attr_mode<DIM, WARPS, STAGES, kTmaResid>();
+         tma_attr_mode<DIM, WARPS, STAGES, kTmaResid>() && tma_attr_mode<DIM, WARPS, STAGES, kTmaArnoldi>();
 }
 
 // Opts the kernels into their dynamic shared memory (call outside capture);
@@ -245,7 +312,8 @@ bool prepare_stencil_tma() {
 template <int DIM, int WARPS, int STAGES, int MODE>
 static void launch_tma(const Dims& g, const float2* A, const float2* x, const float2* aux, float2* out,
                        const float2* dinv, float2* out2, double2* partial, unsigned* ticket, double2* alpha, int* err,
-                       int blocks, cudaStream_t st) {
+                       int blocks, cudaStream_t st, const float2* V = nullptr, int64_t ld = 0, int kd = 0,
+                       ArnoldiTail tail = ArnoldiTail{}) {
   const int64_t ntiles = (g.N + 31) >> 5;
   int64_t nb = (ntiles + WARPS - 1) / WARPS;
   if (nb > blocks) nb = blocks;
@@ -254,19 +322,25 @@ static void launch_tma(const Dims& g, const float2* A, const float2* x, const fl
   constexpr size_t smem = tma_smem_bytes<DIM, WARPS, STAGES>();
   count_launches(1), (g.B > 1 ? k_stencil_tma<DIM, float, true, WARPS, STAGES, MODE>
                               : k_stencil_tma<DIM, float, false, WARPS, STAGES, MODE>)
-                         <<<grid, WARPS * 32, smem, st>>>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err);
+                         <<<grid, WARPS * 32, smem, st>>>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, V,
+                                                          ld, kd, tail);
 }
 
 template <int MODE>
 static void launch_variant(const Dims& g, const float2* A, const float2* x, const float2* aux, float2* out,
                            const float2* dinv, float2* out2, double2* partial, unsigned* ticket, double2* alpha,
-                           int* err, int blocks, int variant, cudaStream_t st) {
+                           int* err, int blocks, int variant, cudaStream_t st, const float2* V = nullptr, int64_t ld = 0,
+                           int kd = 0, ArnoldiTail tail = ArnoldiTail{}) {
   if (variant == 2) {
-    if (g.dim == 2) launch_tma<2, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st);
-    else launch_tma<3, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st);
+    if (g.dim == 2)
+      launch_tma<2, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
+    else
+      launch_tma<3, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
   } else {
-    if (g.dim == 2) launch_tma<2, 16, 1, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st);
-    else launch_tma<3, 16, 1, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st);
+    if (g.dim == 2)
+      launch_tma<2, 16, 1, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
+    else
+      launch_tma<3, 16, 1, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
   }
 }
 
@@ -281,6 +355,13 @@ void launch_stencil_mr_apply_tma(const Dims& g, const float2* A, const float2* z
 void launch_stencil_apply_tma(const Dims& g, const float2* A, const float2* x, float2* y, int* err, int blocks,
                               int variant, cudaStream_t st) {
   launch_variant<kTmaApply>(g, A, x, x, y, nullptr, nullptr, nullptr, nullptr, nullptr, err, blocks, variant, st);
+}
+void launch_stencil_arnoldi_tma(const Dims& g, const float2* A, const float2* z, float2* w, const float2* V, int64_t ld,
+                                int kd, const KrylovScratch& s, const ArnoldiState& st, int j, int finish, double eta,
+                                int* err, int blocks, int variant, cudaStream_t stream) {
+  ArnoldiTail tail{st, s.hb, s.nrm2, j, finish, eta * eta};
+  launch_variant<kTmaArnoldi>(g, A, z, z, w, nullptr, nullptr, s.partial, s.ticket, s.ha, err, blocks, variant, stream, V,
+                              ld, kd, tail);
 }
 void launch_stencil_residual_dinv_tma(const Dims& g, const float2* A, const float2* b, const float2* x,
                                       const float2* dinv, float2* r, float2* z, int* err, int blocks, int variant,

@@ -3,7 +3,8 @@
 // Coefficients: Eq. travel_time_coeff with tau = tau0 tau1, tau0 = |x - x0|
 // (analytic derivatives), d tau1 by central differences (first-order
 // one-sided on the boundary), d^2 tau1 by central differences (second-order
-// one-sided on the boundary).  Rows: Eq. ADR with the Laplacian, the
+// one-sided on the boundary).  A plain tau (no factor tau0) takes the same
+// differences of tau itself.  Rows: Eq. ADR with the Laplacian, the
 // advection of Eqs. londDiff / londUpwindDiff / 1up, the averaging mass of
 // Sec. 2.3 for the Delta-tau term, central advection next to the source
 // (Sec. 2.2), the Neumann condition of Eq. BCADR (n.grad a = i w (n.grad tau) a)
@@ -62,15 +63,15 @@ __global__ void k_coefficients(Dims g, FineInputs in, double* g0, double* g1, do
       d0 = dx[d] * ir;
       dd0 = (1.0 - d0 * d0) * ir;
     }
-    const double gd = __dadd_rn(__dmul_rn(r, d1), __dmul_rn(T1, d0));
-    const double td = T1 * dd0 + 2.0 * d0 * d1 + r * dd1;
+    const double gd = in.plain ? d1 : __dadd_rn(__dmul_rn(r, d1), __dmul_rn(T1, d0));
+    const double td = in.plain ? dd1 : T1 * dd0 + 2.0 * d0 * d1 + r * dd1;
     gout[d][j] = gd;
     tout[d][j] = td;
     grad2 += gd * gd;
   }
   const double k2 = in.kappa[j] * in.kappa[j];
   rho[j] = make_double2(in.omega * in.omega * (k2 - grad2), -in.omega * in.gamma[j] * k2);
-  tau[j] = r * T1;
+  tau[j] = in.plain ? T1 : r * T1;
 }
 
 // Row of M^{-1} H M at the source (one thread).  H has its own Neumann ghost
@@ -79,6 +80,7 @@ __global__ void k_source_row(Dims g, FineInputs in, const double* tau, double2* 
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int k = 0; k < kCross3; ++k) row[k] = make_double2(0.0, 0.0);
   const int64_t js = in.src[0] + g.s1 * in.src[1] + g.s2 * in.src[2];
+  const double ts = tau[js];   // 0 for the factored travel time
   double cre = 0.0;
   for (int d = 0; d < g.dim; ++d) {
     const int64_t stride = d == 0 ? 1 : (d == 1 ? g.s1 : g.s2);
@@ -89,7 +91,7 @@ __global__ void k_source_row(Dims g, FineInputs in, const double* tau, double2* 
       if (k < 0 || k >= g.n[d]) { k = in.src[d] - s; slot_s = -s; }
       const double tn = tau[js + (int64_t)(k - in.src[d]) * stride];
       double sn, cs;
-      sincos(in.omega * (0.0 - tn), &sn, &cs);
+      sincos(in.omega * (ts - tn), &sn, &cs);
       const int slot = 1 + 4 * d + (slot_s < 0 ? 0 : 1);
       row[slot].x += cs * ih2;
       row[slot].y += sn * ih2;

@@ -127,39 +127,6 @@ void launch_set_target(const ArnoldiState& s, const double2* nrm2, double tol, c
 // last-block reductions; see reduce.cuh)
 // ===========================================================================
 
-// Thread 0 holds the block's k sums in blk[0..k); writes them as this block's
-// partials; the last block of the problem to arrive reduces them in block
-// order into out[0..k) and resets the ticket.  Returns true in that block.
-__device__ __forceinline__ bool last_block_rt(int k, const double2* blk, double2* partial, unsigned* ticket, double2* out,
-                                              double2* sh) {
-  __shared__ bool is_last;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < k; ++i) partial[(size_t)blockIdx.x * k + i] = blk[i];
-    __threadfence();
-    const unsigned t = atomicAdd(ticket, 1u);
-    is_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!is_last) return false;
-  __threadfence();
-  // one warp per value: lanes stride over the blocks' partials, then a fixed
-  // shuffle tree (no block-wide step per value)
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < k; i += nw) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (unsigned b = lane; b < gridDim.x; b += 32) {
-      const double2 p = __ldcg(&partial[(size_t)b * k + i]);
-      acc.x += p.x;
-      acc.y += p.y;
-    }
-    acc = warp_sum2(acc);
-    if (lane == 0) out[i] = acc;
-  }
-  if (threadIdx.x == 0) *ticket = 0u;
-  __syncthreads();
-  return true;
-}
-
 // Per-thread sums of conj(V_i[e]) * w[e] for i < k over a grid-stride range,
 // reduced over the block into blk[i].
 template <typename T>
@@ -252,6 +219,121 @@ __global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, i
   }
 }
 
+// Coarsest-grid step with the selective second pass (see coarse_select_dev).
+// First pass (when the apply does not fuse it): ha = V^H w and |w|^2, then
+// the decision in the last block.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgs_dots_sel(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w,
+                                                      int64_t n, KrylovScratch s, ArnoldiState st, int j, int finish,
+                                                      double eta2) {
+  __shared__ double2 sh[32 * 5];
+  __shared__ double2 blk[kMaxKrylov + 2];
+  batch_shift(n, V, w);
+  s = scratch_at(s, blockIdx.y);
+  for (int c = 0; c < k; c += 4) {
+    C<T> acc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = czero<T>();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+      const C<T> we = w[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * ld + e], we, acc[q]);
+      if (c == 0) acc[4] = cfma_conj(we, we, acc[4]);
+    }
+    double2 o[5];
+    block_sum_t<T, 5>(acc, sh, o);
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < 4 && c + q < k; ++q) blk[c + q] = o[q];
+      if (c == 0) blk[k] = o[4];
+    }
+    __syncthreads();
+  }
+  if (last_block_rt(k + 1, blk, s.partial, s.ticket, s.ha, sh) && threadIdx.x == 0)
+    coarse_select_dev(s.ha, s.hb, k, eta2, arnoldi_at(st, blockIdx.y), j, finish, s.nrm2);
+}
+
+// Second pass, only where the first one cancelled (ha[k].y set; the blocks of
+// a problem agree, so the whole problem returns at once otherwise):
+// w -= V ha ; hb = V^H w and |w|^2 ; the column from ha + hb.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgs_reorth(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+                                                    KrylovScratch s, ArnoldiState st, int j, int finish) {
+  s = scratch_at(s, blockIdx.y);
+  if (s.ha[k].y == 0.0) return;
+  __shared__ double2 sh[32 * 5];
+  __shared__ double2 blk[kMaxKrylov + 2];
+  __shared__ C<T> coef[kMaxKrylov + 1];
+  batch_shift(n, V, w);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-s.ha[i].x), (T)(-s.ha[i].y));
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    C<T> acc = w[e];
+    for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
+    w[e] = acc;
+  }
+  for (int c = 0; c < k; c += 4) {
+    C<T> acc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = czero<T>();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+      const C<T> we = w[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c + q < k) acc[q] = cfma_conj(V[(int64_t)(c + q) * ld + e], we, acc[q]);
+      if (c == 0) acc[4] = cfma_conj(we, we, acc[4]);
+    }
+    double2 o[5];
+    block_sum_t<T, 5>(acc, sh, o);
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < 4 && c + q < k; ++q) blk[c + q] = o[q];
+      if (c == 0) blk[k] = o[4];
+    }
+    __syncthreads();
+  }
+  if (last_block_rt(k + 1, blk, s.partial, s.ticket, s.hb, sh) && threadIdx.x == 0)
+    coarse_reorth_dev(s.ha, s.hb, k, arnoldi_at(st, blockIdx.y), j, finish, s.nrm2);
+}
+
+// V_next = (w - V c) / h_{j+1,j} and z = dinv .* V_next (elementwise), c = ha
+// after a single pass (w still A z), hb after the second pass (w already
+// updated by ha).
+template <typename T>
+__global__ void k_cgs_next(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* __restrict__ w, int64_t n,
+                           KrylovScratch s, C<T>* __restrict__ Vnext, const C<T>* __restrict__ dinv, C<T>* __restrict__ z) {
+  __shared__ C<T> coef[kMaxKrylov + 1];
+  __shared__ T s_inv;
+  s = scratch_at(s, blockIdx.y);
+  const double2* c = s.ha[k].y != 0.0 ? s.hb : s.ha;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-c[i].x), (T)(-c[i].y));
+  if (threadIdx.x == 0) s_inv = (T)s.nrm2->y;
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  batch_shift(n, V, w, Vnext, dinv, z);
+  C<T> acc = w[e];
+  for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
+  const C<T> v = cscale(acc, s_inv);
+  Vnext[e] = v;
+  z[e] = cmul(dinv[e], v);
+}
+
+// x = dinv .* sum_{i<k} V_i y_i
+template <typename T>
+__global__ void k_combine_dinv(C<T>* x, const C<T>* __restrict__ V, int64_t ld, int k, ArnoldiState st,
+                               const C<T>* __restrict__ dinv, int64_t n) {
+  __shared__ C<T> coef[kMaxKrylov];
+  const ArnoldiState a = arnoldi_at(st, blockIdx.y);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)a.y[i].x, (T)a.y[i].y);
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  batch_shift(n, x, V, dinv);
+  C<T> acc = czero<T>();
+  for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
+  x[e] = cmul(dinv[e], acc);
+}
+
 // ---------------------------------------------------------------------------
 // Gram-Schmidt with a conditional second pass (selective re-orthogonalisation):
 //   A: ha = V^H w and |w|^2 (kept in ha[k].x)
@@ -336,7 +418,8 @@ __global__ void __launch_bounds__(256) k_sgs_reorth_update(const C<T>* __restric
 
 // |b|^2 and (optionally) the start of an Arnoldi cycle with beta = |b|.
 template <typename T>
-__global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, KrylovScratch s, ArnoldiState st, int start) {
+__global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, KrylovScratch s, ArnoldiState st, int start,
+                                                    double rel_target) {
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[1];
   batch_shift(n, b);
@@ -358,7 +441,12 @@ __global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, Kr
     a.scal[kScalBeta] = beta;
     a.scal[kScalEst] = beta;
     a.iscal[kIScalStop] = beta > 0.0 ? -1 : 0;
-    a.iscal[kIScalConv] = beta <= a.scal[kScalTarget] ? 0 : -1;
+    if (rel_target >= 0.0) {   // a relative target is only tested after a step
+      a.scal[kScalTarget] = rel_target * beta;
+      a.iscal[kIScalConv] = beta > 0.0 ? -1 : 0;
+    } else {
+      a.iscal[kIScalConv] = beta <= a.scal[kScalTarget] ? 0 : -1;
+    }
   }
 }
 
@@ -403,6 +491,28 @@ void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const Kry
   count_launches(1), k_cgs_pass3<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j);
 }
 template <typename T>
+void launch_cgs_dots_sel(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, const KrylovScratch& s,
+                         const ArnoldiState& st, int j, int finish, double eta, cudaStream_t stream, int B) {
+  const dim3 grid(reduction_blocks(n, k + 2), B);
+  count_launches(1), k_cgs_dots_sel<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j, finish, eta * eta);
+}
+template <typename T>
+void launch_cgs_reorth(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
+                       const ArnoldiState& st, int j, int finish, cudaStream_t stream, int B) {
+  const dim3 grid(reduction_blocks(n, k + 2), B);
+  count_launches(1), k_cgs_reorth<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j, finish);
+}
+template <typename T>
+void launch_cgs_next(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, const KrylovScratch& s, C<T>* Vnext,
+                     const C<T>* dinv, C<T>* z, cudaStream_t stream, int B) {
+  count_launches(1), k_cgs_next<T><<<dim3(blocks_for(n, 256), B), 256, 0, stream>>>(V, ld, k, w, n, s, Vnext, dinv, z);
+}
+template <typename T>
+void launch_combine_dinv(C<T>* x, const C<T>* V, int64_t ld, int k, const ArnoldiState& st, const C<T>* dinv, int64_t n,
+                         cudaStream_t stream, int B) {
+  count_launches(1), k_combine_dinv<T><<<dim3(blocks_for(n, 256), B), 256, 0, stream>>>(x, V, ld, k, st, dinv, n);
+}
+template <typename T>
 void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
                           const ArnoldiState& st, int j, double eta, cudaStream_t stream, int B) {
   if (!(eta < 1.0)) {
@@ -416,9 +526,11 @@ void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, 
   count_launches(1), k_sgs_reorth_update<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j);
 }
 template <typename T>
-void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream, int B) {
+void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream, int B,
+                       double rel_target) {
   ArnoldiState dummy{};
-  count_launches(1), k_norm_start<T><<<dim3(reduction_blocks(n, 1), B), 256, 0, stream>>>(b, n, s, st ? *st : dummy, st ? 1 : 0);
+  count_launches(1), k_norm_start<T><<<dim3(reduction_blocks(n, 1), B), 256, 0, stream>>>(b, n, s, st ? *st : dummy,
+                                                                                        st ? 1 : 0, rel_target);
 }
 template <typename T>
 void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n,
@@ -442,7 +554,16 @@ void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, c
                                cudaStream_t, int);                                                                       \
   template void launch_cgs_selective<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&,                 \
                                         const ArnoldiState&, int, double, cudaStream_t, int);                            \
-  template void launch_norm_start<T>(const C<T>*, int64_t, const KrylovScratch&, const ArnoldiState*, cudaStream_t, int); \
+  template void launch_norm_start<T>(const C<T>*, int64_t, const KrylovScratch&, const ArnoldiState*, cudaStream_t, int,  \
+                                     double);                                                                            \
+  template void launch_cgs_dots_sel<T>(const C<T>*, int64_t, int, const C<T>*, int64_t, const KrylovScratch&,           \
+                                       const ArnoldiState&, int, int, double, cudaStream_t, int);                        \
+  template void launch_cgs_reorth<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, \
+                                     int, int, cudaStream_t, int);                                                       \
+  template void launch_cgs_next<T>(const C<T>*, int64_t, int, const C<T>*, int64_t, const KrylovScratch&, C<T>*,         \
+                                   const C<T>*, C<T>*, cudaStream_t, int);                                               \
+  template void launch_combine_dinv<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, const C<T>*, int64_t,      \
+                                       cudaStream_t, int);                                                               \
   template void launch_combine<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, bool, int64_t, cudaStream_t, int); \
   template void launch_mr_update2<T>(C<T>*, const C<T>*, const C<T>*, C<T>*, const C<T>*, const double2*, const C<T>*,    \
                                      C<T>*, bool, int64_t, cudaStream_t, int);

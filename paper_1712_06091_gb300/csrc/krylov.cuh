@@ -15,6 +15,7 @@ namespace adr {
 constexpr int kMaxReduceBlocks = 304;  // 2 x 152 SMs: per-block partials of a reduction
 constexpr int kMaxKrylov = 64;         // largest restart / inner Krylov dimension
 constexpr int kMaxDots = kMaxKrylov + 2;
+static_assert(kMaxDots == kMaxArnoldiDots, "stride of ha / hb per problem");
 static_assert(kPartialStride >= (int64_t)kMaxReduceBlocks * kMaxDots, "partial sums of the Gram-Schmidt passes");
 static_assert(kPartialStride >= (int64_t)kMaxMrBlocks * 2, "partial sums of the relaxation apply");
 
@@ -83,10 +84,42 @@ void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const Kry
 template <typename T>
 void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
                           const ArnoldiState& st, int j, double eta, cudaStream_t stream, int B = 1);
-// |b|^2 into s.nrm2; with st, also starts an Arnoldi cycle with beta = |b|.
+// The Jacobi-preconditioned GMRES step of the coarsest grid with the
+// selective second Gram-Schmidt pass (at most three launches; the column's
+// norm from Pythagoras, see coarse_select_dev / coarse_reorth_dev):
+//   launch_cgs_dots_sel: ha = V^H w, |w|^2, and the decision (when the apply
+//     does not fuse the first pass);
+//   launch_cgs_reorth: the second pass where the first cancelled (returns at
+//     once otherwise);
+//   launch_cgs_next: V_next = (w - V c) / h_{j+1,j}, z = dinv .* V_next.
+// finish > 0 on the last step: the least-squares solve over `finish` columns.
+template <typename T>
+void launch_cgs_dots_sel(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, const KrylovScratch& s,
+                         const ArnoldiState& st, int j, int finish, double eta, cudaStream_t stream, int B = 1);
+template <typename T>
+void launch_cgs_reorth(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
+                       const ArnoldiState& st, int j, int finish, cudaStream_t stream, int B = 1);
+template <typename T>
+void launch_cgs_next(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, const KrylovScratch& s, C<T>* Vnext,
+                     const C<T>* dinv, C<T>* z, cudaStream_t stream, int B = 1);
+// The coarsest step's apply w = A z fused with its first Gram-Schmidt pass
+// (float32 stencil levels, coefficient tiles streamed by bulk copies):
+// ha = V^H w over the kd <= 63 basis vectors V_i = V + i ld, |w|^2, and the
+// selective decision of launch_cgs_dots_sel in the last block (eta: the
+// threshold; finish as there).  NaN coefficients on a failed wait.
+void launch_stencil_arnoldi_tma(const Dims& g, const float2* A, const float2* z, float2* w, const float2* V, int64_t ld,
+                                int kd, const KrylovScratch& s, const ArnoldiState& st, int j, int finish, double eta,
+                                int* err, int blocks, int variant, cudaStream_t stream);
+// x = dinv .* sum_{i<k} V_i y_i (the coarsest solution from its basis).
+template <typename T>
+void launch_combine_dinv(C<T>* x, const C<T>* V, int64_t ld, int k, const ArnoldiState& st, const C<T>* dinv, int64_t n,
+                         cudaStream_t stream, int B = 1);
+// |b|^2 into s.nrm2; with st, also starts an Arnoldi cycle with beta = |b|
+// (rel_target >= 0: the cycle's convergence target becomes rel_target * beta;
+// < 0: the stored target is kept).
 template <typename T>
 void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream,
-                       int B = 1);
+                       int B = 1, double rel_target = -1.0);
 // x = (assign ? 0 : x) + sum_{i<k} Z_i y_i with y from st.
 template <typename T>
 void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n,
@@ -126,7 +159,7 @@ void launch_coarse_gmres_cluster(const Dims& g, const C<T>* A, const C<T>* dinv,
 // (0: no cooperative launch); call it outside capture.
 constexpr int kGridMaxK = 32;
 struct GridScratch {
-  double2* part;   // per problem: 2 x nblk x kGridMaxK partial sums
+  double2* part;   // per problem: 2 x nblk x (kGridMaxK + 1) partial sums
   unsigned* bar;   // per problem: arrival count, generation
   int* err;        // per problem: barrier timeout flag (sticky)
   int nblk;        // blocks per problem
@@ -134,7 +167,7 @@ struct GridScratch {
 int prepare_coarse_grid(int dim, bool f32);
 template <typename T>
 void launch_coarse_gmres_grid(const Dims& g, const C<T>* A, const C<T>* dinv, const C<T>* b, C<T>* x, C<T>* V, C<T>* z,
-                              int k, const GridScratch& gs, cudaStream_t st);
+                              int k, const GridScratch& gs, double eta, cudaStream_t st);
 
 // Whole fixed-count Jacobi-preconditioned GMRES of a small stored-stencil
 // level in one block of 1024 threads per problem (V: basis of stride B n,

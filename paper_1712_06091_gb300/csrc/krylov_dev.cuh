@@ -75,4 +75,42 @@ __device__ __forceinline__ void backsolve_dev(ArnoldiState st, int k) {
   }
 }
 
+// Epilogues of the coarsest-grid Arnoldi step with the selective second
+// Gram-Schmidt pass (one thread, after the totals are in place).
+//
+// After the first pass: ha[0..k) = V^H w, ha[k].x = |w|^2.  The remainder
+// |w - V ha|^2 = |w|^2 - |ha|^2 (V orthonormal) decides: at least eta2 |w|^2
+// keeps the single pass (hb = 0, Arnoldi column j, reciprocal norm in nrm2,
+// ha[k].y = 0, and on the last step the back substitution over `finish`
+// columns); below it, ha[k].y = 1 requests the second pass.
+__device__ __forceinline__ void coarse_select_dev(double2* ha, double2* hb, int k, double eta2, ArnoldiState st, int j,
+                                                  int finish, double2* nrm2) {
+  const double s2 = ha[k].x;
+  double t = s2;
+  for (int i = 0; i < k; ++i) t -= ha[i].x * ha[i].x + ha[i].y * ha[i].y;
+  if (!(t > 0.0)) t = t == t ? 0.0 : t;   // clamp rounding below zero; keep a NaN
+  if (t >= eta2 * s2) {
+    ha[k].y = 0.0;
+    for (int i = 0; i < k; ++i) hb[i] = make_double2(0.0, 0.0);
+    nrm2->x = t;
+    nrm2->y = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    arnoldi_column_dev(st, j, ha, hb, t);
+    if (finish > 0) backsolve_dev(st, finish);
+  } else {
+    ha[k].y = 1.0;
+  }
+}
+// After the second pass: hb[0..k) = V^H w', hb[k].x = |w'|^2 with w' = w - V ha;
+// |w' - V hb|^2 = |w'|^2 - |hb|^2 (hb is at rounding level, no cancellation).
+__device__ __forceinline__ void coarse_reorth_dev(const double2* ha, const double2* hb, int k, ArnoldiState st, int j,
+                                                  int finish, double2* nrm2) {
+  double t = hb[k].x;
+  for (int i = 0; i < k; ++i) t -= hb[i].x * hb[i].x + hb[i].y * hb[i].y;
+  if (!(t > 0.0)) t = t == t ? 0.0 : t;
+  nrm2->x = t;
+  nrm2->y = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+  arnoldi_column_dev(st, j, ha, hb, t);
+  if (finish > 0) backsolve_dev(st, finish);
+}
+
 }  // namespace adr

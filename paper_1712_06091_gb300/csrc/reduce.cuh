@@ -105,4 +105,37 @@ __device__ __forceinline__ bool last_block_total(const double2 (&mine)[K], doubl
   return true;
 }
 
+// Thread 0 holds the block's k sums in blk[0..k); writes them as this block's
+// partials; the last block of the problem to arrive reduces them in block
+// order into out[0..k) and resets the ticket.  Returns true in that block.
+__device__ __forceinline__ bool last_block_rt(int k, const double2* blk, double2* partial, unsigned* ticket, double2* out,
+                                              double2* sh) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < k; ++i) partial[(size_t)blockIdx.x * k + i] = blk[i];
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  // one warp per value: lanes stride over the blocks' partials, then a fixed
+  // shuffle tree (no block-wide step per value)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < k; i += nw) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (unsigned b = lane; b < gridDim.x; b += 32) {
+      const double2 p = __ldcg(&partial[(size_t)b * k + i]);
+      acc.x += p.x;
+      acc.y += p.y;
+    }
+    acc = warp_sum2(acc);
+    if (lane == 0) out[i] = acc;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  __syncthreads();
+  return true;
+}
+
 }  // namespace adr

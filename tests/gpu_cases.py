@@ -19,6 +19,9 @@ CASES = {
     "const3d_17x13x9": lambda: W.constant_medium((17, 13, 9), src=(8, 6, 1)),
     "layered3d_17": lambda: _with_fm(W.layered_3d((17, 17, 9))),
     "corner3d_9x11x13": lambda: W.constant_medium((9, 11, 13), src=(1, 0, 0)),
+    # level 1 = 25 x 25 x 13 = 8125 nodes = 254 tiles of 32: with a grid of one or
+    # two blocks every warp of the streamed relaxation walks 8 to 32 tiles
+    "const3d_49x49x25": lambda: W.constant_medium((49, 49, 25), src=(24, 24, 2), faces=W.faces_except_surface(3)),
 }
 
 
@@ -51,7 +54,9 @@ def oracle_matrix(name, scheme, near=1, beta=0.25, shift=0.0):
 def oracle_cycle_params(p):
     return mg.CycleParams(cycle="VK"[p.cycle], relax=["jacobi", "mr"][p.relax], pre=list(p.pre_sweeps),
                           post=list(p.post_sweeps), weights=list(p.jacobi_weight),
-                          coarse_iterations=p.coarse_iterations, kcycle_iterations=p.kcycle_iterations)
+                          coarse_iterations=p.coarse_iterations, kcycle_iterations=p.kcycle_iterations,
+                          kcycle_threshold=p.kcycle_threshold,
+                          coarse_reorth_eta=p.reorth_eta if p.reorth_eta < 1.0 else None)
 
 
 def make_operator(name, **overrides):

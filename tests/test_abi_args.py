@@ -18,6 +18,7 @@ BAD_PARAMS = [
     ("adjoint", 2, "adjoint"), ("relax_blocks", -1, "relax_blocks"), ("relax_blocks", 10241, "relax_blocks"),
     ("coarse_solver", 99, "coarse_solver"), ("tma", 3, "tma"),
     ("scheme", 3, "scheme"), ("prec_scheme", 9, "prec_scheme"), ("rescale", 2, "rescale"),
+    ("kcycle_threshold", -0.1, "kcycle_threshold"), ("kcycle_threshold", float("nan"), "kcycle_threshold"),
 ]
 
 

@@ -133,6 +133,28 @@ def test_cycle_f64(adrlib, cuda, name, ci):
     assert rel(z, ref) <= 1e-10, (name, ci, rel(z, ref))
 
 
+@pytest.mark.parametrize("name", ["marine2d_65", "layered3d_17", "const3d_17x13x9"])
+@pytest.mark.parametrize("threshold", [0.1, 0.6, 1.0])
+def test_kcycle_early_exit_f64(adrlib, cuda, name, threshold):
+    """Alg. Kcycle with the coarse threshold of Sec. 4.2: an inner FGMRES whose
+    first step already reduces the residual to `threshold` of the restricted
+    residual stops there (1.0 always stops; 0.1 and 0.6 depend on the level).
+    One cycle, then fixed-count FGMRES iterates, against the oracle."""
+    P, params, op = make_operator(name, precision="f64", levels=4, kcycle_threshold=threshold)
+    hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
+    prm = oracle_cycle_params(params)
+    assert prm.kcycle_threshold == threshold and len(hier) >= 3
+    r = W.random_complex(hier[0]["A"].shape[0], 16)
+    z = op.vcycle(_cvec(r)).cpu().numpy()
+    ref = mg.cycle(hier, r, prm)
+    assert rel(z, ref) <= 1e-10, rel(z, ref)
+    q = adr.point_source_rhs(adr.Grid(P.n, P.h), P.src)
+    a, _ = op.solve(tol=0.0, maxit=6, raise_on_fail=False)
+    x, _, _, _ = krylov.fgmres(oracle_matrix(name, "2up"), q, lambda v: mg.cycle(hier, v, prm), tol=0.0, restart=20,
+                               maxit=6, reorth_eta=params.reorth_eta)
+    assert rel(a.cpu().numpy(), x) <= 1e-10, rel(a.cpu().numpy(), x)
+
+
 @pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17"])
 def test_cycle_f32(adrlib, cuda, name):
     P, params, op = make_operator(name, precision="f32")
@@ -276,6 +298,36 @@ def test_bulk_copy_relaxation_matches_plain_loads(adrlib, cuda, name, variant):
     a0, i0 = op_plain.solve(tol=1e-8)
     assert abs(i1["iterations"] - i0["iterations"]) <= 1 and i1["rel_residual"] <= 1e-8
     assert rel(a1.cpu().numpy(), a0.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("variant,blocks", [(1, 1), (1, 2), (2, 1)])
+def test_multi_tile_relaxation_loops_against_oracle(adrlib, cuda, variant, blocks):
+    """The steady state of the streamed relaxation (buffer reuse, mbarrier phase
+    flips, refills after the proxy fence) and of the finest-grid apply's
+    grid-stride loop, against the oracle's cycle: relax_blocks caps both grids,
+    so each warp of the bulk-copy kernel walks several level-1 tiles and each
+    thread of the finest-grid apply walks ~235 nodes.  The float32 cycle must
+    match the oracle's float64 cycle as closely as with the default grid
+    (measured errors are reported by the assertion), and the two grids agree to
+    float32 rounding of the weight's block sums."""
+    name = "const3d_49x49x25"
+    P, params, op = make_operator(name, precision="f32", tma=variant, levels=3, relax_blocks=blocks)
+    n1 = op.info()["levels"][1]["nodes"]
+    warps = 16 if variant == 1 else 8
+    assert (n1 + 31) // 32 >= 7 * warps * blocks          # 254 tiles: 7 to 32 per warp
+    hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
+    r = W.random_complex(P.N, 15)
+    z = op.vcycle(_cvec(r, torch.complex64)).cpu().numpy()
+    ref = mg.cycle(hier, r, oracle_cycle_params(params))
+    _, _, op0 = make_operator(name, precision="f32", tma=variant, levels=3)
+    z0 = op0.vcycle(_cvec(r, torch.complex64)).cpu().numpy()
+    e, e0 = rel(z, ref), rel(z0, ref)
+    assert e <= 2e-4 and e <= 2.0 * e0 + 1e-6, (e, e0)
+    assert rel(z, z0) <= 1e-5, rel(z, z0)
+    # a whole solve with the capped grids reaches the tolerance in the same count
+    a1, i1 = op.solve(tol=1e-8)
+    a0, i0 = op0.solve(tol=1e-8)
+    assert i1["rel_residual"] <= 1e-8 and abs(i1["iterations"] - i0["iterations"]) <= 1
 
 
 # ---------------------------------------------------------------------------

@@ -29,7 +29,7 @@ EXTENT = 2.0
 LAYER_WAVELENGTHS = 3  # thick enough that the layer's reflection stays below the O(h^2) term
 
 
-def _reconstruction_residual(n, phase_sign=-1):
+def _reconstruction_residual(n, phase_sign=-1, plain=False):
     """Relative 5-point Helmholtz residual of the reconstructed ADR solution on
     the nodes farther than 0.1 from the source and outside the layer (2D
     constant medium, fixed omega).  phase_sign = +1 replaces the phase of
@@ -39,13 +39,14 @@ def _reconstruction_residual(n, phase_sign=-1):
     cells = int(round(LAYER_WAVELENGTHS / FREQ / P.h[0]))
     gamma, _ = W.absorbing_layer(P.n, P.h, P.kappa, omega, W.all_faces(2), widths=[cells] * 4)
     g = adr.Grid(P.n, P.h)
-    A = adr.assemble_adr(g, P.src, omega, P.kappa, gamma, P.tau1, "2up")
+    tau1 = adr.PlainTau(adr.travel_time(g, P.src, P.tau1)) if plain else P.tau1
+    A = adr.assemble_adr(g, P.src, omega, P.kappa, gamma, tau1, "2up")
     q = adr.point_source_rhs(g, P.src)
     a = spla.spsolve(A.tocsc(), q)
     if phase_sign < 0:
-        u = adr.reconstruct(g, P.src, omega, P.tau1, a)
+        u = adr.reconstruct(g, P.src, omega, tau1, a)
     else:
-        u = a * np.exp(+1j * omega * adr.travel_time(g, P.src, P.tau1))
+        u = a * np.exp(+1j * omega * adr.travel_time(g, P.src, tau1))
     res = adr.assemble_helmholtz(g, omega, P.kappa, gamma) @ u - q
     X = W.node_coordinates(P.n, P.h)
     r = np.sqrt(sum((x - s * hh) ** 2 for x, s, hh in zip(X, P.src, P.h)))
@@ -193,3 +194,142 @@ def test_kcycle_one_inner_step_is_a_minimal_residual_scaling():
     x2 = x1 + lv["P"] @ (alpha * c)
     x3 = mg.jacobi(lv["A"], lv["dinv"], x2, b, 0.7)
     assert np.linalg.norm(got - x3) <= 1e-12 * np.linalg.norm(x3)
+
+
+# ---------------------------------------------------------------------------
+# Alg. Kcycle's early exit (the 0.1 coarse threshold of Sec. 4.2)
+# ---------------------------------------------------------------------------
+def _level1_system():
+    P0 = W.marine_2d((33, 33))
+    g = adr.Grid(P0.n, P0.h)
+    A = adr.assemble_preconditioner(g, P0.src, P0.omega, P0.kappa, P0.gamma, P0.kappa.copy())
+    hier = mg.build_hierarchy(A, P0.n, 4)
+    prm = mg.CycleParams(cycle="K")
+    b = W.random_complex(hier[1]["A"].shape[0], 9)
+    return hier, prm, b
+
+
+def test_kcycle_inner_solve_threshold_semantics():
+    """The inner FGMRES stops after the first step exactly when that step's
+    residual |b - A x_1| (x_1 = alpha z_0, the one-dimensional least-squares
+    solution along z_0 = B(b/|b|)) is at most threshold |b|; threshold 0 is the
+    fixed-count inner solve."""
+    hier, prm, b = _level1_system()
+    A1 = hier[1]["A"]
+    pc = lambda v: mg.cycle(hier, v, prm, level=1)
+    fixed = mg.fixed_fgmres(A1, b, pc, 2)
+    x0, k0 = mg.kcycle_fgmres(A1, b, pc, 2, 0.0)
+    assert k0 == 2 and np.linalg.norm(x0 - fixed) <= 1e-13 * np.linalg.norm(fixed)
+    z0 = pc(b / np.linalg.norm(b))
+    Az = A1 @ z0
+    alpha = np.vdot(Az, b) / np.vdot(Az, Az).real
+    ratio = np.linalg.norm(b - alpha * Az) / np.linalg.norm(b)
+    assert 0.0 < ratio < 1.0
+    x_hi, k_hi = mg.kcycle_fgmres(A1, b, pc, 2, ratio * (1 + 1e-9))
+    x_lo, k_lo = mg.kcycle_fgmres(A1, b, pc, 2, ratio * (1 - 1e-9))
+    assert k_hi == 1 and k_lo == 2
+    assert np.linalg.norm(x_hi - alpha * z0) <= 1e-12 * np.linalg.norm(alpha * z0)
+    assert np.linalg.norm(x_lo - fixed) <= 1e-13 * np.linalg.norm(fixed)
+
+
+def test_kcycle_threshold_one_is_the_one_step_kcycle():
+    """With a threshold of 1 the first step always satisfies it (a least-squares
+    step never increases the residual), so the cycle is the K-cycle with
+    FGMRES(1), pinned above by the minimal-residual scaling."""
+    P0 = W.marine_2d((33, 33))
+    g = adr.Grid(P0.n, P0.h)
+    A = adr.assemble_preconditioner(g, P0.src, P0.omega, P0.kappa, P0.gamma, P0.kappa.copy())
+    hier = mg.build_hierarchy(A, P0.n, 4)
+    b = W.random_complex(g.N, 10)
+    one = mg.cycle(hier, b, mg.CycleParams(cycle="K", kcycle_iterations=1))
+    thr = mg.cycle(hier, b, mg.CycleParams(cycle="K", kcycle_iterations=2, kcycle_threshold=1.0))
+    assert np.linalg.norm(thr - one) <= 1e-13 * np.linalg.norm(one)
+
+
+# ---------------------------------------------------------------------------
+# Plain travel time (finite-difference coefficients)
+# ---------------------------------------------------------------------------
+def test_plain_tau_coefficients_exact_on_a_plane_wave():
+    """For a linear tau (a plane wave, tau = k.x + c) every difference rule is
+    exact: grad tau = k, d_dd tau = 0 and the reaction is
+    w^2 (kappa^2 - |k|^2) - i w gamma kappa^2 at every node, boundary included."""
+    n, h = (9, 7, 6), (0.1, 0.15, 0.2)
+    g = adr.Grid(n, h)
+    X = W.node_coordinates(n, h)
+    k = (0.3, -0.5, 0.4)
+    tau = 0.7 + sum(kd * x for kd, x in zip(k, X))
+    kappa = W.smooth_random_field(n, seed=3)
+    gamma = np.linspace(0.0, 2.0, g.N)
+    omega = 5.0
+    for j in range(g.N):
+        tv, gr, t, rho = adr.node_coefficients(g, (4, 3, 2), omega, kappa, gamma, adr.PlainTau(tau), j)
+        assert tv == tau[j]
+        assert max(abs(a - b) for a, b in zip(gr, k)) < 1e-12
+        assert max(abs(v) for v in t) < 1e-9
+        k2 = kappa[j] ** 2
+        assert abs(rho - (omega ** 2 * (k2 - sum(v * v for v in k)) - 1j * omega * gamma[j] * k2)) < 1e-9
+
+
+def test_plain_tau_converges_to_factored_coefficients():
+    """tau = kappa r sampled on the grid: away from the source the differences
+    of tau converge to the analytic derivatives of Eq. travel_time_coeff at
+    second order (measured at a fixed physical point); at the source's
+    neighbours they do not (the conical kink), which is why the factored form
+    is the accurate input."""
+    errs = []
+    for n in (17, 33, 65):
+        P = W.constant_medium((n, n), kappa0=0.8)
+        g = adr.Grid(P.n, P.h)
+        tau = adr.travel_time(g, P.src, P.tau1)
+        c = (n - 1) // 2
+        j = g.index((c + (n - 1) // 4, c + (n - 1) // 8))      # physical offset (0.25, 0.125)
+        _, gf, tf, _ = adr.node_coefficients(g, P.src, P.omega, P.kappa, P.gamma, P.tau1, j)
+        _, gp, tp, _ = adr.node_coefficients(g, P.src, P.omega, P.kappa, P.gamma, adr.PlainTau(tau), j)
+        errs.append(max(abs(a - b) for a, b in zip(gf + tf, gp + tp)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 1.8, (errs, rates)
+    # at the diagonal neighbour of the source the central difference spans the
+    # kink: kappa (sqrt 5 - 1) / 2 against the analytic kappa / sqrt 2, at any h
+    for n in (33, 65):
+        P = W.constant_medium((n, n), kappa0=0.8)
+        g = adr.Grid(P.n, P.h)
+        tau = adr.travel_time(g, P.src, P.tau1)
+        j = g.index((P.src[0] + 1, P.src[1] + 1))
+        _, gf, _, _ = adr.node_coefficients(g, P.src, P.omega, P.kappa, P.gamma, P.tau1, j)
+        _, gp, _, _ = adr.node_coefficients(g, P.src, P.omega, P.kappa, P.gamma, adr.PlainTau(tau), j)
+        assert abs(gf[0] - 0.8 / math.sqrt(2)) < 1e-12 and abs(gp[0] - 0.4 * (math.sqrt(5) - 1)) < 1e-12
+
+
+def test_plain_tau_reconstruction_satisfies_helmholtz_to_second_order():
+    """The same Helmholtz-residual pin for the plain-tau coefficients (tau = kappa r
+    given as values): away from the source the finite differences of tau are
+    second-order accurate, so the reconstructed field again solves the 5-point
+    system to O(h^2) (measured 4.7e-2, 7.7e-3, 1.9e-3)."""
+    e = [_reconstruction_residual(n, plain=True) for n in (65, 129, 257)]
+    rates = [math.log2(e[k] / e[k + 1]) for k in range(2)]
+    assert min(rates) > 1.8 and e[-1] < 4e-3, (e, rates)
+
+
+def test_selective_coarse_gmres():
+    """The coarsest GMRES with the selective second Gram-Schmidt pass (reading
+    M2): with as many steps as unknowns it is still a direct solve, and on a
+    coarse Galerkin operator, where the first pass never cancels much, it
+    equals the classical-twice iteration up to rounding."""
+    g, P, A, b = None, None, None, None
+    P0 = W.constant_medium((5, 5), kappa0=1.0, ppw=6)
+    g = adr.Grid(P0.n, P0.h)
+    A = adr.assemble_adr(g, P0.src, P0.omega, P0.kappa, P0.gamma, P0.tau1, "2up")
+    b = W.random_complex(g.N, 4)
+    dinv = 1.0 / A.diagonal()
+    xe = spla.spsolve(A.tocsc(), b)
+    x = mg.coarse_gmres(A, dinv, b, g.N, reorth_eta=0.1)
+    assert np.linalg.norm(x - xe) <= 1e-9 * np.linalg.norm(xe)
+    M = W.marine_2d((65, 65))
+    gm = adr.Grid(M.n, M.h)
+    Ap = adr.assemble_preconditioner(gm, M.src, M.omega, M.kappa, M.gamma, M.kappa.copy())
+    hier = mg.build_hierarchy(Ap, M.n, 3)
+    c = hier[-1]
+    r = W.random_complex(c["A"].shape[0], 5)
+    x2 = mg.coarse_gmres(c["A"], c["dinv"], r, 10)
+    xs = mg.coarse_gmres(c["A"], c["dinv"], r, 10, reorth_eta=0.1)
+    assert np.linalg.norm(xs - x2) <= 1e-13 * np.linalg.norm(x2)
