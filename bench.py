@@ -122,6 +122,8 @@ def parse():
     ap.add_argument("--cycle", default=None)
     ap.add_argument("--sweeps", default=None, help="comma-separated relaxations per level")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-form", default="mixed", choices=["mixed", "per-grid"],
+                    help="batched workload: one operator over problems of all grids (mixed) or one per grid")
     ap.add_argument("--paper-table", action="store_true",
                     help="probe only: the paper's solver configuration on two models at two resolutions each")
     ap.add_argument("--fp-rates", action="store_true",
@@ -779,12 +781,26 @@ def run_batched(args):
         P, probs = batch_problems(n, BATCH_SOURCES)
         probs = [probs[i] for i in mine]
         params = gpu.default_params(precision="f32", levels=BENCH_LEVELS, restart=BENCH_RESTART)
-        tuned = autotune.tune(P.n, P.h, probs, params=params)
-        params.relax_blocks = tuned["relax_blocks"]
+        tuned = autotune.tune(P.n, P.h, probs, params=params) if args.batch_form == "per-grid" else None
+        if tuned:
+            params.relax_blocks = tuned["relax_blocks"]
         groups.append((P, probs, params, tuned))
-    solvers = [autotune.PackedSolver(P.n, P.h, t["packing"], params=prm) for P, _, prm, t in groups]
+    if args.batch_form == "mixed":
+        # every launch of a step covers problems of all three grids (adr_batch_create_grids)
+        mixed = [((P.n, P.h), probs) for P, probs, _, _ in groups]
+        params = gpu.default_params(precision="f32", levels=BENCH_LEVELS, restart=BENCH_RESTART)
+        mtuned = autotune.tune_grids(mixed, params=params)
+        params.relax_blocks = mtuned["relax_blocks"]
+        msolver = autotune.GridsPackedSolver(mtuned["packing"], params=params)
+        solvers = [msolver]
+    else:
+        solvers = [autotune.PackedSolver(P.n, P.h, t["packing"], params=prm) for P, _, prm, t in groups]
 
     def step():
+        if args.batch_form == "mixed":
+            _, infos = msolver.solve(mixed, tol=args.tol, maxit=args.maxit)
+            assert max(i["rel_residual"] for grp in infos for i in grp) <= args.tol
+            return [[i["iterations"] for i in grp] for grp in infos]
         its = []
         for (P, probs, _, _), sol in zip(groups, solvers):
             _, infos = sol.solve(probs, tol=args.tol, maxit=args.maxit)
@@ -843,8 +859,13 @@ def run_batched(args):
         "dtype": "f32 cycle + f64 Krylov", "data": "synthetic (layered model resampled per grid; tau1 from the library's "
                                                  "travel-time kernel)",
         "config": {"workload": "batched3d_3x32", "grids": list(BATCH_GRIDS), "sources_per_grid": BATCH_SOURCES,
-                   "tol": args.tol, "tuned": [{"grid": P.n, "packing": t["packing"], "relax_blocks": t["relax_blocks"],
-                                              "table": t["table"]} for P, _, _, t in groups],
+                   "batch_form": args.batch_form,
+                   "tuned": ([{"grids": "all", "packing_per_grid": mtuned["packing"],
+                               "relax_blocks": mtuned["relax_blocks"], "table": mtuned["table"]}]
+                             if args.batch_form == "mixed" else
+                             [{"grid": P.n, "packing": t["packing"], "relax_blocks": t["relax_blocks"],
+                               "table": t["table"]} for P, _, _, t in groups]),
+                   "tol": args.tol,
                    "iterations_per_grid": [[min(i), max(i)] for i in its],
                    "l2": "no flush: batch working sets exceed L2"},
         "plain_f64": {"value": plain_value, "unit": UNIT, "iterations_per_grid": plain_its,

@@ -147,6 +147,12 @@ typedef struct adr_params {
                                           and its later steps do not enter the result.
                                           0 (default): the fixed kcycle_iterations steps.
                                           0..1e6 */
+  int outer_df;                        /* 1 (default): with a float32 cycle (not
+                                          rescaled) the outer iteration's A z_j reads
+                                          z_j as float32 values and sums exact products
+                                          in double-float arithmetic (float32 pipe;
+                                          about 2^-46 of the row's largest term); 0: the
+                                          float64 apply.  Residuals stay float64 */
 } adr_params_t;
 
 #define ADR_COARSE_AUTO 0      /* cluster up to 32768 nodes, else one block up to 8192, else kernels */
@@ -242,6 +248,29 @@ int adr_operator_update(adr_op_t op, const int* src, double omega, const double*
 int adr_batch_create(int dim, const int* n, const double* h, int problems, const int* src, const double* omega,
                      const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
                      void* stream, adr_op_t* out);
+
+/* A batch whose problems have grids of their own (sizes and spacings), the
+ * paper has no batched form: the many-source, many-frequency setting where
+ * each frequency gets the coarsest grid that keeps its points per wavelength.
+ * Every kernel launch of the cycle and of the Krylov iteration still covers
+ * all problems (grid.y = problem; a problem smaller than the largest leaves
+ * the surplus blocks idle), the problems' FGMRES iterations advance in
+ * lockstep as in adr_batch_create, and each problem's arithmetic is that of
+ * its own single-problem operator up to the rounding order of reductions.
+ *   n: int[3 * problems], nodes per axis per problem (unused axes 1);
+ *   h: double[3 * problems], spacing per axis per problem;
+ *   src: int[3 * problems]; omega: double[problems] (host arrays);
+ *   kappa, tau1, gamma: device float64 arrays of sum_p N_p entries, problem
+ *   p's N_p = n0 n1 n2 entries after the earlier problems' (the same layout
+ *   for every vector of the other entry points and for adr_coefficients,
+ *   whose per-problem blocks are (2 dim + 3) N_p).
+ * Every problem's grid must allow the same number of levels up to
+ * params.levels (the hierarchy stops where any problem stops).  The
+ * persistent cooperative coarsest form is not used for these batches.
+ * Errors as adr_batch_create. */
+int adr_batch_create_grids(int dim, int problems, const int* n, const double* h, const int* src, const double* omega,
+                           const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
+                           void* stream, adr_op_t* out);
 
 /* adr_operator_update for a batch (arrays as in adr_batch_create); the
  * single-problem adr_operator_update refuses batches (ADR_ERR_STATE). */

@@ -30,7 +30,7 @@ TRAVELTIME_STATIC_MAX_SWEEPS = 8192
 # The exported entry points, in the order include/adr.h declares them.
 EXPORTS = (
     "adr_params_default", "adr_operator_create", "adr_operator_create_tau", "adr_operator_update", "adr_batch_create",
-    "adr_batch_update",
+    "adr_batch_create_grids", "adr_batch_update",
     "adr_operator_destroy", "adr_operator_info",
     "adr_coefficients", "adr_apply", "adr_level_stencil", "adr_vcycle", "adr_point_source_rhs",
     "adr_solve", "adr_solve_two_stage", "adr_reconstruct", "adr_solve_host", "adr_adjoint_solve", "adr_apply_adjoint", "adr_vcycle_adjoint",
@@ -66,6 +66,7 @@ class Params(ctypes.Structure):
         ("prec_scheme", ctypes.c_int),
         ("rescale", ctypes.c_int),
         ("kcycle_threshold", ctypes.c_double),
+        ("outer_df", ctypes.c_int),
     ]
 
 
@@ -108,6 +109,7 @@ def load():
         "adr_operator_create_tau": [i, ip, dp, ip, d, vp, vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
         "adr_operator_update": [vp, ip, d, vp, vp, vp],
         "adr_batch_create": [i, ip, dp, i, ip, dp, vp, vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
+        "adr_batch_create_grids": [i, i, ip, dp, ip, dp, vp, vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
         "adr_batch_update": [vp, ip, dp, vp, vp, vp],
         "adr_operator_destroy": [vp],
         "adr_operator_info": [vp, ctypes.POINTER(OpInfo)],

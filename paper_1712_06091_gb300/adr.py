@@ -60,7 +60,7 @@ def params_dict(p: L.Params) -> dict:
         "precision": ["f64", "f32"][p.precond_precision], "reorth_eta": p.reorth_eta,
         "relax_blocks": p.relax_blocks, "coarse_solver": p.coarse_solver, "tma": p.tma,
         "shift": p.shift, "scheme": _SCHEME_NAMES[p.scheme], "prec_scheme": _SCHEME_NAMES[p.prec_scheme],
-        "rescale": p.rescale, "kcycle_threshold": p.kcycle_threshold,
+        "rescale": p.rescale, "kcycle_threshold": p.kcycle_threshold, "outer_df": p.outer_df,
     }
 
 
@@ -518,3 +518,68 @@ class BatchOperator(Operator):
         L.check(rc, () if raise_on_fail else (L.ADR_ERR_NOT_CONVERGED,))
         return a, [{"iterations": i.iterations, "restarts": i.restarts, "rel_residual": i.rel_residual,
                     "rel_estimate": i.rel_estimate, "status": i.status} for i in infos]
+
+
+class GridsBatchOperator(BatchOperator):
+    """adr_batch_create_grids: point-source problems with grids (and spacings)
+    of their own, run together (each launch covers every problem).
+
+    grids: one (n, h) pair per problem.  Inputs and vectors are the problems'
+    node arrays concatenated in order (problem p's N_p entries after the
+    earlier problems'); `offsets[p]` is where problem p starts and `N` the
+    total length.  split(v) returns the per-problem views of such a vector.
+    """
+
+    def __init__(self, grids, srcs, omegas, kappa, tau1, gamma, params=None, device="cuda", stream=None):
+        self._lib = L.load()
+        if not grids:
+            raise ValueError("at least one problem")
+        self.dim = len(grids[0][0])
+        self.grids = [(tuple(int(v) for v in n), tuple(float(v) for v in h)) for n, h in grids]
+        if any(len(n) != self.dim or len(h) != self.dim for n, h in self.grids):
+            raise ValueError("every grid needs dim node counts and spacings")
+        self.problems = len(self.grids)
+        if len(srcs) != self.problems or len(omegas) != self.problems:
+            raise ValueError("one source and one frequency per grid")
+        self.n, self.h = self.grids[0]
+        self.srcs = [tuple(int(v) for v in s) for s in srcs]
+        self.omegas = [float(w) for w in omegas]
+        sizes = [int(np.prod(n)) for n, _ in self.grids]
+        self.offsets = [int(v) for v in np.concatenate([[0], np.cumsum(sizes)[:-1]])]
+        self.sizes = sizes
+        self.nodes = max(sizes)
+        self.N = int(sum(sizes))
+        self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.params = params if params is not None else default_params()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        k = _dev_real(kappa, self.N, self.device)
+        t = _dev_real(tau1, self.N, self.device)
+        g = _dev_real(gamma, self.N, self.device)
+        nn = (ctypes.c_int * (3 * self.problems))()
+        hh = (ctypes.c_double * (3 * self.problems))()
+        for p, (n, h) in enumerate(self.grids):
+            for d in range(3):
+                nn[3 * p + d] = n[d] if d < self.dim else 1
+                hh[3 * p + d] = h[d] if d < self.dim else 1.0
+        ss, ww = self._src_omega(self.srcs, self.omegas)
+        handle = ctypes.c_void_p()
+        L.check(self._lib.adr_batch_create_grids(self.dim, self.problems, nn, hh, ss, ww, _ptr(k), _ptr(t), _ptr(g),
+                                                 ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream),
+                                                 ctypes.byref(handle)))
+        self._h = handle
+        self.cycle_dtype = torch.complex128 if self.params.precond_precision == L.ADR_F64 else torch.complex64
+        self.src = self.srcs[0]
+        self.omega = self.omegas[0]
+
+    def split(self, v):
+        """Per-problem views of a concatenated batch vector."""
+        v = v.reshape(-1)
+        return [v[o:o + s] for o, s in zip(self.offsets, self.sizes)]
+
+    def coefficients(self) -> torch.Tensor:
+        """(2 dim + 3) N_p values per problem, concatenated (see adr_coefficients)."""
+        out = torch.empty((2 * self.dim + 3) * self.N, dtype=torch.float64, device=self.device)
+        L.check(self._lib.adr_coefficients(self._h, _ptr(out)))
+        return out

@@ -119,3 +119,110 @@ class PackedSolver:
         for op in self._ops.values():
             op.close()
         self._ops.clear()
+
+
+# ---------------------------------------------------------------------------
+# Problems on grids of several sizes (GridsBatchOperator): one operator covers
+# `packing` problems of every grid, so each launch of a step runs problems of
+# all sizes together.
+# ---------------------------------------------------------------------------
+def _mixed_chunk(groups, start, packing):
+    """Problems start .. start + packing of every group, as (grids, problems)."""
+    grids, probs = [], []
+    for (n, h), problems in groups:
+        for p in problems[start:start + packing]:
+            grids.append((n, h))
+            probs.append(p)
+    return grids, probs
+
+
+def _cat(problems, k, device):
+    return torch.cat([torch.as_tensor(p[k], dtype=torch.float64, device=device).reshape(-1) for p in problems])
+
+
+def probe_grids(groups, packing, params, iterations=3, repeats=2, device="cuda"):
+    """Device ms per problem-iteration of one mixed-grid operator holding
+    `packing` problems of every group ((n, h), problems)."""
+    grids, probs = _mixed_chunk(groups, 0, packing)
+    op = gpu.GridsBatchOperator(grids, [p[0] for p in probs], [p[1] for p in probs], _cat(probs, 2, device),
+                                _cat(probs, 3, device), _cat(probs, 4, device), params=params, device=device)
+    try:
+        stream = op.stream
+        op.solve(tol=0.0, maxit=iterations, raise_on_fail=False)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(repeats):
+            op.solve(tol=0.0, maxit=iterations, raise_on_fail=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / (repeats * iterations * len(probs))
+    finally:
+        op.close()
+
+
+def tune_grids(groups, params=None, packings=PACKINGS, relax_blocks=RELAX_BLOCKS, iterations=3, device="cuda"):
+    """Best (packing, relax_blocks) for mixed-grid operators over `groups`
+    ((n, h), problems) and the measured table; as tune(), the relaxation grid
+    first at the largest packing, then the packing."""
+    count = min(len(p) for _, p in groups)
+    packings = [b for b in packings if b <= count] or [count]
+    table = []
+    b0 = max(packings)
+    best_rb, best_t = None, float("inf")
+    for rb in relax_blocks:
+        t = probe_grids(groups, b0, _params(params, relax_blocks=rb), iterations, device=device)
+        table.append({"packing": b0, "relax_blocks": rb, "ms_per_problem_iteration": t})
+        if t < best_t:
+            best_rb, best_t = rb, t
+    best_b = b0
+    for b in packings:
+        if b == b0:
+            continue
+        t = probe_grids(groups, b, _params(params, relax_blocks=best_rb), iterations, device=device)
+        table.append({"packing": b, "relax_blocks": best_rb, "ms_per_problem_iteration": t})
+        if t < best_t:
+            best_b, best_t = b, t
+    return {"packing": best_b, "relax_blocks": best_rb, "ms_per_problem_iteration": best_t, "table": table}
+
+
+class GridsPackedSolver:
+    """Solves problems on several grids with mixed-grid operators of `packing`
+    problems per grid, reusing one operator per chunk shape (adr_batch_update
+    between chunks)."""
+
+    def __init__(self, packing, params=None, device="cuda"):
+        self.packing = int(packing)
+        self.params = params if params is not None else gpu.default_params()
+        self.device = torch.device(device)
+        self._ops = {}
+
+    def solve(self, groups, tol=1e-8, maxit=500, reconstruct=True):
+        """(per group: list of wavefields (or amplitudes) per problem, per group: list of info dicts)."""
+        count = max(len(p) for _, p in groups)
+        outs = [[] for _ in groups]
+        infos = [[] for _ in groups]
+        for s in range(0, count, self.packing):
+            grids, probs = _mixed_chunk(groups, s, self.packing)
+            key = tuple(grids)
+            args = ([p[0] for p in probs], [p[1] for p in probs], _cat(probs, 2, self.device),
+                    _cat(probs, 3, self.device), _cat(probs, 4, self.device))
+            op = self._ops.get(key)
+            if op is None:
+                op = gpu.GridsBatchOperator(grids, *args, params=self.params, device=self.device)
+                self._ops[key] = op
+            else:
+                op.update(*args)
+            a, inf = op.solve(tol=tol, maxit=maxit)
+            v = op.split(op.reconstruct(a) if reconstruct else a)
+            k = 0
+            for gi, ((n, h), problems) in enumerate(groups):
+                for _ in problems[s:s + self.packing]:
+                    outs[gi].append(v[k])
+                    infos[gi].append(inf[k])
+                    k += 1
+        return outs, infos
+
+    def close(self):
+        for op in self._ops.values():
+            op.close()
+        self._ops.clear()

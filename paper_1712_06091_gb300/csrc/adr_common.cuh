@@ -70,16 +70,82 @@ template <typename Dst, typename Src> __host__ __device__ __forceinline__ Dst cc
 // ---------------------------------------------------------------------------
 // Grid descriptor
 // ---------------------------------------------------------------------------
+// One problem's grid inside a batch whose problems have grids (and spacings)
+// of their own: its shape, the index-division constants, where its entries
+// start in the batch's node arrays and in its stored stencils, its spacing.
+struct ProblemDims {
+  int n[3];
+  int64_t N, s1, s2;
+  unsigned mul0, mul1;
+  int shr0, shr1;
+  int64_t off;     // first node entry: the earlier problems' N summed
+  int64_t soff;    // first stored-stencil entry: the earlier problems' stencil entries summed
+  double h[3];
+};
+
 struct Dims {
   int dim;
   int n[3];
-  int64_t N;
+  int64_t N;       // nodes of one problem; for per-problem grids (pd) the largest, which sizes launches
   int64_t s1, s2;  // strides of axes 1 and 2
-  int B;           // problems sharing this grid in a batched launch (grid.y)
+  int B;           // problems in a batched launch (grid.y)
   int mrcap;       // largest grid of the relaxation applies (0: kMaxMrBlocks)
   unsigned mul0, mul1;  // division by n[0], n[1] as a multiply and a shift (fast_div_params)
   int shr0, shr1;
+  const ProblemDims* pd;  // device table of per-problem grids; nullptr: every problem has this grid
+  const int* skip;        // per problem: nonzero = frozen, its blocks return at once (nullptr: none)
+  int64_t total;          // node entries of one vector over all problems
+  int64_t off, soff;      // after resolve(): the block's problem's first node / stencil entry
 };
+
+// Entries of a stored Galerkin stencil for N nodes (32-node tiles of W words
+// of the element type: 27 complex + 54 imaginary-only reals in 3D, 9 + 12 in 2D).
+__host__ __device__ __forceinline__ int64_t stencil_words(int dim) { return dim == 2 ? 15 : 54; }
+__host__ __device__ __forceinline__ int64_t stencil_entries_dim(int64_t N, int dim) {
+  return ((N + 31) >> 5) * 32 * stencil_words(dim);
+}
+
+// The grid of the calling block's problem (blockIdx.y): its shape and the
+// first entries of its slices of the batch's arrays.  Every kernel calls it
+// before using g and returns at once when it answers true: the problem is
+// frozen (a batch member that already met its tolerance), so the whole
+// block, and every block of that problem, skips the launch.
+__device__ __forceinline__ bool resolve(Dims& g) {
+  const int p = blockIdx.y;
+  if (g.skip && g.skip[p]) return true;
+  if (g.pd == nullptr) {
+    g.off = (int64_t)p * g.N;
+    g.soff = (int64_t)p * stencil_entries_dim(g.N, g.dim);
+    return false;
+  }
+  const ProblemDims& q = g.pd[p];
+  g.n[0] = q.n[0]; g.n[1] = q.n[1]; g.n[2] = q.n[2];
+  g.N = q.N; g.s1 = q.s1; g.s2 = q.s2;
+  g.mul0 = q.mul0; g.mul1 = q.mul1; g.shr0 = q.shr0; g.shr1 = q.shr1;
+  g.off = q.off;
+  g.soff = q.soff;
+  return false;
+}
+// resolve() for a batch known to share one grid (no table): only the skip
+// test and the offsets, so the shape stays in the launch parameters.
+__device__ __forceinline__ bool resolve_uniform(Dims& g) {
+  const int p = blockIdx.y;
+  if (g.skip && g.skip[p]) return true;
+  g.off = (int64_t)p * g.N;
+  g.soff = (int64_t)p * stencil_entries_dim(g.N, g.dim);
+  return false;
+}
+
+// Pointers moved to the block's problem's slice (node arrays, node arrays of
+// `k` entries per node, stored stencils); the _opt forms leave nullptr alone.
+template <typename... P> __device__ __forceinline__ void shift_nodes(const Dims& g, P&... p) { ((p += g.off), ...); }
+template <typename... P> __device__ __forceinline__ void shift_nodes_opt(const Dims& g, P&... p) {
+  ((p = (p != nullptr) ? p + g.off : p), ...);
+}
+template <typename... P> __device__ __forceinline__ void shift_scaled(const Dims& g, int64_t k, P&... p) {
+  ((p += k * g.off), ...);
+}
+template <typename... P> __device__ __forceinline__ void shift_stencil(const Dims& g, P&... p) { ((p += g.soff), ...); }
 
 // Division of a 31-bit unsigned x by an invariant d >= 1 without a divide
 // instruction (Granlund and Montgomery, "Division by invariant integers using
@@ -121,6 +187,10 @@ inline Dims make_dims(int dim, const int* n) {
   g.mrcap = 0;
   fast_div_params((unsigned)g.n[0], g.mul0, g.shr0);
   fast_div_params((unsigned)g.n[1], g.mul1, g.shr1);
+  g.pd = nullptr;
+  g.skip = nullptr;
+  g.total = g.N;
+  g.off = g.soff = 0;
   return g;
 }
 
@@ -276,6 +346,29 @@ template <typename T> struct FineOp {
 };
 
 
+// The block's problem's grid, and for per-problem grids the spacing
+// constants of f (computed as the host computes them for a single grid).
+template <typename T> __device__ __forceinline__ void problem_spacing(const Dims& g, FineOp<T>& f);
+template <typename T> __device__ __forceinline__ bool resolve(Dims& g, FineOp<T>& f) {
+  if (resolve(g)) return true;
+  if (g.pd != nullptr) problem_spacing(g, f);
+  return false;
+}
+// The spacing constants of the block's problem (per-problem grids).
+template <typename T> __device__ __forceinline__ void problem_spacing(const Dims& g, FineOp<T>& f) {
+  const ProblemDims& q = g.pd[blockIdx.y];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {   // compile-time indices keep f out of local memory
+    if (d < g.dim) {
+      const double h = q.h[d];
+      f.h[d] = (T)h;
+      f.ih2[d] = (T)(1.0 / (h * h));
+      f.ih[d] = (T)(1.0 / h);
+      f.hih[d] = (T)(0.5 / h);
+    }
+  }
+}
+
 // Scheme -> upwind weights.
 template <typename T> inline void set_scheme(FineOp<T>& f, int scheme, double beta) {
   f.central = 0;
@@ -305,7 +398,7 @@ void launch_coefficients(const Dims& g, const FineInputs& in, double* const gd[3
 // float64 -> float32 copy of n reals.
 void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
 // diag(M) = exp(-i w tau) per node of every problem (Eq. matrix_rescaling).
-void launch_phase(const double* tau, const FineDyn* dyn, double2* phase, int64_t N, int B, cudaStream_t st);
+void launch_phase(const Dims& g, const double* tau, const FineDyn* dyn, double2* phase, cudaStream_t st);
 // Stored cross rows A -> M A M^{-1}: entry (i, i + o) times m_i conj(m_{i+o}).
 template <typename T> void launch_rows_rescale(const Dims& g, C<T>* rows, const double2* phase, cudaStream_t st);
 // dst = (Td)(src * m) or, with conj, (Td)(src * conj(m)), m = phase (whole arrays of n entries).
@@ -372,7 +465,7 @@ void launch_stencil_residual_dinv_tma(const Dims& g, const float2* A, const floa
                                       const float2* dinv, float2* r, float2* z, int* err, int blocks, int variant,
                                       cudaStream_t st);
 
-template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, int B, cudaStream_t st);
+template <typename T> void launch_stencil_export(const Dims& g, const C<T>* A, C<T>* out, int S, cudaStream_t st);
 template <typename T> void launch_galerkin_stored(const Dims& gf, const Dims& gc, const C<T>* Af, C<T>* Ac, C<T>* dinv, cudaStream_t st);
 
 // Transfers.
@@ -392,12 +485,20 @@ void count_launches(int n);
 // Records msg as the calling thread's adr_last_error text; returns code.
 int set_last_error(int code, const char* msg);
 
+// The outer float64 operator on a vector of float32 values in double-float
+// arithmetic (see fine.cu): pk2 are the packed rows split into float32
+// (hi, lo) pairs by launch_split_df (n reals).
+struct DfLaplacian { float hi[3], lo[3]; };
+void launch_split_df(const double* src, float2* dst, int64_t n, cudaStream_t st);
+void launch_packed_apply_df(const Dims& g, const FineOp<double>& f, const float2* pk2, const float2* x, double2* y,
+                            cudaStream_t st);
+
 // Vector kernels.
 template <typename T> void launch_cmul_vec(const C<T>* a, const C<T>* b, C<T>* out, int64_t n, cudaStream_t st);  // out = a .* b
 template <typename Ts, typename Td> void launch_ccast(const C<Ts>* src, C<Td>* dst, int64_t n, cudaStream_t st);
 
 // q = value at each problem's source node (dyn[p].src_index), zero elsewhere.
-void launch_rhs_point(double2* q, int64_t N, const FineDyn* dyn, double value, int B, cudaStream_t st);
+void launch_rhs_point(const Dims& g, double2* q, const FineDyn* dyn, double value, cudaStream_t st);
 // Receiver residuals res = R u - d, rhs += M^H R^T res, out = (sum |res|^2, bad indices).
 void launch_receivers(int64_t N, int nrec, const int64_t* rec, const double2* d, const double2* u, const double* tau,
                       double omega, double2* res, double2* rhs, double2* out, cudaStream_t st);
@@ -405,8 +506,7 @@ void launch_receivers(int64_t N, int nrec, const int64_t* rec, const double2* d,
 void launch_kappa_gradient(int64_t N, double omega, const double* kappa, const double* gamma, const double2* a,
                            const double2* lambda, double* grad, cudaStream_t st);
 // u = a exp(-i w tau) with each problem's w from dyn.
-void launch_reconstruct(const double2* a, const double* tau, const FineDyn* dyn, double2* u, int64_t N, int B,
-                        cudaStream_t st);
+void launch_reconstruct(const Dims& g, const double2* a, const double* tau, const FineDyn* dyn, double2* u, cudaStream_t st);
 void launch_pack_coefficients(const Dims& g, const double* const gd[3], const double* const td[3], const double2* rho,
                               const double* tau, double* out, cudaStream_t st);
 

@@ -113,8 +113,24 @@ template <typename T> struct Hier {
 
 struct Op {
   int dim = 0;
-  int B = 1;                        // problems of the batch (same grid; own source, frequency, medium)
-  Dims g0{};
+  int B = 1;                        // problems of the batch (own source, frequency, medium; own grid if hetero)
+  Dims g0{};                        // the finest level (largest grid, totals over the batch)
+  // Batches of unequal grids (adr_batch_create_grids): per problem its nodes
+  // and spacing, per level a table of the problems' grids (host, and its copy
+  // in the arena that the kernels read); every level's Dims, fixed at creation.
+  bool hetero = false;
+  std::vector<int> pn;              // 3 per problem
+  std::vector<double> ph;           // 3 per problem
+  int nlev = 0;
+  Dims lvg[ADR_MAX_LEVELS]{};
+  std::vector<ProblemDims> tab[ADR_MAX_LEVELS];
+  ProblemDims* dtab[ADR_MAX_LEVELS] = {};
+  // Batches: per problem 1 while it is frozen inside adr_solve (the kernels
+  // of the cycle and of the iteration skip it), 0 otherwise; the host's
+  // pinned copy it is uploaded from.
+  int* skip = nullptr;
+  int* host_skip = nullptr;         // kSkipSlots rings of B ints inside the pinned host_scal block
+  int skip_slot = 0;
   adr_params_t p{};
   cudaStream_t st = nullptr;
   double omega = 0;                 // problem 0 (the only one when B = 1)
@@ -148,6 +164,7 @@ struct Op {
   double2* b = nullptr;  // point-source right-hand side
   double2* r = nullptr;
   double* packed_out = nullptr; // packed float64 rows of the outer system (k_fine_pack layout)
+  float2* packed_df = nullptr;  // the same rows split into float32 (hi, lo) pairs (float32 cycle, not rescaled)
   double2* rows_out = nullptr;  // stored float64 rows of the outer system (adjoint operators only)
   ArnoldiState ost{};
   KrylovScratch ks{};
@@ -189,6 +206,23 @@ struct Op {
 };
 
 constexpr int kProfPairs = 256;
+// Pinned slots of the frozen-problem flags: uploads between two stream
+// synchronisations of adr_solve (at most three) never reuse a slot in flight.
+constexpr int kSkipSlots = 4;
+
+// Uploads per-problem skip flags (batches only; ordered before the next launch).
+static int upload_skip(Op& op, const std::vector<int>& frozen) {
+  if (!op.skip) return ADR_OK;
+  int* slot = op.host_skip + (size_t)op.skip_slot * op.B;
+  op.skip_slot = (op.skip_slot + 1) % kSkipSlots;
+  for (int pb = 0; pb < op.B; ++pb) slot[pb] = frozen[pb] ? 1 : 0;
+  const cudaError_t e = cudaMemcpyAsync(op.skip, slot, sizeof(int) * (size_t)op.B, cudaMemcpyHostToDevice, op.st);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("skip flags: ") + cudaGetErrorString(e);
+    return ADR_ERR_CUDA;
+  }
+  return ADR_OK;
+}
 
 // Starts timing one launch of class cls on stream s; returns the pair index or -1.
 static int prof_begin(Op& op, int cls, cudaStream_t s) {
@@ -233,45 +267,104 @@ static bool can_coarsen(const Dims& g) {
   return true;
 }
 
+// One problem's grid record from its nodes and spacing.
+static ProblemDims problem_dims(int dim, const int* n, const double* h) {
+  const Dims d = make_dims(dim, n);
+  ProblemDims q{};
+  for (int k = 0; k < 3; ++k) { q.n[k] = d.n[k]; q.h[k] = k < dim ? h[k] : 1.0; }
+  q.N = d.N; q.s1 = d.s1; q.s2 = d.s2;
+  q.mul0 = d.mul0; q.mul1 = d.mul1; q.shr0 = d.shr0; q.shr1 = d.shr1;
+  return q;
+}
+
+// The grids of every level (op.lvg[0..nlev), op.tab for unequal grids): a
+// level exists while every problem's grid coarsens (reading M1), up to
+// params.levels.  Fixed at creation; the tables' device copies are set by plan().
+static void plan_levels(Op& op) {
+  op.nlev = 0;
+  for (int l = 0; l < op.p.levels; ++l) {
+    Dims g;
+    if (!op.hetero) {
+      if (l == 0) {
+        g = op.g0;
+      } else {
+        if (!can_coarsen(op.lvg[l - 1])) break;
+        int nc[3];
+        for (int d = 0; d < 3; ++d) nc[d] = (op.lvg[l - 1].n[d] - 1) / 2 + 1;
+        g = make_dims(op.dim, nc);
+      }
+    } else {
+      std::vector<ProblemDims> t(op.B);
+      bool ok = true;
+      for (int pb = 0; pb < op.B && ok; ++pb) {
+        int nn[3];
+        double hh[3];
+        for (int d = 0; d < 3; ++d) {
+          nn[d] = l == 0 ? op.pn[3 * pb + d] : (op.tab[l - 1][pb].n[d] - 1) / 2 + 1;
+          hh[d] = l == 0 ? op.ph[3 * pb + d] : 2.0 * op.tab[l - 1][pb].h[d];
+        }
+        if (l > 0) ok = can_coarsen(make_dims(op.dim, op.tab[l - 1][pb].n));
+        t[pb] = problem_dims(op.dim, nn, hh);
+      }
+      if (!ok) break;
+      int64_t off = 0, soff = 0;
+      int big = 0;
+      for (int pb = 0; pb < op.B; ++pb) {
+        t[pb].off = off;
+        t[pb].soff = soff;
+        off += t[pb].N;
+        soff += stencil_entries_dim(t[pb].N, op.dim);
+        if (t[pb].N > t[big].N) big = pb;
+      }
+      g = make_dims(op.dim, t[big].n);   // the largest grid sizes the launches
+      g.total = off;
+      op.tab[l] = t;
+    }
+    g.B = op.B;
+    g.mrcap = op.p.relax_blocks;
+    if (!op.hetero) g.total = g.N * op.B;
+    op.lvg[l] = g;
+    op.nlev = l + 1;
+  }
+}
+
+// Stored-stencil entries of level l over the batch.
+static int64_t stencil_total(const Op& op, int l) {
+  if (!op.hetero) return stencil_entries_dim(op.lvg[l].N, op.dim) * op.B;
+  const ProblemDims& q = op.tab[l].back();
+  return q.soff + stencil_entries_dim(q.N, op.dim);
+}
+
 template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
   const adr_params_t& p = op.p;
-  Dims g = op.g0;
-  H.L = 0;
-  for (int l = 0; l < p.levels; ++l) {
-    if (l > 0) {
-      if (!can_coarsen(H.lv[l - 1].g)) break;
-      int nc[3];
-      for (int d = 0; d < 3; ++d) nc[d] = (H.lv[l - 1].g.n[d] - 1) / 2 + 1;
-      g = make_dims(op.dim, nc);
-      g.B = op.B;
-      g.mrcap = op.g0.mrcap;
-    }
-    H.L = l + 1;
-    H.lv[l].g = g;
+  H.L = op.nlev;
+  for (int l = 0; l < H.L; ++l) {
+    H.lv[l].g = op.lvg[l];
+    H.lv[l].g.pd = op.dtab[l];
+    H.lv[l].g.skip = op.skip;
   }
-  const int S = op.dim == 2 ? kPattern2 : kPattern3;
-  const size_t B = (size_t)op.B;
   const size_t row_reals = op.p.rescale ? (size_t)2 * (1 + 4 * op.dim) : (size_t)(2 + 4 * op.dim);
-  H.packed = a.take<T>(row_reals * (size_t)op.g0.N * B);
+  H.packed = a.take<T>(row_reals * (size_t)op.g0.total);
   for (int l = 0; l < H.L; ++l) {
     Level<T>& L = H.lv[l];
-    const size_t N = (size_t)L.g.N;
-    L.A = l > 0 ? a.take<C<T>>((size_t)stencil_entries((int64_t)N, S) * B) : nullptr;
-    L.dinv = a.take<C<T>>(N * B);
-    L.b = a.take<C<T>>(N * B);
-    L.x = a.take<C<T>>(N * B);
-    L.r = a.take<C<T>>(N * B);
-    L.t = a.take<C<T>>(N * B);
-    L.z = a.take<C<T>>(N * B);
+    const size_t NB = (size_t)L.g.total;
+    L.A = l > 0 ? a.take<C<T>>((size_t)stencil_total(op, l)) : nullptr;
+    L.dinv = a.take<C<T>>(NB);
+    L.b = a.take<C<T>>(NB);
+    L.x = a.take<C<T>>(NB);
+    L.r = a.take<C<T>>(NB);
+    L.t = a.take<C<T>>(NB);
+    L.z = a.take<C<T>>(NB);
     L.kdim = 0;
     if (l == H.L - 1) L.kdim = p.coarse_iterations;
     else if (p.cycle == ADR_CYCLE_K && l > 0) L.kdim = p.kcycle_iterations;
     if (L.kdim > 0) {
-      L.KV = a.take<C<T>>((size_t)(L.kdim + 1) * N * B);
-      L.KZ = (l == H.L - 1) ? nullptr : a.take<C<T>>((size_t)L.kdim * N * B);
+      L.KV = a.take<C<T>>((size_t)(L.kdim + 1) * NB);
+      L.KZ = (l == H.L - 1) ? nullptr : a.take<C<T>>((size_t)L.kdim * NB);
       take_arnoldi(a, L.ks, L.kdim, op.B);
     }
   }
+  const size_t B = (size_t)op.B;
   // persistent coarsest solve: one block per 1024 nodes, all problems co-resident
   H.gs = GridScratch{};
   const int per_problem = op.grid_coresident / op.B;
@@ -302,7 +395,11 @@ template <typename T> static void plan_adjoint(const Hier<T>& H, Hier<T>& HT, Ar
 static void plan(Op& op, Arena& a) {
   const size_t B = (size_t)op.B;
   const size_t N = (size_t)op.g0.N;
-  const size_t NB = N * B;
+  const size_t NB = (size_t)op.g0.total;
+  for (int l = 0; l < op.nlev; ++l) op.dtab[l] = op.hetero ? a.take<ProblemDims>(B) : nullptr;
+  op.skip = op.B > 1 ? a.take<int>(B) : nullptr;
+  op.g0.pd = op.dtab[0];
+  op.g0.skip = op.skip;
   for (int d = 0; d < op.dim; ++d) {
     op.gd[d] = a.take<double>(NB);
     op.td[d] = a.take<double>(NB);
@@ -329,6 +426,8 @@ static void plan(Op& op, Arena& a) {
   op.b = a.take<double2>(NB);
   op.r = a.take<double2>(NB);
   op.packed_out = a.take<double>((size_t)(2 + 4 * op.dim) * NB);
+  if (op.p.outer_df && op.p.precond_precision == ADR_F32 && !op.p.rescale)
+    op.packed_df = a.take<float2>((size_t)(2 + 4 * op.dim) * NB);
   take_arnoldi(a, op.ost, m, op.B);
   op.ks.partial = a.take<double2>((size_t)kPartialStride * B);
   op.ks.ticket = a.take<unsigned>(B);
@@ -465,14 +564,14 @@ template <typename T> struct Cycle {
         x_zero = false;
         C<T>* tmp = cur; cur = oth; oth = tmp;
       }
-      if (cur != x) launch_copy<T>(cur, x, n * L.g.B, st);
+      if (cur != x) launch_copy<T>(cur, x, L.g.total, st);
       return false;
     }
     // Minimal-residual Jacobi: z = D^{-1} r, w = A z, alpha = (w^H r)/(w^H w),
     // x += alpha z, r -= alpha w (two launches per sweep).
     const C<T>* rsrc;
     if (x_zero) {
-      launch_cmul_vec<T>(L.dinv, b, L.z, n * L.g.B, st);
+      launch_cmul_vec<T>(L.dinv, b, L.z, L.g.total, st);
       rsrc = b;
     } else {
       residual_dinv(l, b, x, L.r, L.z);
@@ -481,7 +580,7 @@ template <typename T> struct Cycle {
     for (int s = 0; s < sweeps; ++s) {
       mr_apply(l, L.z, rsrc, L.t);
       launch_mr_update2<T>(x, L.z, rsrc, L.r, L.t, op.ks.alpha, L.dinv, s + 1 < sweeps ? L.z : nullptr, x_zero && s == 0,
-                           n, st, L.g.B);
+                           L.g, st);
       rsrc = L.r;
     }
     x_zero = false;
@@ -491,9 +590,9 @@ template <typename T> struct Cycle {
   // Arnoldi step j: w (holding A z_j) orthogonalised against V_0..V_j by CGS2,
   // Hessenberg column and rotation updated; V_{j+1} = w / |w| if store_next.
   // Vb holds the basis at stride ld = B n (vector-major over the batch).
-  void arnoldi(ArnoldiState& ks, C<T>* Vb, int64_t ld, int j, C<T>* w, int64_t n, int B, bool store_next) {
-    launch_cgs2<T>(Vb, ld, j + 1, w, n, op.ks, ks, j, st, B);
-    if (store_next) launch_scale_inv_norm<T>(w, Vb + (int64_t)(j + 1) * ld, op.ks.nrm2, n, st, B);
+  void arnoldi(ArnoldiState& ks, C<T>* Vb, int64_t ld, int j, C<T>* w, const Dims& g, bool store_next) {
+    launch_cgs2<T>(Vb, ld, j + 1, w, g, op.ks, ks, j, st);
+    if (store_next) launch_scale_inv_norm<T>(w, Vb + (int64_t)(j + 1) * ld, op.ks.nrm2, g, st);
   }
 
   // Fixed-count GMRES from zero, right-preconditioned by D^{-1} (coarsest level).
@@ -508,7 +607,7 @@ template <typename T> struct Cycle {
     const int k = L.kdim;
     const int form = op.p.coarse_solver;
     const bool cluster_ok = l > 0 && op.cluster_size > 0 && k <= kClusterKMax;
-    const bool grid_ok = l > 0 && H.gs.nblk > 0 && k <= kGridMaxK;
+    const bool grid_ok = l > 0 && H.gs.nblk > 0 && k <= kGridMaxK && !op.hetero;
     if (form == ADR_COARSE_CLUSTER || (form == ADR_COARSE_AUTO && n <= kClusterCoarse)) {
       if (cluster_ok) {
         launch_coarse_gmres_cluster<T>(L.g, L.A, L.dinv, b, x, L.KV, L.z, k, L.ks, op.cluster_size, st);
@@ -532,11 +631,10 @@ template <typename T> struct Cycle {
     // first cancelled (reading M2, eta = params.reorth_eta; it returns at once
     // otherwise), and the next basis vector with its Jacobi-scaled direction;
     // the last step's column also solves the least-squares problem.
-    const int B = L.g.B;
-    const int64_t ld = n * B;
+    const int64_t ld = L.g.total;
     const double eta = op.p.reorth_eta;
-    launch_norm_start<T>(b, n, op.ks, &L.ks, st, B);
-    launch_scale_dinv<T>(b, L.KV, L.dinv, L.z, op.ks.nrm2, n, st, B);   // V_0 and z = D^{-1} V_0
+    launch_norm_start<T>(b, L.g, op.ks, &L.ks, st);
+    launch_scale_dinv<T>(b, L.KV, L.dinv, L.z, op.ks.nrm2, L.g, st);   // V_0 and z = D^{-1} V_0
     for (int j = 0; j < k; ++j) {
       const int finish = j + 1 == k ? k : 0;
       bool fused = false;
@@ -549,12 +647,12 @@ template <typename T> struct Cycle {
       }
       if (!fused) {
         apply(l, L.z, L.t);
-        launch_cgs_dots_sel<T>(L.KV, ld, j + 1, L.t, n, op.ks, L.ks, j, finish, eta, st, B);
+        launch_cgs_dots_sel<T>(L.KV, ld, j + 1, L.t, L.g, op.ks, L.ks, j, finish, eta, st);
       }
-      launch_cgs_reorth<T>(L.KV, ld, j + 1, L.t, n, op.ks, L.ks, j, finish, st, B);
-      if (j + 1 < k) launch_cgs_next<T>(L.KV, ld, j + 1, L.t, n, op.ks, L.KV + (int64_t)(j + 1) * ld, L.dinv, L.z, st, B);
+      launch_cgs_reorth<T>(L.KV, ld, j + 1, L.t, L.g, op.ks, L.ks, j, finish, st);
+      if (j + 1 < k) launch_cgs_next<T>(L.KV, ld, j + 1, L.t, L.g, op.ks, L.KV + (int64_t)(j + 1) * ld, L.dinv, L.z, st);
     }
-    launch_combine_dinv<T>(x, L.KV, ld, k, L.ks, L.dinv, n, st, B);
+    launch_combine_dinv<T>(x, L.KV, ld, k, L.ks, L.dinv, L.g, st);
   }
 
   // Inner flexible GMRES of the K-cycle on level l, from zero: kdim steps,
@@ -565,18 +663,17 @@ template <typename T> struct Cycle {
     Level<T>& L = H.lv[l];
     const int64_t n = L.g.N;
     const int k = L.kdim;
-    const int B = L.g.B;
-    const int64_t ld = n * B;
-    launch_norm_start<T>(b, n, op.ks, &L.ks, st, B, op.p.kcycle_threshold);
-    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, n, st, B);
+    const int64_t ld = L.g.total;
+    launch_norm_start<T>(b, L.g, op.ks, &L.ks, st, op.p.kcycle_threshold);
+    launch_scale_inv_norm<T>(b, L.KV, op.ks.nrm2, L.g, st);
     for (int j = 0; j < k; ++j) {
       C<T>* zj = L.KZ + (int64_t)j * ld;
       cycle(l, L.KV + (int64_t)j * ld, zj);
       apply(l, zj, L.t);
-      arnoldi(L.ks, L.KV, ld, j, L.t, n, B, j + 1 < k);
+      arnoldi(L.ks, L.KV, ld, j, L.t, L.g, j + 1 < k);
     }
-    launch_backsolve(L.ks, k, st, B);
-    launch_combine<T>(x, L.KZ, ld, k, L.ks, true, n, st, B);
+    launch_backsolve(L.ks, k, st, L.g.B);
+    launch_combine<T>(x, L.KZ, ld, k, L.ks, true, L.g, st);
   }
 
   // x = B_l^{-1} b, zero initial guess (Alg. TwoGrid / Alg. Kcycle).
@@ -595,7 +692,7 @@ template <typename T> struct Cycle {
     }
     if (op.p.cycle == ADR_CYCLE_K && l + 1 < H.L - 1) kcycle(l + 1, Lc.b, Lc.x);
     else cycle(l + 1, Lc.b, Lc.x);
-    if (x_zero) { launch_zero<T>(x, n * L.g.B, st); x_zero = false; }
+    if (x_zero) { launch_zero<T>(x, L.g.total, st); x_zero = false; }
     launch_prolong_add<T>(L.g, Lc.g, Lc.x, x, st);
     relax(l, b, x, op.p.post_sweeps[l], x_zero);
   }
@@ -643,19 +740,21 @@ template <typename T> static int build_adjoint(Op& op, Hier<T>& H, Hier<T>& HT) 
 // current source / frequency, written into the operator's arena (no sync).
 static int setup(Op& op, const double* kappa, const double* tau1, const double* gamma) {
   const int64_t N = op.g0.N;
-  const int64_t NB = N * op.B;
-  Dims g1 = op.g0;
-  g1.B = 1;
+  const int64_t NB = op.g0.total;
   for (int pb = 0; pb < op.B; ++pb) {   // per-problem coefficients (setup, not the cycle)
+    // this problem alone: its grid, where its entries start, its spacing
+    const ProblemDims* q = op.hetero ? &op.tab[0][pb] : nullptr;
+    const Dims g1 = make_dims(op.dim, q ? q->n : op.g0.n);
+    const int64_t o = q ? q->off : (int64_t)pb * N;
+    const double* hp = q ? q->h : op.h;
     FineDyn dyn{};
     dyn.omega = op.omegas[pb];
     for (int d = 0; d < 3; ++d) dyn.src[d] = op.srcs[3 * pb + d];
-    dyn.src_index = dyn.src[0] + op.g0.s1 * dyn.src[1] + op.g0.s2 * dyn.src[2];
+    dyn.src_index = dyn.src[0] + g1.s1 * dyn.src[1] + g1.s2 * dyn.src[2];
     launch_set_dyn(op.dyn + pb, dyn, op.st);
     FineInputs in{};
-    const int64_t o = (int64_t)pb * N;
     in.kappa = kappa + o; in.tau1 = tau1 + o; in.gamma = gamma + o;
-    for (int d = 0; d < 3; ++d) { in.src[d] = dyn.src[d]; in.h[d] = op.h[d]; in.ih[d] = 1.0 / op.h[d]; }
+    for (int d = 0; d < 3; ++d) { in.src[d] = dyn.src[d]; in.h[d] = hp[d]; in.ih[d] = 1.0 / hp[d]; }
     in.omega = dyn.omega;
     in.plain = op.plain_tau;
     double* gd[3] = {nullptr, nullptr, nullptr};
@@ -676,8 +775,9 @@ static int setup(Op& op, const double* kappa, const double* tau1, const double* 
     launch_to_f32((const double*)op.rhos, op.rhosf, 2 * NB, op.st);
     launch_to_f32((const double*)op.srows, op.srowsf, 2 * kCross3 * op.B, op.st);
   }
-  if (op.phase) launch_phase(op.tau, op.dyn, op.phase, N, op.B, op.st);
+  if (op.phase) launch_phase(op.g0, op.tau, op.dyn, op.phase, op.st);
   launch_fine_pack<double>(op.g0, make_fine<double>(op, op.p.scheme, false), op.packed_out, op.st);
+  if (op.packed_df) launch_split_df(op.packed_out, op.packed_df, (int64_t)(2 + 4 * op.dim) * NB, op.st);
   ADR_TRY(check_launch("coefficients"));
   ADR_TRY(op.p.precond_precision == ADR_F64 ? build_hierarchy(op, op.h64) : build_hierarchy(op, op.h32));
   if (!op.p.adjoint) return ADR_OK;
@@ -739,7 +839,7 @@ template <typename T> static int run_cycle(Op& op, Hier<T>& H, bool adj = false)
 // cycle works on the rescaled variables, Alg. ADRlong; the same form for the
 // adjoint since M is unitary).
 static int precondition(Op& op, const double2* v, double2* z, bool adj = false) {
-  const int64_t NB = op.g0.N * op.B;
+  const int64_t NB = op.g0.total;
   if (op.p.precond_precision == ADR_F64) {
     Hier<double>& H = adj ? op.a64 : op.h64;
     if (op.phase) launch_phase_cast<double, double>(v, op.phase, false, H.lv[0].b, NB, op.st);
@@ -790,6 +890,7 @@ static int validate_params(const adr_params_t& p) {
   if (p.rescale != 0 && p.rescale != 1) return fail(ADR_ERR_ARG, "rescale must be 0 or 1");
   if (!(p.kcycle_threshold >= 0.0 && p.kcycle_threshold <= 1e6))
     return fail(ADR_ERR_ARG, "kcycle_threshold must be in [0, 1e6]");
+  if (p.outer_df != 0 && p.outer_df != 1) return fail(ADR_ERR_ARG, "outer_df must be 0 or 1");
   for (int l = 0; l < ADR_MAX_LEVELS; ++l) {
     if (p.pre_sweeps[l] < 0 || p.pre_sweeps[l] > 16 || p.post_sweeps[l] < 0 || p.post_sweeps[l] > 16)
       return fail(ADR_ERR_ARG, "sweeps must be in [0, 16]");
@@ -832,33 +933,46 @@ int adr_params_default(adr_params_t* p) {
   p->tma = 1;
   p->scheme = ADR_SCHEME_2UP;
   p->prec_scheme = ADR_SCHEME_PREC;
+  p->outer_df = 1;
   return ADR_OK;
 }
 
+// pn, ph (batches of unequal grids): 3 node counts and 3 spacings per
+// problem, in place of n and h.
 static int create_impl(int dim, const int* n, const double* h, int B, const int* src, const double* omega,
                        const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
-                       void* stream, adr_op_t* out, int plain_tau = 0) {
+                       void* stream, adr_op_t* out, int plain_tau = 0, const int* pn = nullptr,
+                       const double* ph = nullptr) {
   if (!out) return fail(ADR_ERR_ARG, "out is null");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(ADR_ERR_ARG, "dim must be 2 or 3");
   if (B < 1 || B > 65535) return fail(ADR_ERR_ARG, "problems must be in [1, 65535]");
-  if (!n || !h || !src || !omega || !kappa || !tau1 || !gamma) return fail(ADR_ERR_ARG, "null argument");
-  for (int d = 0; d < dim; ++d) {
-    if (n[d] < 4) return fail(ADR_ERR_ARG, "every axis needs at least 4 nodes");
-    if (!(h[d] > 0.0)) return fail(ADR_ERR_ARG, "spacings must be positive");
+  const bool hetero = pn != nullptr;
+  if ((hetero ? (!ph) : (!n || !h)) || !src || !omega || !kappa || !tau1 || !gamma)
+    return fail(ADR_ERR_ARG, "null argument");
+  int64_t total = 0;
+  for (int pb = 0; pb < (hetero ? B : 1); ++pb) {
+    const int* np = hetero ? pn + 3 * pb : n;
+    const double* hp = hetero ? ph + 3 * pb : h;
+    for (int d = 0; d < dim; ++d) {
+      if (np[d] < 4) return fail(ADR_ERR_ARG, "every axis needs at least 4 nodes");
+      if (!(hp[d] > 0.0)) return fail(ADR_ERR_ARG, "spacings must be positive");
+    }
+    const int64_t Np = (int64_t)np[0] * np[1] * (dim > 2 ? np[2] : 1);
+    total += hetero ? Np : Np * B;
   }
   for (int pb = 0; pb < B; ++pb) {
     if (!(omega[pb] > 0.0)) return fail(ADR_ERR_ARG, "omega must be positive");
+    const int* np = hetero ? pn + 3 * pb : n;
     for (int d = 0; d < dim; ++d)
-      if (src[3 * pb + d] < 0 || src[3 * pb + d] >= n[d]) return fail(ADR_ERR_ARG, "source outside the grid");
+      if (src[3 * pb + d] < 0 || src[3 * pb + d] >= np[d]) return fail(ADR_ERR_ARG, "source outside the grid");
   }
   adr_params_t p;
   if (params) p = *params;
   else adr_params_default(&p);
   ADR_TRY(validate_params(p));
   if (p.adjoint && B > 1) return fail(ADR_ERR_ARG, "the adjoint operator is built for one problem at a time");
-  const int64_t N = (int64_t)n[0] * n[1] * (dim > 2 ? n[2] : 1);
-  if (N > ((int64_t)1 << 31) - 1) return fail(ADR_ERR_ARG, "grid too large (more than 2^31 - 1 nodes)");
+  if (total > ((int64_t)1 << 31) - 1) return fail(ADR_ERR_ARG, "grid too large (more than 2^31 - 1 nodes)");
 
   adr_op_s* h_ = new (std::nothrow) adr_op_s();
   if (!h_) return fail(ADR_ERR_OOM, "host allocation failed");
@@ -866,19 +980,30 @@ static int create_impl(int dim, const int* n, const double* h, int B, const int*
   op.dim = dim;
   op.B = B;
   op.plain_tau = plain_tau;
-  op.g0 = make_dims(dim, n);
-  op.g0.B = B;
-  op.g0.mrcap = p.relax_blocks;
   op.p = p;
   op.st = (cudaStream_t)stream;
-  for (int d = 0; d < 3; ++d) op.h[d] = d < dim ? h[d] : 1.0;
+  op.hetero = hetero;
+  if (hetero) {
+    op.pn.assign(3 * (size_t)B, 1);
+    op.ph.assign(3 * (size_t)B, 1.0);
+    for (int pb = 0; pb < B; ++pb)
+      for (int d = 0; d < dim; ++d) { op.pn[3 * pb + d] = pn[3 * pb + d]; op.ph[3 * pb + d] = ph[3 * pb + d]; }
+  } else {
+    op.g0 = make_dims(dim, n);
+  }
+  plan_levels(op);
+  op.g0 = op.lvg[0];
+  for (int d = 0; d < 3; ++d) op.h[d] = hetero ? op.ph[d] : (d < dim ? h[d] : 1.0);
   op.omegas.assign(omega, omega + B);
   op.srcs.assign(3 * (size_t)B, 0);
   for (int pb = 0; pb < B; ++pb)
     for (int d = 0; d < dim; ++d) op.srcs[3 * pb + d] = src[3 * pb + d];
   op.omega = op.omegas[0];
   for (int d = 0; d < 3; ++d) op.src[d] = op.srcs[d];
-  op.src_index = op.src[0] + op.g0.s1 * op.src[1] + op.g0.s2 * op.src[2];
+  {
+    const Dims g1 = hetero ? make_dims(dim, op.tab[0][0].n) : op.g0;
+    op.src_index = op.src[0] + g1.s1 * op.src[1] + g1.s2 * op.src[2];
+  }
 
   op.grid_coresident = prepare_coarse_grid(dim, p.precond_precision == ADR_F32);
   {
@@ -898,7 +1023,9 @@ static int create_impl(int dim, const int* n, const double* h, int B, const int*
     return fail(ADR_ERR_OOM, std::string("cudaMalloc of the operator arena failed: ") + cudaGetErrorString(e));
   }
   op.host_scal_count = std::max<size_t>(16, (size_t)B * (kNumScal > 2 ? kNumScal : 2));
-  e = cudaMallocHost(&op.host_scal, op.host_scal_count * sizeof(double));
+  const size_t skip_doubles = ((size_t)kSkipSlots * B * sizeof(int) + sizeof(double) - 1) / sizeof(double);
+  e = cudaMallocHost(&op.host_scal, (op.host_scal_count + skip_doubles) * sizeof(double));
+  if (e == cudaSuccess) op.host_skip = reinterpret_cast<int*>(op.host_scal + op.host_scal_count);
   if (e != cudaSuccess) {
     cudaFree(op.arena);
     delete h_;
@@ -912,6 +1039,8 @@ static int create_impl(int dim, const int* n, const double* h, int B, const int*
   // all of the arena starts at zero: reduction tickets, convergence targets of
   // the inner Krylov instances (0 = never frozen)
   if (e == cudaSuccess) e = cudaMemsetAsync(op.arena, 0, op.arena_bytes, op.st);
+  for (int l = 0; e == cudaSuccess && hetero && l < op.nlev; ++l)   // the per-problem grid tables
+    e = cudaMemcpyAsync(op.dtab[l], op.tab[l].data(), sizeof(ProblemDims) * (size_t)B, cudaMemcpyHostToDevice, op.st);
   if (e != cudaSuccess) {
     if (op.cap) cudaStreamDestroy(op.cap);
     cudaFree(op.arena);
@@ -954,13 +1083,21 @@ int adr_batch_create(int dim, const int* n, const double* h, int problems, const
   return create_impl(dim, n, h, problems, src, omega, kappa, tau1, gamma, params, stream, out);
 }
 
+int adr_batch_create_grids(int dim, int problems, const int* n, const double* h, const int* src, const double* omega,
+                           const double* kappa, const double* tau1, const double* gamma, const adr_params_t* params,
+                           void* stream, adr_op_t* out) {
+  if (!n || !h) return fail(ADR_ERR_ARG, "null argument");
+  return create_impl(dim, nullptr, nullptr, problems, src, omega, kappa, tau1, gamma, params, stream, out, 0, n, h);
+}
+
 static int update_impl(Op& op, const int* src, const double* omega, const double* kappa, const double* tau1,
                        const double* gamma) {
   if (!src || !omega || !kappa || !tau1 || !gamma) return fail(ADR_ERR_ARG, "null argument");
   for (int pb = 0; pb < op.B; ++pb) {
     if (!(omega[pb] > 0.0)) return fail(ADR_ERR_ARG, "omega must be positive");
+    const int* np = op.hetero ? op.tab[0][pb].n : op.g0.n;
     for (int d = 0; d < op.dim; ++d)
-      if (src[3 * pb + d] < 0 || src[3 * pb + d] >= op.g0.n[d]) return fail(ADR_ERR_ARG, "source outside the grid");
+      if (src[3 * pb + d] < 0 || src[3 * pb + d] >= np[d]) return fail(ADR_ERR_ARG, "source outside the grid");
   }
   for (int pb = 0; pb < op.B; ++pb) {
     op.omegas[pb] = omega[pb];
@@ -968,7 +1105,8 @@ static int update_impl(Op& op, const int* src, const double* omega, const double
   }
   op.omega = op.omegas[0];
   for (int d = 0; d < 3; ++d) op.src[d] = op.srcs[d];
-  op.src_index = op.src[0] + op.g0.s1 * op.src[1] + op.g0.s2 * op.src[2];
+  const Dims g1 = op.hetero ? make_dims(op.dim, op.tab[0][0].n) : op.g0;
+  op.src_index = op.src[0] + g1.s1 * op.src[1] + g1.s2 * op.src[2];
   return setup(op, kappa, tau1, gamma);
 }
 
@@ -1100,9 +1238,9 @@ int adr_level_stencil(adr_op_t h, int level, void* out) {
   if (level < 1 || level >= L) return fail(ADR_ERR_ARG, "level must be in [1, levels)");
   const int S = op.dim == 2 ? kPattern2 : kPattern3;
   if (op.p.precond_precision == ADR_F64)
-    launch_stencil_export<double>(op.h64.lv[level].A, (double2*)out, op.h64.lv[level].g.N, S, op.B, op.st);
+    launch_stencil_export<double>(op.h64.lv[level].g, op.h64.lv[level].A, (double2*)out, S, op.st);
   else
-    launch_stencil_export<float>(op.h32.lv[level].A, (float2*)out, op.h32.lv[level].g.N, S, op.B, op.st);
+    launch_stencil_export<float>(op.h32.lv[level].g, op.h32.lv[level].A, (float2*)out, S, op.st);
   ADR_TRY(check_launch("adr_level_stencil"));
   return ADR_OK;
 }
@@ -1111,7 +1249,7 @@ int adr_vcycle(adr_op_t h, const void* r, void* z) {
   if (!h || !r || !z) return fail(ADR_ERR_ARG, "null argument");
   if (r == z) return fail(ADR_ERR_ARG, "z may not alias r");
   Op& op = h->op;
-  const int64_t N = op.g0.N * op.B;
+  const int64_t N = op.g0.total;
   if (op.p.precond_precision == ADR_F64) {
     launch_copy<double>((const double2*)r, op.h64.lv[0].b, N, op.st);
     ADR_TRY(run_cycle(op, op.h64));
@@ -1129,14 +1267,14 @@ int adr_point_source_rhs(adr_op_t h, void* q) {
   Op& op = h->op;
   double vol = 1.0;
   for (int d = 0; d < op.dim; ++d) vol *= op.h[d];
-  launch_rhs_point((double2*)q, op.g0.N, op.dyn, 1.0 / vol, op.B, op.st);
+  launch_rhs_point(op.g0, (double2*)q, op.dyn, 1.0 / vol, op.st);
   return check_launch("adr_point_source_rhs");
 }
 
 int adr_reconstruct(adr_op_t h, const void* a, void* u) {
   if (!h || !a || !u) return fail(ADR_ERR_ARG, "null argument");
   Op& op = h->op;
-  launch_reconstruct((const double2*)a, op.tau, op.dyn, (double2*)u, op.g0.N, op.B, op.st);
+  launch_reconstruct(op.g0, (const double2*)a, op.tau, op.dyn, (double2*)u, op.st);
   return check_launch("adr_reconstruct");
 }
 
@@ -1150,13 +1288,15 @@ int adr_reconstruct(adr_op_t h, const void* a, void* u) {
 static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, double tol, int maxit, adr_solve_info_t* info) {
   cudaStream_t st = op.st;
   const int B = op.B;
-  const int64_t N = op.g0.N;
-  const int64_t NB = N * B;
+  const int64_t NB = op.g0.total;
   const int m = op.p.restart;
-  // the outer operator: packed rows, or the stored conjugate-transposed rows
+  // the outer operator: packed rows, or the stored conjugate-transposed rows;
+  // A z_j with a float32 cycle reads z_j as the cycle left it (float32
+  // values) and sums in double-float arithmetic
   const FineOp<double> fo = outer_op(op);
   auto outer_apply = [&](const double2* x, double2* y) {
     if (adj) launch_rows_apply(op.g0, op.rows_outT, x, y, st);
+    else if (op.packed_df) launch_packed_apply_df(op.g0, fo, op.packed_df, (const float2*)op.h32.lv[0].x, y, st);
     else launch_packed_apply(op.g0, fo, x, y, st);
   };
   auto outer_residual = [&](const double2* bb, const double2* x, double2* r) {
@@ -1165,7 +1305,7 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
   };
   const double* hs = op.host_scal;
 
-  launch_norm_start<double>(b, N, op.ks, nullptr, st, B);
+  launch_norm_start<double>(b, op.g0, op.ks, nullptr, st);
   launch_set_target(op.ost, op.ks.nrm2, tol, st, B);
   ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2 * B));
   std::vector<double> bnorm(B), beta(B), est(B);
@@ -1177,7 +1317,7 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
     launch_zero<double>(a, NB, st);
     launch_copy<double>(b, op.r, NB, st);
   }
-  launch_norm_start<double>(op.r, N, op.ks, &op.ost, st, B);
+  launch_norm_start<double>(op.r, op.g0, op.ks, &op.ost, st);
   ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2 * B));
   int active = 0;
   for (int pb = 0; pb < B; ++pb) {
@@ -1188,11 +1328,15 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
   }
   int its = 0, cycles = 0;
   bool nan = false;
-  std::vector<int> frozen(B);
+  std::vector<int> frozen(B), none(B, 0);
+  // Batches: a frozen problem's blocks skip every launch of the iteration and
+  // of the cycle (op.skip), until the restart's combination and explicit
+  // residual, which run for every problem.
   while (active > 0 && its < maxit) {
     // op.ks.nrm2 holds |r|^2 and op.ost fresh cycles here
-    launch_scale_inv_norm<double>(op.r, op.V, op.ks.nrm2, N, st, B);
     for (int pb = 0; pb < B; ++pb) frozen[pb] = done[pb];
+    ADR_TRY(upload_skip(op, frozen));
+    launch_scale_inv_norm<double>(op.r, op.V, op.ks.nrm2, op.g0, st);
     int k = 0;
     for (int j = 0; j < m; ++j) {
       double2* vj = op.V + (int64_t)j * NB;
@@ -1204,29 +1348,31 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
         outer_apply(zj, w);
         prof_end(op, pk, st);
       }
-      launch_cgs_selective<double>(op.V, NB, j + 1, w, N, op.ks, op.ost, j, op.p.reorth_eta, st, B);
-      launch_scale_inv_norm<double>(w, w, op.ks.nrm2, N, st, B);
+      launch_cgs_selective<double>(op.V, NB, j + 1, w, op.g0, op.ks, op.ost, j, op.p.reorth_eta, st);
+      launch_scale_inv_norm<double>(w, w, op.ks.nrm2, op.g0, st);
       ADR_TRY(check_launch("adr_solve iteration"));
       ADR_TRY(read_scalars(op, op.ost.scal, kNumScal * B));
       ++its;
       k = j + 1;
-      int open = 0;
+      int open = 0, newly = 0;
       for (int pb = 0; pb < B; ++pb) {
         if (frozen[pb]) continue;
         const double* sc = hs + (size_t)pb * kNumScal;
         ++its_p[pb];
         est[pb] = sc[kScalEst] / bnorm[pb];
         if (!std::isfinite(est[pb]) || !std::isfinite(sc[kScalHn])) { nan = true; status[pb] = ADR_ERR_NAN; }
-        if (sc[kScalHn] == 0.0 || sc[kScalEst] <= sc[kScalTarget]) frozen[pb] = 1;
+        if (sc[kScalHn] == 0.0 || sc[kScalEst] <= sc[kScalTarget]) { frozen[pb] = 1; ++newly; }
         else ++open;
       }
       if (nan || open == 0 || its >= maxit) break;
+      if (newly) ADR_TRY(upload_skip(op, frozen));
     }
     if (nan) break;
+    ADR_TRY(upload_skip(op, none));
     launch_backsolve(op.ost, k, st, B);
-    launch_combine<double>(a, op.Z, NB, k, op.ost, false, N, st, B);
+    launch_combine<double>(a, op.Z, NB, k, op.ost, false, op.g0, st);
     outer_residual(b, a, op.r);
-    launch_norm_start<double>(op.r, N, op.ks, &op.ost, st, B);
+    launch_norm_start<double>(op.r, op.g0, op.ks, &op.ost, st);
     ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2 * B));
     ++cycles;
     active = 0;
@@ -1239,8 +1385,12 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
     }
     if (nan) break;
   }
-  for (int pb = 0; pb < B; ++pb)
-    if (bnorm[pb] == 0.0) launch_zero<double>(a + (int64_t)pb * N, N, st);   // zero right-hand side: a = 0
+  ADR_TRY(upload_skip(op, none));
+  for (int pb = 0; pb < B; ++pb) {   // zero right-hand side: a = 0
+    if (bnorm[pb] != 0.0) continue;
+    if (op.hetero) launch_zero<double>(a + op.tab[0][pb].off, op.tab[0][pb].N, st);
+    else launch_zero<double>(a + (int64_t)pb * op.g0.N, op.g0.N, st);
+  }
   ADR_TRY(check_launch("adr_solve"));
   bool all_ok = true;
   for (int pb = 0; pb < B; ++pb) {

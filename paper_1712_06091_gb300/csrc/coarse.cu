@@ -16,11 +16,12 @@ static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n
 // register-capped kernels' spills at their unbatched level.
 template <int DIM, typename T, bool BT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_apply(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
+  if (BT && resolve(g)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
   if (BT) {
-    batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
-    batch_shift(g.N, x, y);
+    shift_stencil(g, A);
+    shift_nodes(g, x, y);
   }
   int i0, i1, i2;
   unravel(g, j, i0, i1, i2);
@@ -30,10 +31,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_apply(D
 template <int DIM, typename T>
 __global__ void k_stencil_residual(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ b,
                                    const C<T>* __restrict__ x, C<T>* __restrict__ r) {
+  if (resolve(g)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
-  batch_shift(g.N, b, x, r);
+  shift_stencil(g, A);
+  shift_nodes(g, b, x, r);
   int i0, i1, i2;
   unravel(g, j, i0, i1, i2);
   r[j] = csub(b[j], stencil_dot<DIM, T>(g, A, x, j, i0, i1, i2));
@@ -42,11 +44,12 @@ __global__ void k_stencil_residual(Dims g, const C<T>* __restrict__ A, const C<T
 template <int DIM, typename T>
 __global__ void k_stencil_jacobi(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ dinv,
                                  const C<T>* __restrict__ b, const C<T>* __restrict__ xin, C<T>* __restrict__ xout, T w) {
+  if (resolve(g)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
-  batch_shift(g.N, dinv, b, xout);
-  batch_shift_opt(g.N, xin);
+  shift_stencil(g, A);
+  shift_nodes(g, dinv, b, xout);
+  shift_nodes_opt(g, xin);
   if (xin == nullptr) {
     xout[j] = cscale(cmul(dinv[j], b[j]), w);
     return;
@@ -61,12 +64,14 @@ __global__ void k_stencil_jacobi(Dims g, const C<T>* __restrict__ A, const C<T>*
 template <int DIM, typename T>
 __global__ void k_galerkin_stored(Dims gf, Dims gc, const C<T>* __restrict__ Af, C<T>* __restrict__ out,
                                   C<T>* __restrict__ dinv) {
+  if (resolve(gf)) return;
+  resolve(gc);
   constexpr int S = PatternSize<DIM>::value;
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= gc.N) return;
-  batch_shift(stencil_entries(gf.N, S), Af);
-  batch_shift(stencil_entries(gc.N, S), out);
-  batch_shift(gc.N, dinv);
+  shift_stencil(gf, Af);
+  shift_stencil(gc, out);
+  shift_nodes(gc, dinv);
   int Ii[3];
   unravel(gc, I, Ii[0], Ii[1], Ii[2]);
   C<T> acc[S];
@@ -111,10 +116,12 @@ __global__ void k_galerkin_stored(Dims gf, Dims gc, const C<T>* __restrict__ Af,
 // r_c = P^T r_f : weights 1 on the coincident node, 1/2 per axis offset by one.
 template <int DIM, typename T>
 __global__ void k_restrict(Dims gf, Dims gc, const C<T>* __restrict__ rf, C<T>* __restrict__ rc) {
+  if (resolve(gf)) return;
+  resolve(gc);
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= gc.N) return;
-  batch_shift(gf.N, rf);
-  batch_shift(gc.N, rc);
+  shift_nodes(gf, rf);
+  shift_nodes(gc, rc);
   int Ii[3];
   unravel(gc, I, Ii[0], Ii[1], Ii[2]);
   C<T> acc = czero<T>();
@@ -139,10 +146,12 @@ __global__ void k_restrict(Dims gf, Dims gc, const C<T>* __restrict__ rf, C<T>* 
 // x_f += P e_c
 template <int DIM, typename T>
 __global__ void k_prolong_add(Dims gf, Dims gc, const C<T>* __restrict__ ec, C<T>* __restrict__ xf) {
+  if (resolve(gf)) return;
+  resolve(gc);
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= gf.N) return;
-  batch_shift(gc.N, ec);
-  batch_shift(gf.N, xf);
+  shift_nodes(gc, ec);
+  shift_nodes(gf, xf);
   int ii[3];
   unravel(gf, j, ii[0], ii[1], ii[2]);
   int pj[3][2];
@@ -163,20 +172,22 @@ __global__ void k_prolong_add(Dims gf, Dims gc, const C<T>* __restrict__ ec, C<T
 
 // Point-major copy (entry p of node j at p * N + j) of a tiled stencil.
 template <typename T>
-__global__ void k_stencil_export(const C<T>* __restrict__ A, C<T>* __restrict__ out, int64_t N, int S) {
+__global__ void k_stencil_export(Dims g, const C<T>* __restrict__ A, C<T>* __restrict__ out, int S) {
+  if (resolve(g)) return;
+  const int64_t N = g.N;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= N * S) return;
-  batch_shift(stencil_entries(N, S), A);
-  batch_shift(N * S, out);
+  shift_stencil(g, A);
+  shift_scaled(g, S, out);
   const int p = (int)(e / N);
   const int64_t j = e - (int64_t)p * N;
   out[e] = S == kPattern2 ? stencil_get<2, T>(A, p, j) : stencil_get<3, T>(A, p, j);
 }
-template <typename T> void launch_stencil_export(const C<T>* A, C<T>* out, int64_t N, int S, int B, cudaStream_t st) {
-  count_launches(1), k_stencil_export<T><<<dim3(blocks_for(N * S, 256), B), 256, 0, st>>>(A, out, N, S);
+template <typename T> void launch_stencil_export(const Dims& g, const C<T>* A, C<T>* out, int S, cudaStream_t st) {
+  count_launches(1), k_stencil_export<T><<<dim3(blocks_for(g.N * S, 256), g.B), 256, 0, st>>>(g, A, out, S);
 }
-template void launch_stencil_export<double>(const double2*, double2*, int64_t, int, int, cudaStream_t);
-template void launch_stencil_export<float>(const float2*, float2*, int64_t, int, int, cudaStream_t);
+template void launch_stencil_export<double>(const Dims&, const double2*, double2*, int, cudaStream_t);
+template void launch_stencil_export<float>(const Dims&, const float2*, float2*, int, cudaStream_t);
 
 template <typename T> void launch_stencil_apply(const Dims& g, const C<T>* A, const C<T>* x, C<T>* y, cudaStream_t st) {
   const int th = 256;
@@ -234,8 +245,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_mr_appl
                                                           double2* partial, unsigned* ticket, double2* alpha) {
   __shared__ double2 sh[32 * 2];
   if (BT) {
-    batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
-    batch_shift(g.N, z, r, w);
+    if (resolve(g)) return;
+    shift_stencil(g, A);
+    shift_nodes(g, z, r, w);
     batch_shift(kPartialStride, partial);
     batch_shift(1, ticket, alpha);
   }
@@ -260,11 +272,12 @@ template <int DIM, typename T, bool BT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_stencil_residual_dinv(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ b,
                                         const C<T>* __restrict__ x, const C<T>* __restrict__ dinv, C<T>* __restrict__ r,
                                         C<T>* __restrict__ z) {
+  if (BT && resolve(g)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
   if (BT) {
-    batch_shift(stencil_entries(g.N, PatternSize<DIM>::value), A);
-    batch_shift(g.N, b, x, dinv, r, z);
+    shift_stencil(g, A);
+    shift_nodes(g, b, x, dinv, r, z);
   }
   int i0, i1, i2;
   unravel(g, j, i0, i1, i2);
@@ -306,10 +319,11 @@ __global__ void __launch_bounds__(1024) k_coarse_gmres_cta(Dims g, const C<T>* _
   __shared__ double2 hb[kMaxKrylov + 1];
   __shared__ C<T> cv[kMaxKrylov + 1];
   __shared__ double s_scale;
+  if (resolve(g)) return;
   const int64_t n = g.N;
-  const int64_t ld = (int64_t)g.B * n;   // basis stride
-  batch_shift(stencil_entries(n, PatternSize<DIM>::value), A);
-  batch_shift(n, dinv, b, x, V, z);
+  const int64_t ld = g.total;   // basis stride
+  shift_stencil(g, A);
+  shift_nodes(g, dinv, b, x, V, z);
   st = arnoldi_at(st, blockIdx.y);
   // beta = |b|, V_0 = b / beta
   {

@@ -69,10 +69,11 @@ __global__ void __launch_bounds__(kClusterThreads) k_coarse_gmres_cluster(Dims g
   cg::cluster_group cl = cg::this_cluster();
   const int nb = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
+  if (resolve(g)) return;
   const int64_t n = g.N;
-  const int64_t ld = (int64_t)g.B * n;   // basis stride (problem = blockIdx.y)
-  batch_shift(stencil_entries(n, PatternSize<DIM>::value), A);
-  batch_shift(n, dinv, b, x, V, z);
+  const int64_t ld = g.total;   // basis stride (problem = blockIdx.y)
+  shift_stencil(g, A);
+  shift_nodes(g, dinv, b, x, V, z);
   st = arnoldi_at(st, blockIdx.y);
   const int64_t chunk = (n + nb - 1) / nb;
   const int64_t lo = rank * chunk < n ? rank * chunk : n;

@@ -119,12 +119,13 @@ __global__ void __launch_bounds__(kGridThreads) k_coarse_gmres_grid(Dims g, cons
                                                                     const C<T>* __restrict__ dinv, const C<T>* b, C<T>* x,
                                                                     C<T>* V, C<T>* z, int k, GridScratch gs,
                                                                     double eta2) {
+  if (resolve(g)) return;
   const int pb = blockIdx.y;
   const unsigned nblk = gridDim.x;
   const int64_t n = g.N;
-  const int64_t ld = (int64_t)g.B * n;
-  batch_shift(stencil_entries(n, PatternSize<DIM>::value), A);
-  batch_shift(n, dinv, b, x, V, z);
+  const int64_t ld = g.total;
+  shift_stencil(g, A);
+  shift_nodes(g, dinv, b, x, V, z);
   double2* part0 = gs.part + (size_t)pb * 2 * gs.nblk * kGridStride;
   double2* part1 = part0 + (size_t)gs.nblk * kGridStride;
   unsigned* bar = gs.bar + 2 * pb;

@@ -48,6 +48,7 @@ template <int DIM> struct Split {
   static constexpr int W = NB + NT / 2;
   static_assert(NT % 2 == 0, "two-point reals fill whole complex words");
 };
+static_assert(Split<2>::W == 15 && Split<3>::W == 54, "stencil_words");
 __host__ __device__ __forceinline__ int64_t stencil_entries(int64_t N, int S) {
   return ((N + 31) >> 5) * 32 * (S == kPattern2 ? Split<2>::W : Split<3>::W);
 }

@@ -140,9 +140,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   __shared__ double2 sh[32 * 2];
   __shared__ int s_fail;
   if (BT) {
-    batch_shift(stencil_entries(g.N, S), A);
-    batch_shift(g.N, x, aux, out);
-    batch_shift_opt(g.N, dinv, out2, V);
+    if (resolve(g)) return;
+    shift_stencil(g, A);
+    shift_nodes(g, x, aux, out);
+    shift_nodes_opt(g, dinv, out2, V);
     batch_shift_opt(kPartialStride, partial);
     batch_shift_opt(1, ticket);
     batch_shift_opt(MODE == kTmaArnoldi ? kMaxArnoldiDots : 1, alpha);

@@ -27,6 +27,7 @@ __device__ __forceinline__ double tau1_at(const Dims& g, const double* tau1, int
 
 __global__ void k_coefficients(Dims g, FineInputs in, double* g0, double* g1, double* g2, double* t0, double* t1,
                                double* t2, double2* rho, double* tau) {
+  if (resolve(g)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
   int ii[3];
@@ -77,6 +78,7 @@ __global__ void k_coefficients(Dims g, FineInputs in, double* g0, double* g1, do
 // Row of M^{-1} H M at the source (one thread).  H has its own Neumann ghost
 // u_{b+s} = u_{b-s}, so an off-grid neighbour folds onto its mirror.
 __global__ void k_source_row(Dims g, FineInputs in, const double* tau, double2* row) {
+  if (resolve(g)) return;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int k = 0; k < kCross3; ++k) row[k] = make_double2(0.0, 0.0);
   const int64_t js = in.src[0] + g.s1 * in.src[1] + g.s2 * in.src[2];
@@ -113,6 +115,7 @@ void launch_coefficients(const Dims& g, const FineInputs& in, double* const gd[3
 // (the diagonal of every row) and the diagonal of the source row.
 __global__ void k_shift(Dims g, FineInputs in, double alpha, const double2* rho, const double2* srow, double2* rho_s,
                         double2* srow_s) {
+  if (resolve(g)) return;
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
   const double m = alpha * in.omega * in.omega;
@@ -146,12 +149,12 @@ void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
 // Writes the row of node j (coordinates ii) in cross form into c[1 + 4*DIM].
 template <int DIM, typename T>
 __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int64_t j, const int ii[3], C<T>* c) {
-  // Problem blockIdx.y of a batch: its coefficients start pb * N entries in,
-  // its FineDyn and source row are entry pb of theirs.
+  // Problem blockIdx.y of a batch (g resolved): its coefficients start g.off
+  // entries in, its FineDyn and source row are entry pb of theirs.
   const int pb = blockIdx.y;
-  const int64_t jo = j + (int64_t)pb * g.N;
+  const int64_t jo = j + g.off;
   if (f.rows) {
-    const C<T>* rows = f.rows + (int64_t)pb * (1 + 4 * DIM) * g.N;
+    const C<T>* rows = f.rows + (int64_t)(1 + 4 * DIM) * g.off;
 #pragma unroll
     for (int q = 0; q < 1 + 4 * DIM; ++q) c[q] = __ldg(rows + (int64_t)q * g.N + j);
     return;
@@ -173,7 +176,7 @@ __device__ __forceinline__ void fine_row(const Dims& g, const FineOp<T>& f, int6
     // are the Laplacian's 1/h^2, doubled onto the inner neighbour on a face
     // (ghost elimination) and zero at the eliminated ghost and at +-2, the
     // same values the computed row holds.
-    const T* pk = f.packed + (int64_t)pb * (2 + 4 * DIM) * g.N + j;
+    const T* pk = f.packed + (int64_t)(2 + 4 * DIM) * g.off + j;
     c[0] = mk<T>(__ldg(pk), __ldg(pk + g.N));
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -284,9 +287,10 @@ __device__ __forceinline__ C<T> cross_dot(const Dims& g, const C<T>* c, const in
 
 template <int DIM, typename T>
 __global__ void k_fine_apply(Dims g, FineOp<T> f, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
+  if (resolve(g, f)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(g.N, x, y);
+  shift_nodes(g, x, y);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -297,9 +301,10 @@ __global__ void k_fine_apply(Dims g, FineOp<T> f, const C<T>* __restrict__ x, C<
 template <int DIM, typename T>
 __global__ void k_fine_residual(Dims g, FineOp<T> f, const C<T>* __restrict__ b, const C<T>* __restrict__ x,
                                 C<T>* __restrict__ r) {
+  if (resolve(g, f)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(g.N, b, x, r);
+  shift_nodes(g, b, x, r);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -310,10 +315,11 @@ __global__ void k_fine_residual(Dims g, FineOp<T> f, const C<T>* __restrict__ b,
 template <int DIM, typename T>
 __global__ void k_fine_jacobi(Dims g, FineOp<T> f, const C<T>* __restrict__ b, const C<T>* __restrict__ xin,
                               C<T>* __restrict__ xout, T w) {
+  if (resolve(g, f)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(g.N, b, xout);
-  batch_shift_opt(g.N, xin);
+  shift_nodes(g, b, xout);
+  shift_nodes_opt(g, xin);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -329,10 +335,11 @@ __global__ void k_fine_jacobi(Dims g, FineOp<T> f, const C<T>* __restrict__ b, c
 
 template <int DIM, typename T>
 __global__ void k_fine_dinv(Dims g, FineOp<T> f, const C<T>* __restrict__ v, C<T>* __restrict__ z) {
+  if (resolve(g, f)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(g.N, z);
-  batch_shift_opt(g.N, v);
+  shift_nodes(g, z);
+  shift_nodes_opt(g, v);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -387,11 +394,13 @@ __device__ __forceinline__ void galerkin_accumulate(const Dims& gf, const Dims& 
 
 template <int DIM, typename T>
 __global__ void k_galerkin_fine(Dims gf, Dims gc, FineOp<T> f, C<T>* __restrict__ out, C<T>* __restrict__ dinv) {
+  if (resolve(gf, f)) return;
+  resolve(gc);
   constexpr int S = PatternSize<DIM>::value;
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= gc.N) return;
-  batch_shift(stencil_entries(gc.N, S), out);
-  batch_shift(gc.N, dinv);
+  shift_stencil(gc, out);
+  shift_nodes(gc, dinv);
   int Ii[3];
   unravel(gc, I, Ii[0], Ii[1], Ii[2]);
   C<T> acc[S];
@@ -454,39 +463,47 @@ ADR_INSTANTIATE_FINE(float)
 // ---------------------------------------------------------------------------
 // Point source, reconstruction, coefficient export
 // ---------------------------------------------------------------------------
-__global__ void k_rhs_point(double2* q, int64_t N, const FineDyn* dyn, double value) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  batch_shift(N, q);
+// value = 1 / prod(h) (per-problem grids: from the problem's own spacing)
+__global__ void k_rhs_point(Dims g, double2* q, const FineDyn* dyn, double value) {
+  if (resolve(g)) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  shift_nodes(g, q);
+  if (g.pd) {
+    double vol = 1.0;
+    for (int d = 0; d < g.dim; ++d) vol *= g.pd[blockIdx.y].h[d];
+    value = 1.0 / vol;
+  }
   q[i] = make_double2(i == dyn[blockIdx.y].src_index ? value : 0.0, 0.0);
 }
-void launch_rhs_point(double2* q, int64_t N, const FineDyn* dyn, double value, int B, cudaStream_t st) {
-  count_launches(1), k_rhs_point<<<dim3(blocks_for(N, 256), B), 256, 0, st>>>(q, N, dyn, value);
+void launch_rhs_point(const Dims& g, double2* q, const FineDyn* dyn, double value, cudaStream_t st) {
+  count_launches(1), k_rhs_point<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, q, dyn, value);
 }
 
-__global__ void k_reconstruct(const double2* a, const double* tau, const FineDyn* dyn, double2* u, int64_t N) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  batch_shift(N, a, tau, u);
+__global__ void k_reconstruct(Dims g, const double2* a, const double* tau, const FineDyn* dyn, double2* u) {
+  if (resolve(g)) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  shift_nodes(g, a, tau, u);
   double s, c;
   sincos(-dyn[blockIdx.y].omega * tau[i], &s, &c);
   u[i] = cmul(a[i], make_double2(c, s));
 }
-void launch_reconstruct(const double2* a, const double* tau, const FineDyn* dyn, double2* u, int64_t N, int B,
-                        cudaStream_t st) {
-  count_launches(1), k_reconstruct<<<dim3(blocks_for(N, 256), B), 256, 0, st>>>(a, tau, dyn, u, N);
+void launch_reconstruct(const Dims& g, const double2* a, const double* tau, const FineDyn* dyn, double2* u, cudaStream_t st) {
+  count_launches(1), k_reconstruct<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, a, tau, dyn, u);
 }
 
-__global__ void k_phase(const double* tau, const FineDyn* dyn, double2* phase, int64_t N) {
+__global__ void k_phase(Dims g, const double* tau, const FineDyn* dyn, double2* phase) {
+  if (resolve(g)) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  batch_shift(N, tau, phase);
+  if (i >= g.N) return;
+  shift_nodes(g, tau, phase);
   double s, c;
   sincos(-dyn[blockIdx.y].omega * tau[i], &s, &c);
   phase[i] = make_double2(c, s);
 }
-void launch_phase(const double* tau, const FineDyn* dyn, double2* phase, int64_t N, int B, cudaStream_t st) {
-  count_launches(1), k_phase<<<dim3(blocks_for(N, 256), B), 256, 0, st>>>(tau, dyn, phase, N);
+void launch_phase(const Dims& g, const double* tau, const FineDyn* dyn, double2* phase, cudaStream_t st) {
+  count_launches(1), k_phase<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, tau, dyn, phase);
 }
 
 template <typename Ts, typename Td>
@@ -510,11 +527,12 @@ template void launch_phase_cast<float, double>(const float2*, const double2*, bo
 
 __global__ void k_pack(Dims g, const double* g0, const double* g1, const double* g2, const double* t0, const double* t1,
                        const double* t2, const double2* rho, const double* tau, double* out) {
+  if (resolve(g)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(g.N, g0, t0, rho, tau);
-  batch_shift_opt(g.N, g1, g2, t1, t2);
-  batch_shift((2 * g.dim + 3) * g.N, out);
+  shift_nodes(g, g0, t0, rho, tau);
+  shift_nodes_opt(g, g1, g2, t1, t2);
+  shift_scaled(g, 2 * g.dim + 3, out);
   const double* gs[3] = {g0, g1, g2};
   const double* ts[3] = {t0, t1, t2};
   int k = 0;
@@ -538,12 +556,18 @@ namespace adr {
 
 // w = A z and, over all nodes, alpha = (w^H r) / (w^H w) (the one-step
 // minimal-residual weight), computed by the last block to finish.
-template <int DIM, typename T>
+// BT: 0 one problem (no per-problem resolution: its offsets are zero), 1 a
+// batch on one grid, 2 a batch of per-problem grids (the spacing is the
+// problem's own); the narrower instantiations keep this register-capped
+// kernel's spills at their level.
+template <int DIM, typename T, int BT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_fine_mr_apply(Dims g, FineOp<T> f, const C<T>* __restrict__ z,
                                                        const C<T>* __restrict__ r, C<T>* __restrict__ w,
                                                        double2* partial, unsigned* ticket, double2* alpha) {
+  if (BT == 1 && resolve_uniform(g)) return;
+  if (BT == 2 && resolve(g, f)) return;
   __shared__ double2 sh[32 * 2];
-  batch_shift(g.N, z, r, w);
+  if (BT) shift_nodes(g, z, r, w);
   C<T> s[2] = {czero<T>(), czero<T>()};
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < g.N; j += (int64_t)gridDim.x * blockDim.x) {
     int ii[3];
@@ -566,12 +590,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_fine_mr_apply(D
 }
 
 // r = b - A x ; z = D^{-1} r
-template <int DIM, typename T>
+template <int DIM, typename T, int BT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_fine_residual_dinv(Dims g, FineOp<T> f, const C<T>* __restrict__ b, const C<T>* __restrict__ x,
                                      const C<T>* __restrict__ dinv, C<T>* __restrict__ r, C<T>* __restrict__ z) {
+  if (BT == 1 && resolve_uniform(g)) return;
+  if (BT == 2 && resolve(g, f)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(g.N, b, x, dinv, r, z);
+  if (BT) shift_nodes(g, b, x, dinv, r, z);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -596,14 +622,20 @@ template <typename T>
 void launch_fine_mr_apply(const Dims& g, const FineOp<T>& f, const C<T>* z, const C<T>* r, C<T>* w, double2* partial,
                           unsigned* ticket, double2* alpha, cudaStream_t st) {
   const unsigned nb = mr_blocks(g);
-  if (g.dim == 2) count_launches(1), k_fine_mr_apply<2, T><<<dim3(nb, g.B), 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
-  else count_launches(1), k_fine_mr_apply<3, T><<<dim3(nb, g.B), 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
+  const int bt = g.pd ? 2 : (g.B > 1 ? 1 : 0);
+  auto kern = g.dim == 2 ? (bt == 2 ? k_fine_mr_apply<2, T, 2> : bt ? k_fine_mr_apply<2, T, 1> : k_fine_mr_apply<2, T, 0>)
+                         : (bt == 2 ? k_fine_mr_apply<3, T, 2> : bt ? k_fine_mr_apply<3, T, 1> : k_fine_mr_apply<3, T, 0>);
+  count_launches(1), kern<<<dim3(nb, g.B), 256, 0, st>>>(g, f, z, r, w, partial, ticket, alpha);
 }
 template <typename T>
 void launch_fine_residual_dinv(const Dims& g, const FineOp<T>& f, const C<T>* b, const C<T>* x, const C<T>* dinv, C<T>* r,
                                C<T>* z, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_fine_residual_dinv<2, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, b, x, dinv, r, z);
-  else count_launches(1), k_fine_residual_dinv<3, T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, b, x, dinv, r, z);
+  const int bt = g.pd ? 2 : (g.B > 1 ? 1 : 0);
+  auto kern = g.dim == 2 ? (bt == 2 ? k_fine_residual_dinv<2, T, 2> : bt ? k_fine_residual_dinv<2, T, 1>
+                                                                          : k_fine_residual_dinv<2, T, 0>)
+                         : (bt == 2 ? k_fine_residual_dinv<3, T, 2> : bt ? k_fine_residual_dinv<3, T, 1>
+                                                                          : k_fine_residual_dinv<3, T, 0>);
+  count_launches(1), kern<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, b, x, dinv, r, z);
 }
 template void launch_fine_mr_apply<double>(const Dims&, const FineOp<double>&, const double2*, const double2*, double2*,
                                            double2*, unsigned*, double2*, cudaStream_t);
@@ -626,9 +658,10 @@ namespace adr {
 
 template <int DIM, typename T>
 __global__ void k_fine_store_rows(Dims g, FineOp<T> f, C<T>* __restrict__ rows) {
+  if (resolve(g, f)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift((1 + 4 * DIM) * g.N, rows);
+  shift_scaled(g, 1 + 4 * DIM, rows);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -640,10 +673,11 @@ __global__ void k_fine_store_rows(Dims g, FineOp<T> f, C<T>* __restrict__ rows) 
 // The packed form of the rows (see fine_row), built from the computed rows.
 template <int DIM, typename T>
 __global__ void k_fine_pack(Dims g, FineOp<T> f, T* __restrict__ packed) {
+  if (resolve(g, f)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
   f.packed = nullptr;
-  batch_shift((2 + 4 * DIM) * g.N, packed);
+  shift_scaled(g, 2 + 4 * DIM, packed);
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   C<T> c[1 + 4 * DIM];
@@ -672,20 +706,22 @@ __device__ __forceinline__ C<T> rows_dot(const Dims& g, const C<T>* __restrict__
 
 template <int DIM, typename T>
 __global__ void k_rows_apply(Dims g, const C<T>* __restrict__ rows, const C<T>* __restrict__ x, C<T>* __restrict__ y) {
+  if (resolve(g)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift((1 + 4 * DIM) * g.N, rows);
-  batch_shift(g.N, x, y);
+  shift_scaled(g, 1 + 4 * DIM, rows);
+  shift_nodes(g, x, y);
   y[j] = rows_dot<DIM, T>(g, rows, j, x);
 }
 
 template <int DIM, typename T>
 __global__ void k_rows_residual(Dims g, const C<T>* __restrict__ rows, const C<T>* __restrict__ b,
                                 const C<T>* __restrict__ x, C<T>* __restrict__ r) {
+  if (resolve(g)) return;
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift((1 + 4 * DIM) * g.N, rows);
-  batch_shift(g.N, b, x, r);
+  shift_scaled(g, 1 + 4 * DIM, rows);
+  shift_nodes(g, b, x, r);
   r[j] = csub(b[j], rows_dot<DIM, T>(g, rows, j, x));
 }
 
@@ -707,7 +743,7 @@ __device__ __forceinline__ double2 packed_dot(const Dims& g, const FineOp<double
     fine_row<DIM, double>(g, f, j, ii, c);   // the source row (Eq. helmADR2)
     return cross_dot<DIM, double>(g, c, ii, j, x);
   }
-  const double* pk = f.packed + (int64_t)blockIdx.y * (2 + 4 * DIM) * g.N + j;
+  const double* pk = f.packed + (int64_t)(2 + 4 * DIM) * g.off + j;
   const double2 xj = __ldg(x + j);
   const double cr = __ldg(pk), ci = __ldg(pk + g.N);
   double ar = cr * xj.x, ai = cr * xj.y;
@@ -742,32 +778,177 @@ __device__ __forceinline__ double2 packed_dot(const Dims& g, const FineOp<double
   return make_double2(ar + br, ai + bi);
 }
 
-template <int DIM>
+// BT as for k_fine_mr_apply: 0 one problem, 1 one grid, 2 per-problem grids.
+template <int DIM, int BT>
 __global__ void __launch_bounds__(256) k_packed_apply(Dims g, FineOp<double> f, const double2* __restrict__ x,
                                                       double2* __restrict__ y) {
+  if (BT == 1 && resolve_uniform(g)) return;
+  if (BT == 2 && resolve(g, f)) return;
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(g.N, x, y);
+  if (BT) shift_nodes(g, x, y);
   y[j] = packed_dot<DIM>(g, f, j, x);
 }
 
-template <int DIM>
+template <int DIM, int BT>
 __global__ void __launch_bounds__(256) k_packed_residual(Dims g, FineOp<double> f, const double2* __restrict__ b,
                                                          const double2* __restrict__ x, double2* __restrict__ r) {
+  if (BT == 1 && resolve_uniform(g)) return;
+  if (BT == 2 && resolve(g, f)) return;
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  batch_shift(g.N, b, x, r);
+  if (BT) shift_nodes(g, b, x, r);
   r[j] = csub(b[j], packed_dot<DIM>(g, f, j, x));
 }
 
 void launch_packed_apply(const Dims& g, const FineOp<double>& f, const double2* x, double2* y, cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_packed_apply<2><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, x, y);
-  else count_launches(1), k_packed_apply<3><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, x, y);
+  const int bt = g.pd ? 2 : (g.B > 1 ? 1 : 0);
+  auto kern = g.dim == 2 ? (bt == 2 ? k_packed_apply<2, 2> : bt ? k_packed_apply<2, 1> : k_packed_apply<2, 0>)
+                         : (bt == 2 ? k_packed_apply<3, 2> : bt ? k_packed_apply<3, 1> : k_packed_apply<3, 0>);
+  count_launches(1), kern<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, x, y);
 }
 void launch_packed_residual(const Dims& g, const FineOp<double>& f, const double2* b, const double2* x, double2* r,
                             cudaStream_t st) {
-  if (g.dim == 2) count_launches(1), k_packed_residual<2><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, b, x, r);
-  else count_launches(1), k_packed_residual<3><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, b, x, r);
+  const int bt = g.pd ? 2 : (g.B > 1 ? 1 : 0);
+  auto kern = g.dim == 2 ? (bt == 2 ? k_packed_residual<2, 2> : bt ? k_packed_residual<2, 1> : k_packed_residual<2, 0>)
+                         : (bt == 2 ? k_packed_residual<3, 2> : bt ? k_packed_residual<3, 1> : k_packed_residual<3, 0>);
+  count_launches(1), kern<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, b, x, r);
+}
+
+// ---------------------------------------------------------------------------
+// The outer float64 operator applied to a vector whose entries are float32
+// values (the float32 cycle's output z_j), in double-float arithmetic.
+//
+// The float64 pipe of this GPU is far slower than the float32 one, and every
+// product of a float64 coefficient c with a float32 x is recovered exactly by
+// float32 error-free transformations: c = c_hi + c_lo (float32 pair, split at
+// setup, |c - c_hi - c_lo| <= 2^-48 |c|), c_hi x = p + e exactly (the FMA
+// two-product: p = fl(c_hi x), e = fma(c_hi, x, -p)), and the sums of the p
+// are kept exactly as (s, t) by Knuth's two-sum while the small terms
+// e + c_lo x gather in a float32 tail.  The row sum is then good to about
+// 2^-46 of its largest term (float64: 2^-53), within rounding of the float64
+// kernel for the outer Krylov iteration, which recomputes its residual
+// explicitly in float64 at every restart.
+// ---------------------------------------------------------------------------
+struct DfSum { float s, t; };
+
+__device__ __forceinline__ void df_add_prod(DfSum& a, float c_hi, float c_lo, float x) {
+  const float p = __fmul_rn(c_hi, x);
+  float e = __fmaf_rn(c_hi, x, -p);
+  e = __fmaf_rn(c_lo, x, e);
+  const float s = __fadd_rn(a.s, p);                     // two-sum: s + u = a.s + p exactly
+  const float bb = __fsub_rn(s, a.s);
+  const float u = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  a.s = s;
+  a.t = __fadd_rn(a.t, __fadd_rn(u, e));
+}
+__device__ __forceinline__ double df_value(const DfSum& a, const DfSum& b) {
+  return ((double)a.s + (double)b.s) + ((double)a.t + (double)b.t);
+}
+
+template <int DIM, int BT>
+__global__ void __launch_bounds__(256) k_packed_apply_df(Dims g, FineOp<double> f, const float2* __restrict__ pk2,
+                                                         DfLaplacian lap, const float2* __restrict__ x,
+                                                         double2* __restrict__ y) {
+  if (BT == 1 && resolve_uniform(g)) return;
+  if (BT == 2 && resolve(g, f)) return;
+  if (BT == 2)   // the problem's own spacing
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      lap.hi[d] = (float)f.ih2[d];
+      lap.lo[d] = (float)(f.ih2[d] - (double)lap.hi[d]);
+    }
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  if (BT) shift_nodes(g, x, y);
+  int ii[3];
+  unravel(g, j, ii[0], ii[1], ii[2]);
+  if (j == f.dyn[blockIdx.y].src_index) {        // the source row (Eq. helmADR2), in float64
+    double2 c[1 + 4 * DIM];
+    fine_row<DIM, double>(g, f, j, ii, c);
+    const float2 x0 = __ldg(x + j);
+    double2 acc = cmul(c[0], make_double2(x0.x, x0.y));
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int64_t st = axis_stride<DIM>(g, d);
+      const int k = ii[d], n = g.n[d];
+      const int64_t nb[4] = {k >= 1 ? j - st : j, k <= n - 2 ? j + st : j, k >= 2 ? j - 2 * st : j,
+                             k <= n - 3 ? j + 2 * st : j};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 xv = __ldg(x + nb[q]);
+        acc = cfma(c[1 + 4 * d + q], make_double2(xv.x, xv.y), acc);
+      }
+    }
+    y[j] = acc;
+    return;
+  }
+  const float2* pk = pk2 + (int64_t)(2 + 4 * DIM) * g.off + j;
+  const float2 xj = __ldg(x + j);
+  const float2 cr = __ldg(pk), ci = __ldg(pk + g.N);
+  DfSum ar{0.f, 0.f}, ai{0.f, 0.f}, br{0.f, 0.f}, bi{0.f, 0.f};
+  df_add_prod(ar, cr.x, cr.y, xj.x);
+  df_add_prod(ar, -ci.x, -ci.y, xj.y);
+  df_add_prod(ai, cr.x, cr.y, xj.y);
+  df_add_prod(ai, ci.x, ci.y, xj.x);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int64_t s = axis_stride<DIM>(g, d);
+    const int k = ii[d], n = g.n[d];
+    const int64_t jm1 = k >= 1 ? j - s : j, jp1 = k <= n - 2 ? j + s : j;
+    const int64_t jm2 = k >= 2 ? j - 2 * s : j, jp2 = k <= n - 3 ? j + 2 * s : j;
+    // real parts of the +-1 entries: the Laplacian's 1/h^2, doubled on a face, zero off the grid
+    const float mh = k == 0 ? 0.f : (k == n - 1 ? 2.f * lap.hi[d] : lap.hi[d]);
+    const float ml = k == 0 ? 0.f : (k == n - 1 ? 2.f * lap.lo[d] : lap.lo[d]);
+    const float ph = k == n - 1 ? 0.f : (k == 0 ? 2.f * lap.hi[d] : lap.hi[d]);
+    const float pl = k == n - 1 ? 0.f : (k == 0 ? 2.f * lap.lo[d] : lap.lo[d]);
+    const float2 xm1 = __ldg(x + jm1), xp1 = __ldg(x + jp1), xm2 = __ldg(x + jm2), xp2 = __ldg(x + jp2);
+    const float2 bm1 = __ldg(pk + (int64_t)(2 + 4 * d + 0) * g.N), bp1 = __ldg(pk + (int64_t)(2 + 4 * d + 1) * g.N);
+    const float2 bm2 = __ldg(pk + (int64_t)(2 + 4 * d + 2) * g.N), bp2 = __ldg(pk + (int64_t)(2 + 4 * d + 3) * g.N);
+    df_add_prod(ar, mh, ml, xm1.x);
+    df_add_prod(ai, mh, ml, xm1.y);
+    df_add_prod(br, ph, pl, xp1.x);
+    df_add_prod(bi, ph, pl, xp1.y);
+    df_add_prod(ar, -bm1.x, -bm1.y, xm1.y);
+    df_add_prod(ai, bm1.x, bm1.y, xm1.x);
+    df_add_prod(br, -bp1.x, -bp1.y, xp1.y);
+    df_add_prod(bi, bp1.x, bp1.y, xp1.x);
+    df_add_prod(ar, -bm2.x, -bm2.y, xm2.y);
+    df_add_prod(ai, bm2.x, bm2.y, xm2.x);
+    df_add_prod(br, -bp2.x, -bp2.y, xp2.y);
+    df_add_prod(bi, bp2.x, bp2.y, xp2.x);
+  }
+  y[j] = make_double2(df_value(ar, br), df_value(ai, bi));
+}
+
+// Split of the float64 packed rows into float32 (hi, lo) pairs.
+__global__ void k_split_df(const double* __restrict__ src, float2* __restrict__ dst, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = src[i];
+  const float hi = __double2float_rn(v);
+  dst[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+DfLaplacian df_laplacian(const FineOp<double>& f) {
+  DfLaplacian l{};
+  for (int d = 0; d < 3; ++d) {
+    const double v = f.ih2[d];
+    l.hi[d] = (float)v;
+    l.lo[d] = (float)(v - (double)l.hi[d]);
+  }
+  return l;
+}
+void launch_split_df(const double* src, float2* dst, int64_t n, cudaStream_t st) {
+  count_launches(1), k_split_df<<<blocks_for(n, 256), 256, 0, st>>>(src, dst, n);
+}
+void launch_packed_apply_df(const Dims& g, const FineOp<double>& f, const float2* pk2, const float2* x, double2* y,
+                            cudaStream_t st) {
+  const DfLaplacian lap = df_laplacian(f);
+  const int bt = g.pd ? 2 : (g.B > 1 ? 1 : 0);
+  auto kern = g.dim == 2 ? (bt == 2 ? k_packed_apply_df<2, 2> : bt ? k_packed_apply_df<2, 1> : k_packed_apply_df<2, 0>)
+                         : (bt == 2 ? k_packed_apply_df<3, 2> : bt ? k_packed_apply_df<3, 1> : k_packed_apply_df<3, 0>);
+  count_launches(1), kern<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, pk2, lap, x, y);
 }
 
 void launch_fine_store_rows(const Dims& g, const FineOp<double>& f, double2* rows, cudaStream_t st) {
@@ -784,9 +965,10 @@ void launch_fine_store_rows(const Dims& g, const FineOp<float>& f, float2* rows,
 // when i + o is off the grid, where A has no row).
 template <int DIM, typename T>
 __global__ void k_rows_adjoint(Dims g, const C<T>* __restrict__ rows, C<T>* __restrict__ rowsT) {
+  if (resolve(g)) return;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
-  batch_shift((1 + 4 * DIM) * g.N, rows, rowsT);
+  shift_scaled(g, 1 + 4 * DIM, rows, rowsT);
   int ii[3];
   unravel(g, i, ii[0], ii[1], ii[2]);
   const C<T> c0 = rows[i];
@@ -820,10 +1002,11 @@ template void launch_rows_adjoint<double>(const Dims&, const double2*, double2*,
 // and the zero slots of off-grid neighbours are unchanged.
 template <int DIM, typename T>
 __global__ void k_rows_rescale(Dims g, C<T>* __restrict__ rows, const double2* __restrict__ phase) {
+  if (resolve(g)) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
-  batch_shift((1 + 4 * DIM) * g.N, rows);
-  batch_shift(g.N, phase);
+  shift_scaled(g, 1 + 4 * DIM, rows);
+  shift_nodes(g, phase);
   int ii[3];
   unravel(g, i, ii[0], ii[1], ii[2]);
   const double2 mi = phase[i];

@@ -36,34 +36,38 @@ int reduction_blocks(int64_t n, int values) {
 // that reduced nrm2->x (zero if the norm vanishes): no per-thread float64
 // square root or division.
 template <typename T>
-__global__ void k_scale_inv_norm(const C<T>* w, C<T>* out, const double2* __restrict__ nrm2, int64_t n) {
+__global__ void k_scale_inv_norm(const C<T>* w, C<T>* out, const double2* __restrict__ nrm2, Dims g) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  batch_shift(n, w, out);
+  shift_nodes(g, w, out);
   const T inv = (T)nrm2[blockIdx.y].y;
   out[e] = cscale(w[e], inv);
 }
 template <typename T>
-void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, int64_t n, cudaStream_t st, int B) {
-  count_launches(1), k_scale_inv_norm<T><<<dim3(blocks_for(n, 256), B), 256, 0, st>>>(w, out, nrm2, n);
+void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, const Dims& g, cudaStream_t st) {
+  count_launches(1), k_scale_inv_norm<T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(w, out, nrm2, g);
 }
 
 // out = w / |w| and z = dinv .* out (the next Jacobi-preconditioned direction)
 template <typename T>
 __global__ void k_scale_dinv(const C<T>* w, C<T>* out, const C<T>* __restrict__ dinv, C<T>* z,
-                             const double2* __restrict__ nrm2, int64_t n) {
+                             const double2* __restrict__ nrm2, Dims g) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  batch_shift(n, w, out, dinv, z);
+  shift_nodes(g, w, out, dinv, z);
   const T inv = (T)nrm2[blockIdx.y].y;
   const C<T> v = cscale(w[e], inv);
   out[e] = v;
   z[e] = cmul(dinv[e], v);
 }
 template <typename T>
-void launch_scale_dinv(const C<T>* w, C<T>* out, const C<T>* dinv, C<T>* z, const double2* nrm2, int64_t n,
-                       cudaStream_t st, int B) {
-  count_launches(1), k_scale_dinv<T><<<dim3(blocks_for(n, 256), B), 256, 0, st>>>(w, out, dinv, z, nrm2, n);
+void launch_scale_dinv(const C<T>* w, C<T>* out, const C<T>* dinv, C<T>* z, const double2* nrm2, const Dims& g,
+                       cudaStream_t st) {
+  count_launches(1), k_scale_dinv<T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(w, out, dinv, z, nrm2, g);
 }
 
 template <typename T>
@@ -176,11 +180,13 @@ __device__ __forceinline__ bool update_norm(const C<T>* __restrict__ V, int64_t 
 
 // pass 1: ha = V^H w
 template <typename T>
-__global__ void __launch_bounds__(256) k_cgs_pass1(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w, int64_t n,
+__global__ void __launch_bounds__(256) k_cgs_pass1(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w, Dims g,
                                                    KrylovScratch s) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[kMaxKrylov + 1];
-  batch_shift(n, V, w);
+  shift_nodes(g, V, w);
   s = scratch_at(s, blockIdx.y);
   block_dots<T>(V, ld, k, w, n, blk, sh);
   last_block_rt(k, blk, s.partial, s.ticket, s.ha, sh);
@@ -188,12 +194,14 @@ __global__ void __launch_bounds__(256) k_cgs_pass1(const C<T>* __restrict__ V, i
 
 // pass 2: w -= V ha ; hb = V^H w
 template <typename T>
-__global__ void __launch_bounds__(256) k_cgs_pass2(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+__global__ void __launch_bounds__(256) k_cgs_pass2(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, Dims g,
                                                    KrylovScratch s) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[kMaxKrylov + 1];
   __shared__ C<T> coef[kMaxKrylov + 1];
-  batch_shift(n, V, w);
+  shift_nodes(g, V, w);
   s = scratch_at(s, blockIdx.y);
   for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-s.ha[i].x), (T)(-s.ha[i].y));
   __syncthreads();
@@ -208,9 +216,11 @@ __global__ void __launch_bounds__(256) k_cgs_pass2(const C<T>* __restrict__ V, i
 
 // pass 3: w -= V hb ; |w|^2 ; Arnoldi column j and Givens rotation (last block)
 template <typename T>
-__global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+__global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, Dims g,
                                                    KrylovScratch s, ArnoldiState st, int j) {
-  batch_shift(n, V, w);
+  if (resolve(g)) return;
+  const int64_t n = g.N;
+  shift_nodes(g, V, w);
   s = scratch_at(s, blockIdx.y);
   if (update_norm<T>(V, ld, k, w, n, s.hb, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
     const double s2t = s.nrm2->x;
@@ -224,11 +234,13 @@ __global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, i
 // the decision in the last block.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cgs_dots_sel(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w,
-                                                      int64_t n, KrylovScratch s, ArnoldiState st, int j, int finish,
+                                                      Dims g, KrylovScratch s, ArnoldiState st, int j, int finish,
                                                       double eta2) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   __shared__ double2 sh[32 * 5];
   __shared__ double2 blk[kMaxKrylov + 2];
-  batch_shift(n, V, w);
+  shift_nodes(g, V, w);
   s = scratch_at(s, blockIdx.y);
   for (int c = 0; c < k; c += 4) {
     C<T> acc[5];
@@ -257,14 +269,16 @@ __global__ void __launch_bounds__(256) k_cgs_dots_sel(const C<T>* __restrict__ V
 // a problem agree, so the whole problem returns at once otherwise):
 // w -= V ha ; hb = V^H w and |w|^2 ; the column from ha + hb.
 template <typename T>
-__global__ void __launch_bounds__(256) k_cgs_reorth(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+__global__ void __launch_bounds__(256) k_cgs_reorth(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, Dims g,
                                                     KrylovScratch s, ArnoldiState st, int j, int finish) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   s = scratch_at(s, blockIdx.y);
   if (s.ha[k].y == 0.0) return;
   __shared__ double2 sh[32 * 5];
   __shared__ double2 blk[kMaxKrylov + 2];
   __shared__ C<T> coef[kMaxKrylov + 1];
-  batch_shift(n, V, w);
+  shift_nodes(g, V, w);
   for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)(-s.ha[i].x), (T)(-s.ha[i].y));
   __syncthreads();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -299,8 +313,10 @@ __global__ void __launch_bounds__(256) k_cgs_reorth(const C<T>* __restrict__ V, 
 // after a single pass (w still A z), hb after the second pass (w already
 // updated by ha).
 template <typename T>
-__global__ void k_cgs_next(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* __restrict__ w, int64_t n,
+__global__ void k_cgs_next(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* __restrict__ w, Dims g,
                            KrylovScratch s, C<T>* __restrict__ Vnext, const C<T>* __restrict__ dinv, C<T>* __restrict__ z) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   __shared__ C<T> coef[kMaxKrylov + 1];
   __shared__ T s_inv;
   s = scratch_at(s, blockIdx.y);
@@ -310,7 +326,7 @@ __global__ void k_cgs_next(const C<T>* __restrict__ V, int64_t ld, int k, const 
   __syncthreads();
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  batch_shift(n, V, w, Vnext, dinv, z);
+  shift_nodes(g, V, w, Vnext, dinv, z);
   C<T> acc = w[e];
   for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
   const C<T> v = cscale(acc, s_inv);
@@ -321,14 +337,16 @@ __global__ void k_cgs_next(const C<T>* __restrict__ V, int64_t ld, int k, const 
 // x = dinv .* sum_{i<k} V_i y_i
 template <typename T>
 __global__ void k_combine_dinv(C<T>* x, const C<T>* __restrict__ V, int64_t ld, int k, ArnoldiState st,
-                               const C<T>* __restrict__ dinv, int64_t n) {
+                               const C<T>* __restrict__ dinv, Dims g) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   __shared__ C<T> coef[kMaxKrylov];
   const ArnoldiState a = arnoldi_at(st, blockIdx.y);
   for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)a.y[i].x, (T)a.y[i].y);
   __syncthreads();
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  batch_shift(n, x, V, dinv);
+  shift_nodes(g, x, V, dinv);
   C<T> acc = czero<T>();
   for (int i = 0; i < k; ++i) acc = cfma(V[(int64_t)i * ld + e], coef[i], acc);
   x[e] = cmul(dinv[e], acc);
@@ -346,10 +364,12 @@ __global__ void k_combine_dinv(C<T>* x, const C<T>* __restrict__ V, int64_t ld, 
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_sgs_dots_norm(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w,
-                                                       int64_t n, KrylovScratch s) {
+                                                       Dims g, KrylovScratch s) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   __shared__ double2 sh[32 * 5];
   __shared__ double2 blk[kMaxKrylov + 2];
-  batch_shift(n, V, w);
+  shift_nodes(g, V, w);
   s = scratch_at(s, blockIdx.y);
   for (int c = 0; c < k; c += 4) {
     C<T> acc[5];
@@ -374,9 +394,11 @@ __global__ void __launch_bounds__(256) k_sgs_dots_norm(const C<T>* __restrict__ 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_sgs_update_test(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+__global__ void __launch_bounds__(256) k_sgs_update_test(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, Dims g,
                                                          KrylovScratch s, ArnoldiState st, int j, double eta2) {
-  batch_shift(n, V, w);
+  if (resolve(g)) return;
+  const int64_t n = g.N;
+  shift_nodes(g, V, w);
   s = scratch_at(s, blockIdx.y);
   if (update_norm<T>(V, ld, k, w, n, s.ha, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
     const double t = s.nrm2->x;
@@ -393,22 +415,26 @@ __global__ void __launch_bounds__(256) k_sgs_update_test(const C<T>* __restrict_
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sgs_reorth_dots(const C<T>* __restrict__ V, int64_t ld, int k, const C<T>* w,
-                                                         int64_t n, KrylovScratch s) {
+                                                         Dims g, KrylovScratch s) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   s = scratch_at(s, blockIdx.y);
   if (s.ha[k].y == 0.0) return;   // uniform over the problem's blocks
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[kMaxKrylov + 1];
-  batch_shift(n, V, w);
+  shift_nodes(g, V, w);
   block_dots<T>(V, ld, k, w, n, blk, sh);
   last_block_rt(k, blk, s.partial, s.ticket, s.hb, sh);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_sgs_reorth_update(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, int64_t n,
+__global__ void __launch_bounds__(256) k_sgs_reorth_update(const C<T>* __restrict__ V, int64_t ld, int k, C<T>* w, Dims g,
                                                            KrylovScratch s, ArnoldiState st, int j) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   s = scratch_at(s, blockIdx.y);
   if (s.ha[k].y == 0.0) return;   // uniform over the problem's blocks
-  batch_shift(n, V, w);
+  shift_nodes(g, V, w);
   if (update_norm<T>(V, ld, k, w, n, s.hb, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
     const double s2t = s.nrm2->x;
     s.nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
@@ -418,11 +444,13 @@ __global__ void __launch_bounds__(256) k_sgs_reorth_update(const C<T>* __restric
 
 // |b|^2 and (optionally) the start of an Arnoldi cycle with beta = |b|.
 template <typename T>
-__global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, KrylovScratch s, ArnoldiState st, int start,
+__global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, Dims g, KrylovScratch s, ArnoldiState st, int start,
                                                     double rel_target) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   __shared__ double2 sh[32 * 4];
   __shared__ double2 blk[1];
-  batch_shift(n, b);
+  shift_nodes(g, b);
   s = scratch_at(s, blockIdx.y);
   C<T> s2[1] = {czero<T>()};
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -452,14 +480,16 @@ __global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, int64_t n, Kr
 
 // x = (assign ? 0 : x) + sum_i Z_i y_i  (y from the state, i < k)
 template <typename T>
-__global__ void k_combine(C<T>* x, const C<T>* __restrict__ Z, int64_t ld, int k, ArnoldiState st, int assign, int64_t n) {
+__global__ void k_combine(C<T>* x, const C<T>* __restrict__ Z, int64_t ld, int k, ArnoldiState st, int assign, Dims g) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   __shared__ C<T> coef[kMaxKrylov];
   const ArnoldiState a = arnoldi_at(st, blockIdx.y);
   for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = mk<T>((T)a.y[i].x, (T)a.y[i].y);
   __syncthreads();
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  batch_shift(n, x, Z);
+  shift_nodes(g, x, Z);
   C<T> acc = assign ? czero<T>() : x[e];
   for (int i = 0; i < k; ++i) acc = cfma(Z[(int64_t)i * ld + e], coef[i], acc);
   x[e] = acc;
@@ -469,11 +499,13 @@ __global__ void k_combine(C<T>* x, const C<T>* __restrict__ Z, int64_t ld, int k
 template <typename T>
 __global__ void k_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst,
                              const C<T>* __restrict__ w, const double2* __restrict__ alpha, const C<T>* __restrict__ dinv,
-                             C<T>* znext, int x_zero, int64_t n) {
+                             C<T>* znext, int x_zero, Dims g) {
+  if (resolve(g)) return;
+  const int64_t n = g.N;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  batch_shift(n, x, z, r_src, r_dst, w, dinv);
-  batch_shift_opt(n, znext);
+  shift_nodes(g, x, z, r_src, r_dst, w, dinv);
+  shift_nodes_opt(g, znext);
   const double2 ad = alpha[blockIdx.y];
   const C<T> al = mk<T>((T)ad.x, (T)ad.y);
   x[e] = cfma(al, z[e], x_zero ? czero<T>() : x[e]);
@@ -483,90 +515,90 @@ __global__ void k_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_
 }
 
 template <typename T>
-void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s, const ArnoldiState& st, int j,
-                 cudaStream_t stream, int B) {
-  const dim3 grid(reduction_blocks(n, k + 2), B);
-  count_launches(1), k_cgs_pass1<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
-  count_launches(1), k_cgs_pass2<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
-  count_launches(1), k_cgs_pass3<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j);
+void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, const Dims& g, const KrylovScratch& s, const ArnoldiState& st, int j,
+                 cudaStream_t stream) {
+  const dim3 grid(reduction_blocks(g.N, k + 2), g.B);
+  count_launches(1), k_cgs_pass1<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s);
+  count_launches(1), k_cgs_pass2<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s);
+  count_launches(1), k_cgs_pass3<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s, st, j);
 }
 template <typename T>
-void launch_cgs_dots_sel(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, const KrylovScratch& s,
-                         const ArnoldiState& st, int j, int finish, double eta, cudaStream_t stream, int B) {
-  const dim3 grid(reduction_blocks(n, k + 2), B);
-  count_launches(1), k_cgs_dots_sel<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j, finish, eta * eta);
+void launch_cgs_dots_sel(const C<T>* V, int64_t ld, int k, const C<T>* w, const Dims& g, const KrylovScratch& s,
+                         const ArnoldiState& st, int j, int finish, double eta, cudaStream_t stream) {
+  const dim3 grid(reduction_blocks(g.N, k + 2), g.B);
+  count_launches(1), k_cgs_dots_sel<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s, st, j, finish, eta * eta);
 }
 template <typename T>
-void launch_cgs_reorth(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
-                       const ArnoldiState& st, int j, int finish, cudaStream_t stream, int B) {
-  const dim3 grid(reduction_blocks(n, k + 2), B);
-  count_launches(1), k_cgs_reorth<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j, finish);
+void launch_cgs_reorth(const C<T>* V, int64_t ld, int k, C<T>* w, const Dims& g, const KrylovScratch& s,
+                       const ArnoldiState& st, int j, int finish, cudaStream_t stream) {
+  const dim3 grid(reduction_blocks(g.N, k + 2), g.B);
+  count_launches(1), k_cgs_reorth<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s, st, j, finish);
 }
 template <typename T>
-void launch_cgs_next(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, const KrylovScratch& s, C<T>* Vnext,
-                     const C<T>* dinv, C<T>* z, cudaStream_t stream, int B) {
-  count_launches(1), k_cgs_next<T><<<dim3(blocks_for(n, 256), B), 256, 0, stream>>>(V, ld, k, w, n, s, Vnext, dinv, z);
+void launch_cgs_next(const C<T>* V, int64_t ld, int k, const C<T>* w, const Dims& g, const KrylovScratch& s, C<T>* Vnext,
+                     const C<T>* dinv, C<T>* z, cudaStream_t stream) {
+  count_launches(1), k_cgs_next<T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, stream>>>(V, ld, k, w, g, s, Vnext, dinv, z);
 }
 template <typename T>
-void launch_combine_dinv(C<T>* x, const C<T>* V, int64_t ld, int k, const ArnoldiState& st, const C<T>* dinv, int64_t n,
-                         cudaStream_t stream, int B) {
-  count_launches(1), k_combine_dinv<T><<<dim3(blocks_for(n, 256), B), 256, 0, stream>>>(x, V, ld, k, st, dinv, n);
+void launch_combine_dinv(C<T>* x, const C<T>* V, int64_t ld, int k, const ArnoldiState& st, const C<T>* dinv, const Dims& g,
+                         cudaStream_t stream) {
+  count_launches(1), k_combine_dinv<T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, stream>>>(x, V, ld, k, st, dinv, g);
 }
 template <typename T>
-void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
-                          const ArnoldiState& st, int j, double eta, cudaStream_t stream, int B) {
+void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, const Dims& g, const KrylovScratch& s,
+                          const ArnoldiState& st, int j, double eta, cudaStream_t stream) {
   if (!(eta < 1.0)) {
-    launch_cgs2<T>(V, ld, k, w, n, s, st, j, stream, B);
+    launch_cgs2<T>(V, ld, k, w, g, s, st, j, stream);
     return;
   }
-  const dim3 grid(reduction_blocks(n, k + 2), B);
-  count_launches(1), k_sgs_dots_norm<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
-  count_launches(1), k_sgs_update_test<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j, eta * eta);
-  count_launches(1), k_sgs_reorth_dots<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s);
-  count_launches(1), k_sgs_reorth_update<T><<<grid, 256, 0, stream>>>(V, ld, k, w, n, s, st, j);
+  const dim3 grid(reduction_blocks(g.N, k + 2), g.B);
+  count_launches(1), k_sgs_dots_norm<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s);
+  count_launches(1), k_sgs_update_test<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s, st, j, eta * eta);
+  count_launches(1), k_sgs_reorth_dots<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s);
+  count_launches(1), k_sgs_reorth_update<T><<<grid, 256, 0, stream>>>(V, ld, k, w, g, s, st, j);
 }
 template <typename T>
-void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream, int B,
+void launch_norm_start(const C<T>* b, const Dims& g, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream,
                        double rel_target) {
   ArnoldiState dummy{};
-  count_launches(1), k_norm_start<T><<<dim3(reduction_blocks(n, 1), B), 256, 0, stream>>>(b, n, s, st ? *st : dummy,
+  count_launches(1), k_norm_start<T><<<dim3(reduction_blocks(g.N, 1), g.B), 256, 0, stream>>>(b, g, s, st ? *st : dummy,
                                                                                         st ? 1 : 0, rel_target);
 }
 template <typename T>
-void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n,
-                    cudaStream_t stream, int B) {
-  count_launches(1), k_combine<T><<<dim3(blocks_for(n, 256), B), 256, 0, stream>>>(x, Z, ld, k, st, assign ? 1 : 0, n);
+void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, const Dims& g,
+                    cudaStream_t stream) {
+  count_launches(1), k_combine<T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, stream>>>(x, Z, ld, k, st, assign ? 1 : 0, g);
 }
 template <typename T>
 void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, const C<T>* w, const double2* alpha,
-                       const C<T>* dinv, C<T>* znext, bool x_zero, int64_t n, cudaStream_t stream, int B) {
-  count_launches(1), k_mr_update2<T><<<dim3(blocks_for(n, 256), B), 256, 0, stream>>>(x, z, r_src, r_dst, w, alpha, dinv,
-                                                                                       znext, x_zero ? 1 : 0, n);
+                       const C<T>* dinv, C<T>* znext, bool x_zero, const Dims& g, cudaStream_t stream) {
+  count_launches(1), k_mr_update2<T><<<dim3(blocks_for(g.N, 256), g.B), 256, 0, stream>>>(x, z, r_src, r_dst, w, alpha, dinv,
+                                                                                       znext, x_zero ? 1 : 0, g);
 }
 
 #define ADR_INSTANTIATE_KRYLOV(T)                                                                                        \
-  template void launch_scale_inv_norm<T>(const C<T>*, C<T>*, const double2*, int64_t, cudaStream_t, int);               \
-  template void launch_scale_dinv<T>(const C<T>*, C<T>*, const C<T>*, C<T>*, const double2*, int64_t, cudaStream_t, int); \
+  template void launch_scale_inv_norm<T>(const C<T>*, C<T>*, const double2*, const Dims&, cudaStream_t);               \
+  template void launch_scale_dinv<T>(const C<T>*, C<T>*, const C<T>*, C<T>*, const double2*, const Dims&, cudaStream_t); \
   template void launch_copy<T>(const C<T>*, C<T>*, int64_t, cudaStream_t);                                               \
   template void launch_zero<T>(C<T>*, int64_t, cudaStream_t);                                                            \
   template void launch_cmul_vec<T>(const C<T>*, const C<T>*, C<T>*, int64_t, cudaStream_t);                              \
-  template void launch_cgs2<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, int, \
-                               cudaStream_t, int);                                                                       \
-  template void launch_cgs_selective<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&,                 \
-                                        const ArnoldiState&, int, double, cudaStream_t, int);                            \
-  template void launch_norm_start<T>(const C<T>*, int64_t, const KrylovScratch&, const ArnoldiState*, cudaStream_t, int,  \
+  template void launch_cgs2<T>(const C<T>*, int64_t, int, C<T>*, const Dims&, const KrylovScratch&, const ArnoldiState&, int, \
+                               cudaStream_t);                                                                       \
+  template void launch_cgs_selective<T>(const C<T>*, int64_t, int, C<T>*, const Dims&, const KrylovScratch&,                 \
+                                        const ArnoldiState&, int, double, cudaStream_t);                            \
+  template void launch_norm_start<T>(const C<T>*, const Dims&, const KrylovScratch&, const ArnoldiState*, cudaStream_t,   \
                                      double);                                                                            \
-  template void launch_cgs_dots_sel<T>(const C<T>*, int64_t, int, const C<T>*, int64_t, const KrylovScratch&,           \
-                                       const ArnoldiState&, int, int, double, cudaStream_t, int);                        \
-  template void launch_cgs_reorth<T>(const C<T>*, int64_t, int, C<T>*, int64_t, const KrylovScratch&, const ArnoldiState&, \
-                                     int, int, cudaStream_t, int);                                                       \
-  template void launch_cgs_next<T>(const C<T>*, int64_t, int, const C<T>*, int64_t, const KrylovScratch&, C<T>*,         \
-                                   const C<T>*, C<T>*, cudaStream_t, int);                                               \
-  template void launch_combine_dinv<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, const C<T>*, int64_t,      \
-                                       cudaStream_t, int);                                                               \
-  template void launch_combine<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, bool, int64_t, cudaStream_t, int); \
+  template void launch_cgs_dots_sel<T>(const C<T>*, int64_t, int, const C<T>*, const Dims&, const KrylovScratch&,           \
+                                       const ArnoldiState&, int, int, double, cudaStream_t);                        \
+  template void launch_cgs_reorth<T>(const C<T>*, int64_t, int, C<T>*, const Dims&, const KrylovScratch&, const ArnoldiState&, \
+                                     int, int, cudaStream_t);                                                       \
+  template void launch_cgs_next<T>(const C<T>*, int64_t, int, const C<T>*, const Dims&, const KrylovScratch&, C<T>*,         \
+                                   const C<T>*, C<T>*, cudaStream_t);                                               \
+  template void launch_combine_dinv<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, const C<T>*, const Dims&, \
+                                       cudaStream_t);                                                               \
+  template void launch_combine<T>(C<T>*, const C<T>*, int64_t, int, const ArnoldiState&, bool, const Dims&, cudaStream_t); \
   template void launch_mr_update2<T>(C<T>*, const C<T>*, const C<T>*, C<T>*, const C<T>*, const double2*, const C<T>*,    \
-                                     C<T>*, bool, int64_t, cudaStream_t, int);
+                                     C<T>*, bool, const Dims&, cudaStream_t);
 ADR_INSTANTIATE_KRYLOV(double)
 ADR_INSTANTIATE_KRYLOV(float)
 template void launch_ccast<double, float>(const C<double>*, C<float>*, int64_t, cudaStream_t);

@@ -77,13 +77,13 @@ __host__ __device__ inline KrylovScratch scratch_at(KrylovScratch s, int pb) {
 // CGS2 step j: w <- w - V (V^H w) twice, |w|^2, Arnoldi column j and Givens
 // rotation in st (three launches).
 template <typename T>
-void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s, const ArnoldiState& st, int j,
-                 cudaStream_t stream, int B = 1);
+void launch_cgs2(const C<T>* V, int64_t ld, int k, C<T>* w, const Dims& g, const KrylovScratch& s, const ArnoldiState& st, int j,
+                 cudaStream_t stream);
 // Gram-Schmidt step j with the second pass only when the first one cancelled
 // |w| below eta |w| (four launches; eta >= 1 is launch_cgs2).
 template <typename T>
-void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
-                          const ArnoldiState& st, int j, double eta, cudaStream_t stream, int B = 1);
+void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, const Dims& g, const KrylovScratch& s,
+                          const ArnoldiState& st, int j, double eta, cudaStream_t stream);
 // The Jacobi-preconditioned GMRES step of the coarsest grid with the
 // selective second Gram-Schmidt pass (at most three launches; the column's
 // norm from Pythagoras, see coarse_select_dev / coarse_reorth_dev):
@@ -94,14 +94,14 @@ void launch_cgs_selective(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, 
 //   launch_cgs_next: V_next = (w - V c) / h_{j+1,j}, z = dinv .* V_next.
 // finish > 0 on the last step: the least-squares solve over `finish` columns.
 template <typename T>
-void launch_cgs_dots_sel(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, const KrylovScratch& s,
-                         const ArnoldiState& st, int j, int finish, double eta, cudaStream_t stream, int B = 1);
+void launch_cgs_dots_sel(const C<T>* V, int64_t ld, int k, const C<T>* w, const Dims& g, const KrylovScratch& s,
+                         const ArnoldiState& st, int j, int finish, double eta, cudaStream_t stream);
 template <typename T>
-void launch_cgs_reorth(const C<T>* V, int64_t ld, int k, C<T>* w, int64_t n, const KrylovScratch& s,
-                       const ArnoldiState& st, int j, int finish, cudaStream_t stream, int B = 1);
+void launch_cgs_reorth(const C<T>* V, int64_t ld, int k, C<T>* w, const Dims& g, const KrylovScratch& s,
+                       const ArnoldiState& st, int j, int finish, cudaStream_t stream);
 template <typename T>
-void launch_cgs_next(const C<T>* V, int64_t ld, int k, const C<T>* w, int64_t n, const KrylovScratch& s, C<T>* Vnext,
-                     const C<T>* dinv, C<T>* z, cudaStream_t stream, int B = 1);
+void launch_cgs_next(const C<T>* V, int64_t ld, int k, const C<T>* w, const Dims& g, const KrylovScratch& s, C<T>* Vnext,
+                     const C<T>* dinv, C<T>* z, cudaStream_t stream);
 // The coarsest step's apply w = A z fused with its first Gram-Schmidt pass
 // (float32 stencil levels, coefficient tiles streamed by bulk copies):
 // ha = V^H w over the kd <= 63 basis vectors V_i = V + i ld, |w|^2, and the
@@ -112,28 +112,26 @@ void launch_stencil_arnoldi_tma(const Dims& g, const float2* A, const float2* z,
                                 int* err, int blocks, int variant, cudaStream_t stream);
 // x = dinv .* sum_{i<k} V_i y_i (the coarsest solution from its basis).
 template <typename T>
-void launch_combine_dinv(C<T>* x, const C<T>* V, int64_t ld, int k, const ArnoldiState& st, const C<T>* dinv, int64_t n,
-                         cudaStream_t stream, int B = 1);
+void launch_combine_dinv(C<T>* x, const C<T>* V, int64_t ld, int k, const ArnoldiState& st, const C<T>* dinv, const Dims& g,
+                         cudaStream_t stream);
 // |b|^2 into s.nrm2; with st, also starts an Arnoldi cycle with beta = |b|
 // (rel_target >= 0: the cycle's convergence target becomes rel_target * beta;
 // < 0: the stored target is kept).
 template <typename T>
-void launch_norm_start(const C<T>* b, int64_t n, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream,
-                       int B = 1, double rel_target = -1.0);
+void launch_norm_start(const C<T>* b, const Dims& g, const KrylovScratch& s, const ArnoldiState* st, cudaStream_t stream, double rel_target = -1.0);
 // x = (assign ? 0 : x) + sum_{i<k} Z_i y_i with y from st.
 template <typename T>
-void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, int64_t n,
-                    cudaStream_t stream, int B = 1);
+void launch_combine(C<T>* x, const C<T>* Z, int64_t ld, int k, const ArnoldiState& st, bool assign, const Dims& g,
+                    cudaStream_t stream);
 // x = (x_zero ? 0 : x) + alpha z ; r_dst = r_src - alpha w ; znext = dinv .* r_dst (if not null)
 template <typename T>
 void launch_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_dst, const C<T>* w, const double2* alpha,
-                       const C<T>* dinv, C<T>* znext, bool x_zero, int64_t n, cudaStream_t stream, int B = 1);
+                       const C<T>* dinv, C<T>* znext, bool x_zero, const Dims& g, cudaStream_t stream);
 // out = w * (1 / |w|) with the reciprocal norm from s.nrm2 (per problem).
-template <typename T> void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, int64_t n, cudaStream_t st,
-                                                 int B = 1);
+template <typename T> void launch_scale_inv_norm(const C<T>* w, C<T>* out, const double2* nrm2, const Dims& g, cudaStream_t st);
 // out = w * (1 / |w|) and z = dinv .* out (per problem).
 template <typename T> void launch_scale_dinv(const C<T>* w, C<T>* out, const C<T>* dinv, C<T>* z, const double2* nrm2,
-                                             int64_t n, cudaStream_t st, int B = 1);
+                                             const Dims& g, cudaStream_t st);
 // Whole-array elementwise operations (n = all problems' entries).
 template <typename T> void launch_copy(const C<T>* a, C<T>* b, int64_t n, cudaStream_t st);
 template <typename T> void launch_zero(C<T>* a, int64_t n, cudaStream_t st);

@@ -19,6 +19,7 @@ BAD_PARAMS = [
     ("coarse_solver", 99, "coarse_solver"), ("tma", 3, "tma"),
     ("scheme", 3, "scheme"), ("prec_scheme", 9, "prec_scheme"), ("rescale", 2, "rescale"),
     ("kcycle_threshold", -0.1, "kcycle_threshold"), ("kcycle_threshold", float("nan"), "kcycle_threshold"),
+    ("outer_df", 2, "outer_df"),
 ]
 
 

@@ -155,6 +155,28 @@ def test_kcycle_early_exit_f64(adrlib, cuda, name, threshold):
     assert rel(a.cpu().numpy(), x) <= 1e-10, rel(a.cpu().numpy(), x)
 
 
+@pytest.mark.parametrize("name", ["marine2d_65", "layered3d_17", "corner3d_9x11x13", "const3d_49x49x25"])
+def test_double_float_outer_apply(adrlib, cuda, name):
+    """With a float32 cycle the outer A z_j sums in double-float arithmetic on
+    the float32 pipe (params.outer_df).  The two applies differ at rounding
+    level (2^-46 of a row's largest term against 2^-53); the float32 cycle
+    turns such differences into float32-level ones now and then (a float64
+    input within rounding of a float32 tie rounds the other way), so fixed-count
+    iterates agree to the float32 cycle's precision (measured 4e-9 on the 65^2
+    marine case), a wrong term would show at O(1).  A solve to 1e-10 reaches
+    its explicit float64 residual in the same number of iterations and the
+    two solutions agree to the solve's accuracy."""
+    P, _, op_df = make_operator(name, precision="f32", levels=3, outer_df=1)
+    _, _, op_64 = make_operator(name, precision="f32", levels=3, outer_df=0)
+    a1, _ = op_df.solve(tol=0.0, maxit=12, raise_on_fail=False)
+    a0, _ = op_64.solve(tol=0.0, maxit=12, raise_on_fail=False)
+    assert rel(a1.cpu().numpy(), a0.cpu().numpy()) <= 1e-6, rel(a1.cpu().numpy(), a0.cpu().numpy())
+    b1, i1 = op_df.solve(tol=1e-10, maxit=400)
+    b0, i0 = op_64.solve(tol=1e-10, maxit=400)
+    assert i1["rel_residual"] <= 1e-10 and abs(i1["iterations"] - i0["iterations"]) <= 1
+    assert rel(b1.cpu().numpy(), b0.cpu().numpy()) <= 1e-8
+
+
 @pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17"])
 def test_cycle_f32(adrlib, cuda, name):
     P, params, op = make_operator(name, precision="f32")
