@@ -148,11 +148,15 @@ typedef struct adr_params {
                                           0 (default): the fixed kcycle_iterations steps.
                                           0..1e6 */
   int outer_df;                        /* 1 (default): with a float32 cycle (not
-                                          rescaled) the outer iteration's A z_j reads
-                                          z_j as float32 values and sums exact products
-                                          in double-float arithmetic (float32 pipe;
-                                          about 2^-46 of the row's largest term); 0: the
-                                          float64 apply.  Residuals stay float64 */
+                                          rescaled) and adjoint = 0, the outer
+                                          iteration runs in double-float arithmetic
+                                          (pairs of float32 values, float32 pipe; about
+                                          2^-46 relative per operation against
+                                          float64's 2^-53): A z_j on the float32 z_j,
+                                          the Gram-Schmidt passes, the normalisation and
+                                          x += Z y.  The solution, the Hessenberg
+                                          matrix and the residual at every restart stay
+                                          float64.  0: all outer work in float64 */
 } adr_params_t;
 
 #define ADR_COARSE_AUTO 0      /* cluster up to 32768 nodes, else one block up to 8192, else kernels */

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libadr.so")
-SOURCES = ["fine.cu", "coarse.cu", "coarse_cluster.cu", "krylov.cu", "api.cu", "eikonal.cu", "adjoint.cu", "coarse_grid.cu", "coarse_tma.cu"]
+SOURCES = ["fine.cu", "coarse.cu", "coarse_cluster.cu", "krylov.cu", "krylov_df.cu", "api.cu", "eikonal.cu", "adjoint.cu", "coarse_grid.cu", "coarse_tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--extended-lambda", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -487,11 +487,13 @@ int set_last_error(int code, const char* msg);
 
 // The outer float64 operator on a vector of float32 values in double-float
 // arithmetic (see fine.cu): pk2 are the packed rows split into float32
-// (hi, lo) pairs by launch_split_df (n reals).
+// (hi, lo) pairs by launch_split_df (n reals).  y = A x as double-float planes
+// (high parts at y, low parts at y + ylo); x is also copied to zcopy when
+// that is not null.
 struct DfLaplacian { float hi[3], lo[3]; };
 void launch_split_df(const double* src, float2* dst, int64_t n, cudaStream_t st);
-void launch_packed_apply_df(const Dims& g, const FineOp<double>& f, const float2* pk2, const float2* x, double2* y,
-                            cudaStream_t st);
+void launch_packed_apply_df(const Dims& g, const FineOp<double>& f, const float2* pk2, const float2* x, float2* y,
+                            int64_t ylo, float2* zcopy, cudaStream_t st);
 
 // Vector kernels.
 template <typename T> void launch_cmul_vec(const C<T>* a, const C<T>* b, C<T>* out, int64_t n, cudaStream_t st);  // out = a .* b

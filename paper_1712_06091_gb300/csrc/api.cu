@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "krylov.cuh"
+#include "krylov_df.cuh"
 #include "coarse_stencil.cuh"
 
 namespace adr {
@@ -373,6 +374,7 @@ template <typename T> static void plan_hierarchy(Op& op, Hier<T>& H, Arena& a) {
     const int64_t want = (Lc.g.N + 1023) / 1024;
     H.gs.nblk = (int)(want < per_problem ? want : per_problem);
     H.gs.part = a.take<double2>((size_t)2 * H.gs.nblk * (kGridMaxK + 1) * B);
+    H.gs.tot = a.take<double2>((size_t)(kGridMaxK + 1) * B);
     H.gs.bar = a.take<unsigned>(2 * B);
     H.gs.err = a.take<int>(B);
   }
@@ -1296,9 +1298,17 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
   const FineOp<double> fo = outer_op(op);
   auto outer_apply = [&](const double2* x, double2* y) {
     if (adj) launch_rows_apply(op.g0, op.rows_outT, x, y, st);
-    else if (op.packed_df) launch_packed_apply_df(op.g0, fo, op.packed_df, (const float2*)op.h32.lv[0].x, y, st);
     else launch_packed_apply(op.g0, fo, x, y, st);
   };
+  // The double-float outer iteration (params.outer_df with the float32
+  // cycle): basis vector j as two float32 planes at Vf + 2 j NB (low parts NB
+  // further), z_j as the cycle's float32 output at Zf + j NB, and the cycle's
+  // input written by the kernel that normalises the basis vector.  The
+  // solution and the restart residual stay float64.
+  const bool dfk = op.packed_df != nullptr && !adj;
+  float2* const Vf = (float2*)op.V;
+  float2* const Zf = (float2*)op.Z;
+  float2* const cyc = op.h32.lv[0].b;
   auto outer_residual = [&](const double2* bb, const double2* x, double2* r) {
     if (adj) launch_rows_residual(op.g0, op.rows_outT, bb, x, r, st);
     else launch_packed_residual(op.g0, fo, bb, x, r, st);
@@ -1336,20 +1346,31 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
     // op.ks.nrm2 holds |r|^2 and op.ost fresh cycles here
     for (int pb = 0; pb < B; ++pb) frozen[pb] = done[pb];
     ADR_TRY(upload_skip(op, frozen));
-    launch_scale_inv_norm<double>(op.r, op.V, op.ks.nrm2, op.g0, st);
+    if (dfk) launch_df_from_double(op.r, Vf, NB, op.ks.nrm2, cyc, op.g0, st);
+    else launch_scale_inv_norm<double>(op.r, op.V, op.ks.nrm2, op.g0, st);
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      double2* vj = op.V + (int64_t)j * NB;
-      double2* zj = op.Z + (int64_t)j * NB;
-      double2* w = op.V + (int64_t)(j + 1) * NB;  // A z_j, orthogonalised and normalised in place
-      ADR_TRY(precondition(op, vj, zj, adj));
-      {
-        const int pk = adj ? -1 : prof_begin(op, ADR_PROF_OUTER_APPLY, st);
-        outer_apply(zj, w);
+      if (dfk) {
+        float2* w = Vf + (int64_t)(j + 1) * 2 * NB;   // A z_j, orthogonalised and normalised in place
+        ADR_TRY(run_cycle(op, op.h32));
+        const int pk = prof_begin(op, ADR_PROF_OUTER_APPLY, st);
+        launch_packed_apply_df(op.g0, fo, op.packed_df, op.h32.lv[0].x, w, NB, Zf + (int64_t)j * NB, st);
         prof_end(op, pk, st);
+        launch_df_selective(Vf, 2 * NB, NB, j + 1, w, op.g0, op.ks, op.ost, j, op.p.reorth_eta, st);
+        launch_df_scale(w, NB, op.ks.nrm2, j + 1 < m ? cyc : nullptr, op.g0, st);
+      } else {
+        double2* vj = op.V + (int64_t)j * NB;
+        double2* zj = op.Z + (int64_t)j * NB;
+        double2* w = op.V + (int64_t)(j + 1) * NB;  // A z_j, orthogonalised and normalised in place
+        ADR_TRY(precondition(op, vj, zj, adj));
+        {
+          const int pk = adj ? -1 : prof_begin(op, ADR_PROF_OUTER_APPLY, st);
+          outer_apply(zj, w);
+          prof_end(op, pk, st);
+        }
+        launch_cgs_selective<double>(op.V, NB, j + 1, w, op.g0, op.ks, op.ost, j, op.p.reorth_eta, st);
+        launch_scale_inv_norm<double>(w, w, op.ks.nrm2, op.g0, st);
       }
-      launch_cgs_selective<double>(op.V, NB, j + 1, w, op.g0, op.ks, op.ost, j, op.p.reorth_eta, st);
-      launch_scale_inv_norm<double>(w, w, op.ks.nrm2, op.g0, st);
       ADR_TRY(check_launch("adr_solve iteration"));
       ADR_TRY(read_scalars(op, op.ost.scal, kNumScal * B));
       ++its;
@@ -1370,7 +1391,8 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
     if (nan) break;
     ADR_TRY(upload_skip(op, none));
     launch_backsolve(op.ost, k, st, B);
-    launch_combine<double>(a, op.Z, NB, k, op.ost, false, op.g0, st);
+    if (dfk) launch_df_combine(a, Zf, NB, k, op.ost, op.g0, st);
+    else launch_combine<double>(a, op.Z, NB, k, op.ost, false, op.g0, st);
     outer_residual(b, a, op.r);
     launch_norm_start<double>(op.r, op.g0, op.ks, &op.ost, st);
     ADR_TRY(read_scalars(op, (const double*)op.ks.nrm2, 2 * B));

@@ -12,6 +12,7 @@
 #include "adr_common.cuh"
 #include "coarse_stencil.cuh"
 #include "reduce.cuh"
+#include "df.cuh"
 
 namespace adr {
 
@@ -828,28 +829,14 @@ void launch_packed_residual(const Dims& g, const FineOp<double>& f, const double
 // e + c_lo x gather in a float32 tail.  The row sum is then good to about
 // 2^-46 of its largest term (float64: 2^-53), within rounding of the float64
 // kernel for the outer Krylov iteration, which recomputes its residual
-// explicitly in float64 at every restart.
+// explicitly in float64 at every restart.  The row sums are stored as
+// normalised double-float planes (the next basis vector of the double-float
+// outer iteration, krylov_df.cu), and x is copied out as z_j on the way.
 // ---------------------------------------------------------------------------
-struct DfSum { float s, t; };
-
-__device__ __forceinline__ void df_add_prod(DfSum& a, float c_hi, float c_lo, float x) {
-  const float p = __fmul_rn(c_hi, x);
-  float e = __fmaf_rn(c_hi, x, -p);
-  e = __fmaf_rn(c_lo, x, e);
-  const float s = __fadd_rn(a.s, p);                     // two-sum: s + u = a.s + p exactly
-  const float bb = __fsub_rn(s, a.s);
-  const float u = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  a.s = s;
-  a.t = __fadd_rn(a.t, __fadd_rn(u, e));
-}
-__device__ __forceinline__ double df_value(const DfSum& a, const DfSum& b) {
-  return ((double)a.s + (double)b.s) + ((double)a.t + (double)b.t);
-}
-
 template <int DIM, int BT>
 __global__ void __launch_bounds__(256) k_packed_apply_df(Dims g, FineOp<double> f, const float2* __restrict__ pk2,
                                                          DfLaplacian lap, const float2* __restrict__ x,
-                                                         double2* __restrict__ y) {
+                                                         float2* __restrict__ y, int64_t ylo, float2* __restrict__ zcopy) {
   if (BT == 1 && resolve_uniform(g)) return;
   if (BT == 2 && resolve(g, f)) return;
   if (BT == 2)   // the problem's own spacing
@@ -860,7 +847,10 @@ __global__ void __launch_bounds__(256) k_packed_apply_df(Dims g, FineOp<double> 
     }
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= g.N) return;
-  if (BT) shift_nodes(g, x, y);
+  if (BT) {
+    shift_nodes(g, x, y);
+    shift_nodes_opt(g, zcopy);
+  }
   int ii[3];
   unravel(g, j, ii[0], ii[1], ii[2]);
   if (j == f.dyn[blockIdx.y].src_index) {        // the source row (Eq. helmADR2), in float64
@@ -880,7 +870,10 @@ __global__ void __launch_bounds__(256) k_packed_apply_df(Dims g, FineOp<double> 
         acc = cfma(c[1 + 4 * d + q], make_double2(xv.x, xv.y), acc);
       }
     }
-    y[j] = acc;
+    const float2 r = df_split(acc.x), m = df_split(acc.y);
+    y[j] = make_float2(r.x, m.x);
+    y[j + ylo] = make_float2(r.y, m.y);
+    if (zcopy) zcopy[j] = x0;
     return;
   }
   const float2* pk = pk2 + (int64_t)(2 + 4 * DIM) * g.off + j;
@@ -918,7 +911,12 @@ __global__ void __launch_bounds__(256) k_packed_apply_df(Dims g, FineOp<double> 
     df_add_prod(br, -bp2.x, -bp2.y, xp2.y);
     df_add_prod(bi, bp2.x, bp2.y, xp2.x);
   }
-  y[j] = make_double2(df_value(ar, br), df_value(ai, bi));
+  df_add(ar, br);
+  df_add(ai, bi);
+  const float2 r = df_pair(ar), m = df_pair(ai);
+  y[j] = make_float2(r.x, m.x);
+  y[j + ylo] = make_float2(r.y, m.y);
+  if (zcopy) zcopy[j] = xj;
 }
 
 // Split of the float64 packed rows into float32 (hi, lo) pairs.
@@ -942,13 +940,13 @@ DfLaplacian df_laplacian(const FineOp<double>& f) {
 void launch_split_df(const double* src, float2* dst, int64_t n, cudaStream_t st) {
   count_launches(1), k_split_df<<<blocks_for(n, 256), 256, 0, st>>>(src, dst, n);
 }
-void launch_packed_apply_df(const Dims& g, const FineOp<double>& f, const float2* pk2, const float2* x, double2* y,
-                            cudaStream_t st) {
+void launch_packed_apply_df(const Dims& g, const FineOp<double>& f, const float2* pk2, const float2* x, float2* y,
+                            int64_t ylo, float2* zcopy, cudaStream_t st) {
   const DfLaplacian lap = df_laplacian(f);
   const int bt = g.pd ? 2 : (g.B > 1 ? 1 : 0);
   auto kern = g.dim == 2 ? (bt == 2 ? k_packed_apply_df<2, 2> : bt ? k_packed_apply_df<2, 1> : k_packed_apply_df<2, 0>)
                          : (bt == 2 ? k_packed_apply_df<3, 2> : bt ? k_packed_apply_df<3, 1> : k_packed_apply_df<3, 0>);
-  count_launches(1), kern<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, pk2, lap, x, y);
+  count_launches(1), kern<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(g, f, pk2, lap, x, y, ylo, zcopy);
 }
 
 void launch_fine_store_rows(const Dims& g, const FineOp<double>& f, double2* rows, cudaStream_t st) {

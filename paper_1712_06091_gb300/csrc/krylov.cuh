@@ -158,6 +158,7 @@ void launch_coarse_gmres_cluster(const Dims& g, const C<T>* A, const C<T>* dinv,
 constexpr int kGridMaxK = 32;
 struct GridScratch {
   double2* part;   // per problem: 2 x nblk x (kGridMaxK + 1) partial sums
+  double2* tot;    // per problem: kGridMaxK + 1 totals of the last reduction
   unsigned* bar;   // per problem: arrival count, generation
   int* err;        // per problem: barrier timeout flag (sticky)
   int nblk;        // blocks per problem

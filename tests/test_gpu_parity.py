@@ -155,25 +155,37 @@ def test_kcycle_early_exit_f64(adrlib, cuda, name, threshold):
     assert rel(a.cpu().numpy(), x) <= 1e-10, rel(a.cpu().numpy(), x)
 
 
-@pytest.mark.parametrize("name", ["marine2d_65", "layered3d_17", "corner3d_9x11x13", "const3d_49x49x25"])
-def test_double_float_outer_apply(adrlib, cuda, name):
-    """With a float32 cycle the outer A z_j sums in double-float arithmetic on
-    the float32 pipe (params.outer_df).  The two applies differ at rounding
-    level (2^-46 of a row's largest term against 2^-53); the float32 cycle
-    turns such differences into float32-level ones now and then (a float64
-    input within rounding of a float32 tie rounds the other way), so fixed-count
-    iterates agree to the float32 cycle's precision (measured 4e-9 on the 65^2
-    marine case), a wrong term would show at O(1).  A solve to 1e-10 reaches
-    its explicit float64 residual in the same number of iterations and the
-    two solutions agree to the solve's accuracy."""
-    P, _, op_df = make_operator(name, precision="f32", levels=3, outer_df=1)
-    _, _, op_64 = make_operator(name, precision="f32", levels=3, outer_df=0)
-    a1, _ = op_df.solve(tol=0.0, maxit=12, raise_on_fail=False)
-    a0, _ = op_64.solve(tol=0.0, maxit=12, raise_on_fail=False)
-    assert rel(a1.cpu().numpy(), a0.cpu().numpy()) <= 1e-6, rel(a1.cpu().numpy(), a0.cpu().numpy())
-    b1, i1 = op_df.solve(tol=1e-10, maxit=400)
-    b0, i0 = op_64.solve(tol=1e-10, maxit=400)
-    assert i1["rel_residual"] <= 1e-10 and abs(i1["iterations"] - i0["iterations"]) <= 1
+@pytest.mark.parametrize("name,restart,eta", [("marine2d_65", 8, 0.1), ("layered3d_17", 8, 0.1),
+                                              ("corner3d_9x11x13", 4, 0.0), ("const3d_49x49x25", 8, 0.1),
+                                              ("marine2d_65", 3, 2.0), ("layered3d_17", 5, 0.0)])
+def test_double_float_outer_iteration(adrlib, cuda, name, restart, eta):
+    """With a float32 cycle the outer iteration runs in double-float
+    arithmetic on the float32 pipe (params.outer_df): A z_j, the selective
+    Gram-Schmidt passes (never, selectively and always re-orthogonalised),
+    the normalisation and x += Z y over several restarts.  Each operation
+    differs from float64 at rounding level (2^-46 against 2^-53); the float32
+    cycle turns such differences into float32-level ones now and then (an
+    input within rounding of a float32 tie rounds the other way).  Within the
+    first restart cycle that is rare and the iterates agree closely; each
+    restart takes v_0 from the explicit residual, whose relative difference
+    grows as the residual falls, so after several restarts iterates agree to
+    the float32 cycle's precision only (measured 1.3e-6 after four restarts
+    of FGMRES(3) on the 65^2 marine case); a wrong term would show at O(1).
+    The precision check is the solve: to 1e-10 (where float32 arithmetic in
+    the Krylov passes would stall near 1e-7) it reaches its explicit float64
+    residual in the iterations of the float64 path (within one), and the two
+    solutions agree to the solve's accuracy."""
+    P, _, op_df = make_operator(name, precision="f32", levels=3, outer_df=1, restart=restart, reorth_eta=eta)
+    _, _, op_64 = make_operator(name, precision="f32", levels=3, outer_df=0, restart=restart, reorth_eta=eta)
+    for its, bound in ((restart, 1e-7), (12, 1e-5)):
+        a1, _ = op_df.solve(tol=0.0, maxit=its, raise_on_fail=False)
+        a0, _ = op_64.solve(tol=0.0, maxit=its, raise_on_fail=False)
+        d = rel(a1.cpu().numpy(), a0.cpu().numpy())
+        print(f"{name} FGMRES({restart}) eta {eta}: {its} iterations, iterates differ by {d:.2e}")
+        assert d <= bound, (its, d)
+    b1, i1 = op_df.solve(tol=1e-10, maxit=1000)
+    b0, i0 = op_64.solve(tol=1e-10, maxit=1000)
+    assert i1["rel_residual"] <= 1e-10 and abs(i1["iterations"] - i0["iterations"]) <= 1, (i1, i0)
     assert rel(b1.cpu().numpy(), b0.cpu().numpy()) <= 1e-8
 
 
