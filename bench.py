@@ -119,6 +119,9 @@ def parse():
     ap.add_argument("--restart", type=int, default=None)
     ap.add_argument("--coarse-solver", default=None, choices=["auto", "kernels", "cta", "cluster", "grid"],
                     help="form of the coarsest-grid GMRES (same arithmetic; default: the library's choice)")
+    ap.add_argument("--tma", type=int, default=None, choices=[0, 1, 2],
+                    help="stored-stencil applies: 1 bulk copies, 16 warps (library default); 2 bulk copies, 8 warps "
+                         "with two buffers; 0 plain loads")
     ap.add_argument("--cycle", default=None)
     ap.add_argument("--sweeps", default=None, help="comma-separated relaxations per level")
     ap.add_argument("--no-e2e", action="store_true")
@@ -160,6 +163,8 @@ def build_params(args, method=None):
         kw["cycle"] = args.cycle
     if args.coarse_solver:
         kw["coarse_solver"] = args.coarse_solver
+    if args.tma is not None:
+        kw["tma"] = args.tma
     if args.sweeps:
         kw["sweeps"] = [int(v) for v in args.sweeps.split(",")]
     if method == "helmholtz-sl":
@@ -597,7 +602,8 @@ def cycle_bytes(levels, pd, dim=3):
         b = C * n + 4 * C * n                                # |b|, V_0 and z = D^{-1} V_0
         for j in range(k):
             b += (stencil + 2 * C + (j + 1) * C) * n         # w = A z with the first pass's dots
-            b += (2 * C + 2 * (j + 1) * C) * n               # w -= V ha, hb = V^H w, |w|^2
+            if pd.get("reorth_eta", 0.1) >= 1.0:             # the second pass (selective: not taken on
+                b += (2 * C + 2 * (j + 1) * C) * n           # the bench's coarse operators, reading M2)
             if j + 1 < k:
                 b += ((j + 1) * C + 5 * C) * n               # V_{j+1}, z
         return b + (k * C + 2 * C) * n                       # x = D^{-1} V y

@@ -65,25 +65,61 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblk, int* 
 }
 
 // Thread 0 holds the block's K slice sums in mine[0..K) (K <= kGridStride):
-// row blockIdx.x of part; barrier; totals over the problem's blocks -> tot
-// (one warp per value, lanes over the blocks, fixed shuffle tree).
-__device__ __forceinline__ bool grid_totals(const double2* mine, int K, double2* part, unsigned* bar, unsigned nblk,
-                                            int* err, double2* tot) {
-  if (threadIdx.x == 0)
+// row blockIdx.x of part.  The last block to arrive adds the rows in block
+// order (one warp per value, lanes over the blocks, fixed shuffle tree) into
+// tot_g and only then releases the others; every block copies the K totals
+// into tot (shared).  One pass over the partials per reduction, by one block.
+__device__ __forceinline__ bool grid_totals(const double2* mine, int K, double2* part, double2* tot_g, unsigned* bar,
+                                            unsigned nblk, int* err, double2* tot) {
+  __shared__ int s_last, s_ok;
+  __shared__ unsigned s_gen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
     for (int i = 0; i < K; ++i) part[(size_t)blockIdx.x * kGridStride + i] = mine[i];
-  if (!grid_barrier(bar, nblk, err)) return false;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < K; i += nw) {
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll 4
-    for (unsigned b = lane; b < nblk; b += 32) {
-      const double2 p = __ldcg(&part[(size_t)b * kGridStride + i]);
-      acc.x += p.x;
-      acc.y += p.y;
-    }
-    acc = warp_sum2(acc);
-    if (lane == 0) tot[i] = acc;
+    s_gen = *(volatile unsigned*)(bar + 1);   // before arriving: the release comes after every arrival
+    __threadfence();
+    s_last = atomicAdd(bar, 1u) == nblk - 1;
   }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < K; i += nw) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 4
+      for (unsigned b = lane; b < nblk; b += 32) {
+        const double2 p = __ldcg(&part[(size_t)b * kGridStride + i]);
+        acc.x += p.x;
+        acc.y += p.y;
+      }
+      acc = warp_sum2(acc);
+      if (lane == 0) {
+        tot_g[i] = acc;
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+      s_ok = !*(volatile int*)err;
+    }
+  } else if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    int ok = 1;
+    unsigned spins = 0;
+    while (*gen == s_gen) {
+      if (++spins > kBarrierSpins || *(volatile int*)err) { ok = 0; break; }
+      __nanosleep(32);
+    }
+    if (!ok) atomicExch(err, 1);
+    __threadfence();
+    s_ok = ok && !*(volatile int*)err;
+  }
+  __syncthreads();
+  if (!s_ok) return false;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) tot[i] = __ldcg(&tot_g[i]);
   __syncthreads();
   return true;
 }
@@ -128,6 +164,7 @@ __global__ void __launch_bounds__(kGridThreads) k_coarse_gmres_grid(Dims g, cons
   shift_nodes(g, dinv, b, x, V, z);
   double2* part0 = gs.part + (size_t)pb * 2 * gs.nblk * kGridStride;
   double2* part1 = part0 + (size_t)gs.nblk * kGridStride;
+  double2* tot_g = gs.tot + (size_t)pb * kGridStride;
   unsigned* bar = gs.bar + 2 * pb;
   int* err = gs.err + pb;
   const int64_t chunk = (n + nblk - 1) / nblk;
@@ -144,7 +181,7 @@ __global__ void __launch_bounds__(kGridThreads) k_coarse_gmres_grid(Dims g, cons
   __shared__ double2 sn[kGridMaxK];
   __shared__ double2 gg[kGridMaxK + 1];
   __shared__ double2 y[kGridMaxK];
-  __shared__ double s_val;
+  __shared__ T s_inv;
   __shared__ int s_stop, s_two;
   int buf = 0;
   bool ok = true;
@@ -157,14 +194,16 @@ __global__ void __launch_bounds__(kGridThreads) k_coarse_gmres_grid(Dims g, cons
     double2 o[1];
     block_sum_t<T, 1>(s, sh, o);
     if (threadIdx.x == 0) blk[0] = o[0];
-    ok = grid_totals(blk, 1, part(), bar, nblk, err, ha);
-    const double beta = sqrt(ha[0].x);
-    if (threadIdx.x == 0) {
+    ok = grid_totals(blk, 1, part(), tot_g, bar, nblk, err, ha);
+    if (threadIdx.x == 0) {   // float64 square root and division once per block
+      const double beta = sqrt(ha[0].x);
       for (int i = 0; i <= kGridMaxK; ++i) gg[i] = make_double2(0.0, 0.0);
       gg[0] = make_double2(beta, 0.0);
       s_stop = beta > 0.0 ? k : 0;
+      s_inv = beta > 0.0 ? (T)(1.0 / beta) : T(0);
     }
-    const T inv = beta > 0.0 ? (T)(1.0 / beta) : T(0);
+    __syncthreads();
+    const T inv = s_inv;
     for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
       const C<T> v = cscale(b[e], inv);
       V[e] = v;
@@ -182,7 +221,7 @@ __global__ void __launch_bounds__(kGridThreads) k_coarse_gmres_grid(Dims g, cons
     __syncthreads();
     // first Gram-Schmidt pass: ha = V^H w and |w|^2; the selective decision
     slice_dots_g<T>(V, ld, lo, hi, j + 1, w, true, blk, sh);
-    if (!(ok = grid_totals(blk, j + 2, part(), bar, nblk, err, ha))) break;
+    if (!(ok = grid_totals(blk, j + 2, part(), tot_g, bar, nblk, err, ha))) break;
     if (threadIdx.x == 0) {
       double t = ha[j + 1].x;
       for (int i = 0; i <= j; ++i) t -= ha[i].x * ha[i].x + ha[i].y * ha[i].y;
@@ -204,7 +243,7 @@ __global__ void __launch_bounds__(kGridThreads) k_coarse_gmres_grid(Dims g, cons
       __syncthreads();
       // second pass: hb = V^H w and |w|^2 in one reduction
       slice_dots_g<T>(V, ld, lo, hi, j + 1, w, true, blk, sh);
-      if (!(ok = grid_totals(blk, j + 2, part(), bar, nblk, err, hb))) break;
+      if (!(ok = grid_totals(blk, j + 2, part(), tot_g, bar, nblk, err, hb))) break;
     }
     if (threadIdx.x == 0) {
       // Hessenberg column j, earlier rotations, new rotation (same in every block)
@@ -232,7 +271,7 @@ __global__ void __launch_bounds__(kGridThreads) k_coarse_gmres_grid(Dims g, cons
       gg[j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
       gg[j] = make_double2(c * gj.x, c * gj.y);
       if (!(hn > 0.0) && s_stop > j + 1) s_stop = j + 1;
-      s_val = hn;
+      s_inv = hn > 0.0 ? (T)(1.0 / hn) : T(0);
     }
     __syncthreads();
     // V_{j+1} = (w - V c) / h with c = hb after the second pass (w already
@@ -241,7 +280,7 @@ __global__ void __launch_bounds__(kGridThreads) k_coarse_gmres_grid(Dims g, cons
       const double2* c = s_two ? hb : ha;
       for (int i = threadIdx.x; i <= j; i += blockDim.x) cv[i] = mk<T>((T)(-c[i].x), (T)(-c[i].y));
       __syncthreads();
-      const T inv = s_val > 0.0 ? (T)(1.0 / s_val) : T(0);
+      const T inv = s_inv;
       for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
         C<T> acc = w[e];
         for (int i = 0; i <= j; ++i) acc = cfma(V[(int64_t)i * ld + e], cv[i], acc);

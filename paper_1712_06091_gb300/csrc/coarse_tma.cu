@@ -123,10 +123,11 @@ template <typename T> __device__ __forceinline__ C<T> warp_allsum(C<T> v) {
 //   kTmaArnoldi: out = A x and the first Gram-Schmidt pass of an Arnoldi step,
 //              ha[i] = sum_e conj(V_i[e]) out[e] for i < kd and ha[kd] =
 //              |out|^2 (kd <= 63): each tile's products are summed over the
-//              warp, lane i (and i - 32) keeps value i's running sum in
-//              float64, the warps add theirs in warp order, the last block
+//              warp, lane i (and i - 32) keeps value i's running sum over the
+//              warp's tiles (float32: a coarsest level gives a warp a few
+//              tiles), the warps add theirs in float64 in warp order, the last block
 //              adds the blocks' in block order (deterministic for a given
-//              grid) and takes the selective decision (coarse_select_dev)
+//              grid) and takes the selective decision (coarse_select_block)
 template <int DIM, typename T, bool BT, int WARPS, int STAGES, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, 1)
     k_stencil_tma(Dims g, const C<T>* __restrict__ A, const C<T>* __restrict__ x, const C<T>* __restrict__ aux,
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   unsigned phase = 0u;   // bit s: parity of stage s's next completion
   bool fail = false;
   C<T> sacc[2] = {czero<T>(), czero<T>()};
-  double2 dacc0 = make_double2(0.0, 0.0), dacc1 = make_double2(0.0, 0.0);   // kTmaArnoldi: bases lane, lane + 32
+  C<T> facc0 = czero<T>(), facc1 = czero<T>();   // kTmaArnoldi: running sums of values lane, lane + 32
   int s = 0;
   int64_t t = t0;
   for (; t < ntiles; t += stride, s = STAGES > 1 ? s ^ 1 : 0) {
@@ -216,13 +217,38 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       }
     }
     if constexpr (MODE == kTmaArnoldi) {
-      for (int i = 0; i <= kd; ++i) {   // value kd: |A x|^2
-        const C<T> vi = i == kd ? axw : (j < g.N ? V[(int64_t)i * ld + j] : czero<T>());
-        const C<T> p = warp_allsum<T>(cfma_conj(vi, axw, czero<T>()));
-        if (lane == (i & 31)) {
-          double2& d = i < 32 ? dacc0 : dacc1;
-          d.x += (double)p.x;
-          d.y += (double)p.y;
+      // Value i < kd: conj(V_i) . Ax over the tile; value kd: |Ax|^2.  Eight
+      // values per round: their basis entries are all loaded before any
+      // reduction, and their eight butterflies interleave.
+      for (int i0 = 0; i0 <= kd; i0 += 8) {
+        C<T> p[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + q;
+          C<T> vi = czero<T>();
+          if (i < kd) {
+            if (j < g.N) vi = V[(int64_t)i * ld + j];
+          } else if (i == kd) {
+            vi = axw;
+          }
+          p[q] = cfma_conj(vi, axw, czero<T>());
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            p[q].x += __shfl_xor_sync(0xffffffffu, p[q].x, o);
+            p[q].y += __shfl_xor_sync(0xffffffffu, p[q].y, o);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + q;
+          if (i <= kd && lane == (i & 31)) {
+            C<T>& d = i < 32 ? facc0 : facc1;
+            d.x += p[q].x;
+            d.y += p[q].y;
+          }
         }
       }
     }
@@ -254,21 +280,39 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     }
   }
   if constexpr (MODE == kTmaArnoldi) {
+    // Every warp is past its tiles: the tile buffers are scratch from here on.
+    // The warps' running sums go to shared memory and one thread per value
+    // adds them in warp order (float64).
     const int nv = kd + 1;
     __shared__ double2 s_dots[kMaxArnoldiDots];
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) s_dots[i] = make_double2(0.0, 0.0);
     __syncthreads();
-    for (int w = 0; w < WARPS; ++w) {   // warps in order
-      if (warp == w) {
-        if (lane < nv) s_dots[lane] = cadd(s_dots[lane], dacc0);
-        if (lane + 32 < nv) s_dots[lane + 32] = cadd(s_dots[lane + 32], dacc1);
+    C<T>* wsum = reinterpret_cast<C<T>*>(tma_smem);   // [WARPS][64]
+    wsum[warp * 64 + lane] = facc0;
+    wsum[warp * 64 + 32 + lane] = facc1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int w = 0; w < WARPS; ++w) {
+        const C<T> v = wsum[w * 64 + i];
+        acc.x += (double)v.x;
+        acc.y += (double)v.y;
       }
-      __syncthreads();
+      s_dots[i] = acc;
     }
-    if (last_block_rt(nv, s_dots, partial, ticket, alpha, sh) && threadIdx.x == 0) {
-      if (*(volatile int*)err != 0 || s_fail)
+    __syncthreads();
+    if (last_block_rt(nv, s_dots, partial, ticket, alpha, sh)) {   // uniform over the block
+      if (threadIdx.x == 0 && (*(volatile int*)err != 0 || s_fail))
         for (int i = 0; i < nv; ++i) alpha[i] = make_double2(NAN, NAN);
-      coarse_select_dev(alpha, tail.hb, kd, tail.eta2, arnoldi_at(tail.st, blockIdx.y), tail.j, tail.finish, tail.nrm2);
+      __syncthreads();
+      const ArnoldiState ast = arnoldi_at(tail.st, blockIdx.y);
+      constexpr size_t kScratch = (size_t)WARPS * STAGES * W * 32 * sizeof(C<T>);   // the dynamic shared memory
+      constexpr size_t kSums = (size_t)WARPS * 64 * sizeof(C<T>);
+      if (kSums + (size_t)arnoldi_stage_words(ast.m, kd) * sizeof(double2) <= kScratch) {
+        double2* stage = reinterpret_cast<double2*>(tma_smem + kSums);
+        coarse_select_block(alpha, tail.hb, kd, tail.eta2, ast, tail.j, tail.finish, tail.nrm2, stage);
+      } else if (threadIdx.x == 0) {   // a long basis on a 2D level: the state does not fit beside the sums
+        coarse_select_dev(alpha, tail.hb, kd, tail.eta2, ast, tail.j, tail.finish, tail.nrm2);
+      }
     }
   }
   if constexpr (MODE == kTmaMr) {

@@ -32,6 +32,20 @@ int reduction_blocks(int64_t n, int values) {
 // ---------------------------------------------------------------------------
 // Elementwise
 // ---------------------------------------------------------------------------
+// A per-problem float64 scalar as complex T for every thread of the block,
+// converted once by thread 0 through shared memory: a float64 conversion in
+// every thread of a finest-grid launch costs tens of microseconds at the
+// float64 pipe's rate.  Call once per kernel, from every thread.
+template <typename T> __device__ __forceinline__ C<T> block_scalar(const double2* p) {
+  __shared__ C<T> s;
+  if (threadIdx.x == 0) {
+    const double2 v = *p;
+    s = mk<T>((T)v.x, (T)v.y);
+  }
+  __syncthreads();
+  return s;
+}
+
 // out = w / |w| with the reciprocal norm precomputed in nrm2->y by the kernel
 // that reduced nrm2->x (zero if the norm vanishes): no per-thread float64
 // square root or division.
@@ -39,10 +53,10 @@ template <typename T>
 __global__ void k_scale_inv_norm(const C<T>* w, C<T>* out, const double2* __restrict__ nrm2, Dims g) {
   if (resolve(g)) return;
   const int64_t n = g.N;
+  const T inv = block_scalar<T>(nrm2 + blockIdx.y).y;   // the reciprocal norm
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
   shift_nodes(g, w, out);
-  const T inv = (T)nrm2[blockIdx.y].y;
   out[e] = cscale(w[e], inv);
 }
 template <typename T>
@@ -56,10 +70,10 @@ __global__ void k_scale_dinv(const C<T>* w, C<T>* out, const C<T>* __restrict__ 
                              const double2* __restrict__ nrm2, Dims g) {
   if (resolve(g)) return;
   const int64_t n = g.N;
+  const T inv = block_scalar<T>(nrm2 + blockIdx.y).y;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
   shift_nodes(g, w, out, dinv, z);
-  const T inv = (T)nrm2[blockIdx.y].y;
   const C<T> v = cscale(w[e], inv);
   out[e] = v;
   z[e] = cmul(dinv[e], v);
@@ -224,7 +238,7 @@ __global__ void __launch_bounds__(256) k_cgs_pass3(const C<T>* __restrict__ V, i
   s = scratch_at(s, blockIdx.y);
   if (update_norm<T>(V, ld, k, w, n, s.hb, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
     const double s2t = s.nrm2->x;
-    s.nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
+    s.nrm2->y = s2t > 0.0 ? rsqrt(s2t) : 0.0;
     if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, s2t);
   }
 }
@@ -405,7 +419,7 @@ __global__ void __launch_bounds__(256) k_sgs_update_test(const C<T>* __restrict_
     if (t >= eta2 * s.ha[k].x) {
       s.ha[k].y = 0.0;
       for (int i = 0; i < k; ++i) s.hb[i] = make_double2(0.0, 0.0);
-      s.nrm2->y = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+      s.nrm2->y = t > 0.0 ? rsqrt(t) : 0.0;
       if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, t);
     } else {
       s.ha[k].y = 1.0;
@@ -437,7 +451,7 @@ __global__ void __launch_bounds__(256) k_sgs_reorth_update(const C<T>* __restric
   shift_nodes(g, V, w);
   if (update_norm<T>(V, ld, k, w, n, s.hb, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
     const double s2t = s.nrm2->x;
-    s.nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
+    s.nrm2->y = s2t > 0.0 ? rsqrt(s2t) : 0.0;
     if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, s2t);
   }
 }
@@ -460,8 +474,9 @@ __global__ void __launch_bounds__(256) k_norm_start(const C<T>* b, Dims g, Krylo
   if (threadIdx.x == 0) blk[0] = o[0];
   __syncthreads();
   if (last_block_rt(1, blk, s.partial, s.ticket, s.nrm2, sh) && threadIdx.x == 0) {
-    const double beta = sqrt(s.nrm2->x);
-    s.nrm2->y = beta > 0.0 ? 1.0 / beta : 0.0;
+    double beta, ibeta;
+    sqrt_pair(s.nrm2->x, beta, ibeta);
+    s.nrm2->y = ibeta;
     if (!start) return;
     const ArnoldiState a = arnoldi_at(st, blockIdx.y);
     for (int i = 0; i <= a.m; ++i) a.g[i] = make_double2(0.0, 0.0);
@@ -502,12 +517,11 @@ __global__ void k_mr_update2(C<T>* x, const C<T>* z, const C<T>* r_src, C<T>* r_
                              C<T>* znext, int x_zero, Dims g) {
   if (resolve(g)) return;
   const int64_t n = g.N;
+  const C<T> al = block_scalar<T>(alpha + blockIdx.y);
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
   shift_nodes(g, x, z, r_src, r_dst, w, dinv);
   shift_nodes_opt(g, znext);
-  const double2 ad = alpha[blockIdx.y];
-  const C<T> al = mk<T>((T)ad.x, (T)ad.y);
   x[e] = cfma(al, z[e], x_zero ? czero<T>() : x[e]);
   const C<T> rn = csub(r_src[e], cmul(al, w[e]));
   r_dst[e] = rn;

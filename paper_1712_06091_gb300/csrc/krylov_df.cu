@@ -21,6 +21,18 @@ namespace adr {
 
 static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// Blocks of the Gram-Schmidt passes: these stream the basis from memory, so
+// they want more resident warps than the short reductions of the coarse
+// levels (reduction_blocks): up to four 256-thread blocks per SM of the
+// 152, one per 1024 entries, within the partial-sum stride for `values` sums.
+static int df_blocks(int64_t n, int values) {
+  int64_t b = (n + 1023) / 1024;
+  if (b > 608) b = 608;
+  const int64_t cap = kPartialStride / values;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
 // Block sum of K complex double-float values per thread: the warp stage in
 // double-float (float32 shuffles and two-sums), each warp's sum widened to
 // float64 and the warps added in order.  Result valid in thread 0.
@@ -106,6 +118,7 @@ __device__ __forceinline__ bool df_update_norm(const float2* __restrict__ V, int
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const float2 wh = w[e], wl = w[e + lo];
     DfSum ar{wh.x, wl.x}, ai{wh.y, wl.y};
+#pragma unroll 4
     for (int i = 0; i < k; ++i) {
       const float4 cc = coef[i];
       const float2* v = V + (int64_t)i * ld + e;
@@ -156,7 +169,7 @@ __global__ void __launch_bounds__(256) k_df_update_test(const float2* __restrict
     if (t >= eta2 * s.ha[k].x) {
       s.ha[k].y = 0.0;
       for (int i = 0; i < k; ++i) s.hb[i] = make_double2(0.0, 0.0);
-      s.nrm2->y = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+      s.nrm2->y = t > 0.0 ? rsqrt(t) : 0.0;
       if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, t);
     } else {
       s.ha[k].y = 1.0;
@@ -184,7 +197,7 @@ __global__ void __launch_bounds__(256) k_df_reorth_update(const float2* __restri
   shift_nodes(g, V, w);
   if (df_update_norm(V, ld, lo, k, w, g.N, s.hb, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
     const double s2t = s.nrm2->x;
-    s.nrm2->y = s2t > 0.0 ? 1.0 / sqrt(s2t) : 0.0;
+    s.nrm2->y = s2t > 0.0 ? rsqrt(s2t) : 0.0;
     if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, s2t);
   }
 }
@@ -261,7 +274,7 @@ void launch_df_selective(const float2* V, int64_t ld, int64_t lo, int k, float2*
                          const KrylovScratch& s, const ArnoldiState& st, int j, double eta, cudaStream_t stream) {
   // eta >= 1: the second pass always runs (as launch_cgs2)
   const double eta2 = eta < 1.0 ? eta * eta : INFINITY;
-  const dim3 grid(reduction_blocks(g.N, k + 2), g.B);
+  const dim3 grid(df_blocks(g.N, k + 2), g.B);
   count_launches(1), k_df_dots_norm<<<grid, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
   count_launches(1), k_df_update_test<<<grid, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j, eta2);
   count_launches(1), k_df_reorth_dots<<<grid, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
