@@ -23,21 +23,24 @@ static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n
 
 // Blocks of the Gram-Schmidt passes: these stream the basis from memory, so
 // they want more resident warps than the short reductions of the coarse
-// levels (reduction_blocks): up to four 256-thread blocks per SM of the
-// 152, one per 1024 entries, within the partial-sum stride for `values` sums.
-static int df_blocks(int64_t n, int values) {
+// levels (reduction_blocks): one resident wave of `per_sm` 256-thread blocks
+// on each of the 152 SMs, one per 1024 entries, within the partial-sum
+// stride for `values` sums.
+static int df_blocks(int64_t n, int values, int per_sm) {
   int64_t b = (n + 1023) / 1024;
-  if (b > 608) b = 608;
+  if (b > 152 * per_sm) b = 152 * per_sm;
   const int64_t cap = kPartialStride / values;
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
 
-// Block sum of K complex double-float values per thread: the warp stage in
-// double-float (float32 shuffles and two-sums), each warp's sum widened to
-// float64 and the warps added in order.  Result valid in thread 0.
+// Block sum of K complex double-float values per thread, in double-float up
+// to the block's total (float32 shuffles and two-sums: on this GPU a float64
+// instruction costs the float64 pipe's rate even with one active lane), then
+// widened to float64 once per value.  Result valid in thread 0; sh must hold
+// 32 K float4.
 template <int K>
-__device__ __forceinline__ void block_sum_df(DfSum (&re)[K], DfSum (&im)[K], double2* sh, double2 (&out)[K]) {
+__device__ __forceinline__ void block_sum_df(DfSum (&re)[K], DfSum (&im)[K], float4* sh, double2 (&out)[K]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -50,31 +53,45 @@ __device__ __forceinline__ void block_sum_df(DfSum (&re)[K], DfSum (&im)[K], dou
   __syncthreads();
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) sh[wid * K + k] = make_double2(df_double(re[k]), df_double(im[k]));
+    for (int k = 0; k < K; ++k) sh[wid * K + k] = make_float4(re[k].s, re[k].t, im[k].s, im[k].t);
   }
   __syncthreads();
+  __shared__ double2 s_tot[K];
   if (wid == 0) {
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < K; ++k) {
-      const double2 s = lane < nw ? sh[lane * K + k] : make_double2(0.0, 0.0);
-      out[k] = warp_sum2(s);
+      const float4 v = lane < nw ? sh[lane * K + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      DfSum a{v.x, v.y}, b{v.z, v.w};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {   // the total lands in lane 0
+        df_add(a, df_shfl_down(a, o));
+        df_add(b, df_shfl_down(b, o));
+      }
+      if (lane == 0) s_tot[k] = make_double2(df_double(a), df_double(b));
+    }
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) out[k] = s_tot[k];
     }
   }
 }
 
 // Block partials of conj(V_i)^T w for i < k into blk[0..k) and, when norm,
-// |w|^2 into blk[k].  Four basis vectors per sweep over w.
+// |w|^2 into blk[k].  Four basis vectors per sweep over w (eight measured
+// slower: 231 against 188 us on the 257x257x129 grid, fewer resident warps).
+constexpr int kDfChunk = 4;
 __device__ __forceinline__ void df_block_dots(const float2* __restrict__ V, int64_t ld, int64_t lo, int k,
-                                              const float2* w, int64_t n, bool norm, double2* blk, double2* sh) {
-  for (int c = 0; c < k; c += 4) {
-    DfSum re[5], im[5];
+                                              const float2* w, int64_t n, bool norm, double2* blk, float4* sh) {
+  for (int c = 0; c < k; c += kDfChunk) {
+    DfSum re[kDfChunk + 1], im[kDfChunk + 1];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) re[q] = im[q] = DfSum{0.f, 0.f};
+    for (int q = 0; q <= kDfChunk; ++q) re[q] = im[q] = DfSum{0.f, 0.f};
     const bool nq = norm && c == 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
       const float2 wh = w[e], wl = w[e + lo];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kDfChunk; ++q) {
         if (c + q < k) {
           const float2* v = V + (int64_t)(c + q) * ld + e;
           const float2 vh = __ldg(v), vl = __ldg(v + lo);
@@ -86,15 +103,15 @@ __device__ __forceinline__ void df_block_dots(const float2* __restrict__ V, int6
         }
       }
       if (nq) {
-        df_add_prod2(re[4], wh.x, wl.x, wh.x, wl.x);
-        df_add_prod2(re[4], wh.y, wl.y, wh.y, wl.y);
+        df_add_prod2(re[kDfChunk], wh.x, wl.x, wh.x, wl.x);
+        df_add_prod2(re[kDfChunk], wh.y, wl.y, wh.y, wl.y);
       }
     }
-    double2 o[5];
-    block_sum_df<5>(re, im, sh, o);
+    double2 o[kDfChunk + 1];
+    block_sum_df<kDfChunk + 1>(re, im, sh, o);
     if (threadIdx.x == 0) {
-      for (int q = 0; q < 4 && c + q < k; ++q) blk[c + q] = o[q];
-      if (nq) blk[k] = o[4];
+      for (int q = 0; q < kDfChunk && c + q < k; ++q) blk[c + q] = o[q];
+      if (nq) blk[k] = o[kDfChunk];
     }
     __syncthreads();
   }
@@ -136,7 +153,7 @@ __device__ __forceinline__ bool df_update_norm(const float2* __restrict__ V, int
     df_add_prod2(s2[0], m.x, m.y, m.x, m.y);
   }
   double2 o[1];
-  block_sum_df<1>(s2, zero, sh, o);
+  block_sum_df<1>(s2, zero, reinterpret_cast<float4*>(sh), o);
   if (threadIdx.x == 0) blk[0] = o[0];
   __syncthreads();
   return last_block_rt(1, blk, partial, ticket, nrm2, sh);
@@ -147,14 +164,14 @@ __device__ __forceinline__ bool df_update_norm(const float2* __restrict__ V, int
 //   B: w -= V ha, |w'|^2, keep the column when |w'|^2 >= eta^2 |w|^2
 //   C: (only if flagged) hb = V^H w'
 //   D: (only if flagged) w' -= V hb, |w''|^2, the Arnoldi column from ha + hb
-__global__ void __launch_bounds__(256) k_df_dots_norm(const float2* __restrict__ V, int64_t ld, int64_t lo, int k,
+__global__ void __launch_bounds__(256, 4) k_df_dots_norm(const float2* __restrict__ V, int64_t ld, int64_t lo, int k,
                                                       const float2* w, Dims g, KrylovScratch s) {
   if (resolve(g)) return;
-  __shared__ double2 sh[32 * 5];
+  __shared__ double2 sh[32 * (kDfChunk + 1)];
   __shared__ double2 blk[kMaxKrylov + 2];
   shift_nodes(g, V, w);
   s = scratch_at(s, blockIdx.y);
-  df_block_dots(V, ld, lo, k, w, g.N, true, blk, sh);
+  df_block_dots(V, ld, lo, k, w, g.N, true, blk, reinterpret_cast<float4*>(sh));
   last_block_rt(k + 1, blk, s.partial, s.ticket, s.ha, sh);
 }
 
@@ -177,15 +194,15 @@ __global__ void __launch_bounds__(256) k_df_update_test(const float2* __restrict
   }
 }
 
-__global__ void __launch_bounds__(256) k_df_reorth_dots(const float2* __restrict__ V, int64_t ld, int64_t lo, int k,
+__global__ void __launch_bounds__(256, 4) k_df_reorth_dots(const float2* __restrict__ V, int64_t ld, int64_t lo, int k,
                                                         const float2* w, Dims g, KrylovScratch s) {
   if (resolve(g)) return;
   s = scratch_at(s, blockIdx.y);
   if (s.ha[k].y == 0.0) return;   // uniform over the problem's blocks
-  __shared__ double2 sh[32 * 5];
+  __shared__ double2 sh[32 * (kDfChunk + 1)];
   __shared__ double2 blk[kMaxKrylov + 2];
   shift_nodes(g, V, w);
-  df_block_dots(V, ld, lo, k, w, g.N, false, blk, sh);
+  df_block_dots(V, ld, lo, k, w, g.N, false, blk, reinterpret_cast<float4*>(sh));
   last_block_rt(k, blk, s.partial, s.ticket, s.hb, sh);
 }
 
@@ -274,11 +291,11 @@ void launch_df_selective(const float2* V, int64_t ld, int64_t lo, int k, float2*
                          const KrylovScratch& s, const ArnoldiState& st, int j, double eta, cudaStream_t stream) {
   // eta >= 1: the second pass always runs (as launch_cgs2)
   const double eta2 = eta < 1.0 ? eta * eta : INFINITY;
-  const dim3 grid(df_blocks(g.N, k + 2), g.B);
-  count_launches(1), k_df_dots_norm<<<grid, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
-  count_launches(1), k_df_update_test<<<grid, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j, eta2);
-  count_launches(1), k_df_reorth_dots<<<grid, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
-  count_launches(1), k_df_reorth_update<<<grid, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j);
+  const dim3 gdots(df_blocks(g.N, k + 2, 4), g.B), gupd(df_blocks(g.N, k + 2, 4), g.B);
+  count_launches(1), k_df_dots_norm<<<gdots, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
+  count_launches(1), k_df_update_test<<<gupd, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j, eta2);
+  count_launches(1), k_df_reorth_dots<<<gdots, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
+  count_launches(1), k_df_reorth_update<<<gupd, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j);
 }
 
 void launch_df_scale(float2* w, int64_t lo, const double2* nrm2, float2* cyc, const Dims& g, cudaStream_t st) {

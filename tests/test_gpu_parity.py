@@ -191,12 +191,20 @@ def test_double_float_outer_iteration(adrlib, cuda, name, restart, eta):
 
 @pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17"])
 def test_cycle_f32(adrlib, cuda, name):
+    """One float32 cycle against the oracle's float64 cycle.  Measured on
+    GB300 (printed with -s): 3.0e-7 (const2d_33), 1.5e-6 (marine2d_65),
+    2.5e-7 (layered3d_17), float32 rounding (6e-8) grown through the cycle's
+    minimal-residual weights and coarse solves, which divide by inner
+    products of near-cancelling Laplacian and reaction terms.  The bound 2e-5
+    leaves a margin of about 13 over the largest; a wrong term or index shows
+    at O(1)."""
     P, params, op = make_operator(name, precision="f32")
     hier = mg.build_hierarchy(oracle_matrix(name, "prec"), P.n, params.levels)
     r = W.random_complex(hier[0]["A"].shape[0], 12)
     z = op.vcycle(_cvec(r, torch.complex64)).cpu().numpy()
     ref = mg.cycle(hier, r, oracle_cycle_params(params))
-    assert rel(z, ref) <= 2e-4, rel(z, ref)
+    print(f"float32 cycle against the float64 oracle, {name}: {rel(z, ref):.2e}")
+    assert rel(z, ref) <= 2e-5, rel(z, ref)
 
 
 @pytest.mark.parametrize("name", ["const2d_33", "marine2d_65", "layered3d_17", "corner3d_9x11x13"])
