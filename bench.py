@@ -85,8 +85,9 @@ CEN_FULL_ITERATIONS = 60.0   # stage 1 + stage 2 iterations of the GPU solve at 
 # The kernel whose roofline is reported, and its algorithmic bytes per node of
 # level 1: the 81-point stencil stored as 27 complex box entries and 54
 # imaginary parts (float32), z and r read, w written (complex float32).
-ROOFLINE_KERNEL = ("k_stencil_tma<3,float,false,16,1,kTmaMr> on level 1 (minimal-residual relaxation apply, "
-                   "81-point Galerkin stencil streamed into shared memory by bulk copies)")
+ROOFLINE_KERNEL = ("k_stencil_tma<3,float,false,16,kHalves,kTmaMr> on level 1 (minimal-residual relaxation apply, "
+                   "81-point Galerkin stencil streamed into shared memory by bulk copies, each warp's tile buffer "
+                   "refilled in halves)")
 ROOFLINE_BYTES_PER_NODE = 27 * 8 + 54 * 4 + 3 * 8
 # The finest-grid relaxation apply: packed rows (14 floats) plus z, r read and w written (complex float32).
 FINE_RELAX_BYTES_PER_NODE = 14 * 4 + 3 * 8
@@ -119,9 +120,11 @@ def parse():
     ap.add_argument("--restart", type=int, default=None)
     ap.add_argument("--coarse-solver", default=None, choices=["auto", "kernels", "cta", "cluster", "grid"],
                     help="form of the coarsest-grid GMRES (same arithmetic; default: the library's choice)")
-    ap.add_argument("--tma", type=int, default=None, choices=[0, 1, 2],
+    ap.add_argument("--tma", type=int, default=None, choices=[0, 1, 2, 3],
                     help="stored-stencil applies: 1 bulk copies, 16 warps (library default); 2 bulk copies, 8 warps "
-                         "with two buffers; 0 plain loads")
+                         "with two buffers; 3 bulk copies, 16 warps, buffers refilled in halves; 0 plain loads")
+    ap.add_argument("--outer-df", type=int, default=None, choices=[0, 1],
+                    help="outer Krylov iteration with the float32 cycle: 1 double-float (library default), 0 float64")
     ap.add_argument("--cycle", default=None)
     ap.add_argument("--sweeps", default=None, help="comma-separated relaxations per level")
     ap.add_argument("--no-e2e", action="store_true")
@@ -165,6 +168,8 @@ def build_params(args, method=None):
         kw["coarse_solver"] = args.coarse_solver
     if args.tma is not None:
         kw["tma"] = args.tma
+    if args.outer_df is not None:
+        kw["outer_df"] = args.outer_df
     if args.sweeps:
         kw["sweeps"] = [int(v) for v in args.sweeps.split(",")]
     if method == "helmholtz-sl":
@@ -516,12 +521,14 @@ def run_ours(args):
         comparison = [method_comparison(m, P, kappa, gamma, tau1, args, dev) for m in METHODS if m != args.method]
         if args.precision == "f32":     # the same method with the float64 cycle (the plain float64 solve)
             comparison.append(method_comparison(args.method, P, kappa, gamma, tau1, args, dev, precision="f64"))
+            if outer_label(args) == "df64":   # the same FP32 cycle inside a float64 outer iteration
+                comparison.append(method_comparison(args.method, P, kappa, gamma, tau1, args, dev, outer_df=0))
 
     if rank == 0:
         out = {
             "metric": metric_for(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 cycle + f64 Krylov" if args.precision == "f32" else "f64",
+            "vs_baseline": None, "dtype": dtype_label(args),
             "data": "synthetic (seeded layered-gradient model with Gaussian anomalies; " +
                     ("tau1 = 0: the standard Helmholtz matrix)" if args.method == "helmholtz-sl" else
                      "tau1 from the library's second-order travel-time kernel)"),
@@ -673,17 +680,18 @@ def cycle_roofline(breakdown, levels, pd, peak, peak_kind):
                     "bench.cycle_bytes) over its live event time"}
 
 
-def method_comparison(method, P, kappa, gamma, tau1, args, dev, precision=None):
-    """Another method (or the same one in another cycle precision) on the same
-    medium, source and tolerance (the paper's comparison of Sec. 4): one
-    warm-up step, then one step (operator setup, solve, reconstruction) timed
-    with CUDA events."""
+def method_comparison(method, P, kappa, gamma, tau1, args, dev, precision=None, outer_df=None):
+    """Another method (or the same one in another cycle or outer precision) on
+    the same medium, source and tolerance (the paper's comparison of Sec. 4):
+    one warm-up step, then one step (operator setup, solve, reconstruction)
+    timed with CUDA events."""
     import copy
     import torch
     from paper_1712_06091_gb300 import adr as gpu
-    if precision:
+    if precision or outer_df is not None:
         args = copy.copy(args)
-        args.precision = precision
+        args.precision = precision or args.precision
+        args.outer_df = outer_df if outer_df is not None else args.outer_df
     solver = MethodSolver(method, P, kappa, tau1, gamma, args, dev)
     a = torch.empty(P.N, dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -695,7 +703,7 @@ def method_comparison(method, P, kappa, gamma, tau1, args, dev, precision=None):
     info, _ = solver.step(a)
     ev1.record(stream)
     torch.cuda.synchronize()
-    out = {"method": method, "precision": args.precision,
+    out = {"method": method, "precision": args.precision, "outer": outer_label(args),
            "metric": {"helmholtz-sl": SL_METRIC, "adr-central": CEN_METRIC}.get(method, METRIC),
            "value": 1e3 / ev0.elapsed_time(ev1), "unit": UNIT, "ms_per_step": ev0.elapsed_time(ev1),
            "iterations": info["iterations"], "rel_residual": info["rel_residual"],
@@ -704,6 +712,18 @@ def method_comparison(method, P, kappa, gamma, tau1, args, dev, precision=None):
         out["stage1_iterations"] = info["stage1_iterations"]
     solver.close()
     return out
+
+
+def outer_label(args):
+    """Arithmetic of the outer Krylov iteration: double-float with the float32
+    cycle unless params.outer_df = 0 (float64 residual and solution either way)."""
+    return "df64" if args.precision == "f32" and args.outer_df != 0 else "f64"
+
+
+def dtype_label(args):
+    if args.precision != "f32":
+        return "f64"
+    return "f32 cycle + " + ("df64 Krylov (f64 residual)" if outer_label(args) == "df64" else "f64 Krylov")
 
 
 def run_reference(args):
@@ -862,7 +882,7 @@ def run_batched(args):
     out = {
         "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 cycle + f64 Krylov", "data": "synthetic (layered model resampled per grid; tau1 from the library's "
+        "dtype": dtype_label(args), "data": "synthetic (layered model resampled per grid; tau1 from the library's "
                                                  "travel-time kernel)",
         "config": {"workload": "batched3d_3x32", "grids": list(BATCH_GRIDS), "sources_per_grid": BATCH_SOURCES,
                    "batch_form": args.batch_form,
@@ -926,7 +946,7 @@ def run_gradient(args):
     out = {
         "metric": GRAD_METRIC, "value": args.steps / (ms / 1e3), "unit": "gradients/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 cycle + f64 Krylov", "data": "synthetic (layered model; data from a 2% "
+        "vs_baseline": None, "dtype": "f32 cycle + df64 Krylov (forward), f64 Krylov (adjoint)", "data": "synthetic (layered model; data from a 2% "
                                                                           "smooth slowness perturbation)",
         "config": {"workload": "gradient3d_129_16src", "grid": list(P.n), "sources": 16, "receivers": int(rec.numel()),
                    "tol": args.tol, "misfit": J, "grad_norm": float(grad.norm())},

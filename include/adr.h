@@ -114,9 +114,12 @@ typedef struct adr_params {
                                           stencil levels stream their coefficients into
                                           shared memory with bulk copies (16 warps, one
                                           buffer each); 2: the same with 8 warps, two
-                                          buffers each; 0: plain loads.  Same per-node
-                                          arithmetic; the weight's block sums follow the
-                                          kernel's grid.  Default 1 */
+                                          buffers each; 3: 16 warps, one buffer each
+                                          refilled in halves (box entries, two-point
+                                          entries; the coarsest grid's GMRES step keeps
+                                          whole tiles); 0: plain loads.  Same products;
+                                          the sums' order and the weight's block sums
+                                          follow the kernel.  Default 3 */
   double shift;                        /* complex shift alpha of the cycle's operator
                                           (Eq. shift): the multigrid hierarchy is built
                                           from the preconditioner minus i alpha w^2

@@ -91,6 +91,30 @@ __device__ __forceinline__ C<T> tile_dot_seq(const C<T>* __restrict__ tb, const 
   return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
 
+// One phase of a node's row: the box points (PHASE 0, complex coefficients
+// from tb) or the two-points (PHASE 1, imaginary parts from tr), so that the
+// box half of a tile can be consumed while the other half is still arriving.
+template <int DIM, typename T, int PHASE, int P>
+__device__ __forceinline__ void stencil_term_phase(const C<T>* tb, const T* tr, const C<T>* __restrict__ x, int64_t j,
+                                                   int64_t s1, int64_t s2, unsigned m0, unsigned m1, unsigned m2,
+                                                   C<T>& acc) {
+  if constexpr (PointKind<DIM, P>::two == (PHASE == 1)) stencil_term_smem<DIM, T, P>(tb, tr, x, j, s1, s2, m0, m1, m2, acc);
+}
+template <int DIM, typename T, int PHASE, int... P>
+__device__ __forceinline__ C<T> tile_dot_phase(const C<T>* __restrict__ tb, const T* __restrict__ tr,
+                                               const C<T>* __restrict__ x, int64_t j, int64_t s1, int64_t s2, unsigned m0,
+                                               unsigned m1, unsigned m2, std::integer_sequence<int, P...>) {
+  C<T> acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+  (stencil_term_phase<DIM, T, PHASE, P>(tb, tr, x, j, s1, s2, m0, m1, m2, acc[P & 3]), ...);
+  return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+}
+
+// Tile buffers per warp for STAGES: 1 and 2 whole tiles; kHalves one tile
+// refilled in halves (box entries, then two-point entries, each half reissued
+// for the warp's next tile as soon as it has been consumed).
+constexpr int kHalves = 3;
+__host__ __device__ constexpr int tile_buffers(int stages) { return stages == 2 ? 2 : 1; }
+
 // Modes of the streamed stencil kernel.
 enum { kTmaMr = 0, kTmaApply = 1, kTmaResid = 2, kTmaArnoldi = 3 };
 
@@ -115,7 +139,9 @@ template <typename T> __device__ __forceinline__ C<T> warp_allsum(C<T> v) {
 
 // One pass over the level with the coefficient tiles streamed into shared
 // memory.  WARPS warps per block, each with STAGES tile buffers (1: the other
-// warps of the SM overlap its copy; 2: it overlaps its own).
+// warps of the SM overlap its copy; 2: it overlaps its own; kHalves: one
+// buffer whose halves are refilled separately, so the box half of the next
+// tile arrives while the two-point half of this one is consumed).
 //   kTmaMr:    out = A x and the partial sums of out^H aux, out^H out; the last
 //              block writes the minimal-residual weight to alpha
 //   kTmaApply: out = A x
@@ -155,11 +181,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     batch_shift(1, err);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  C<T>* const buf0 = reinterpret_cast<C<T>*>(tma_smem) + (size_t)warp * STAGES * W * 32;
-  C<T>* const buf1 = buf0 + (STAGES > 1 ? W * 32 : 0);
+  constexpr bool HALVES = STAGES == kHalves;
+  constexpr unsigned kBoxBytes = NB * 32 * sizeof(C<T>);          // first half: the box entries
+  C<T>* const buf0 = reinterpret_cast<C<T>*>(tma_smem) + (size_t)warp * tile_buffers(STAGES) * W * 32;
+  C<T>* const buf1 = buf0 + (STAGES == 2 ? W * 32 : 0);
   if (threadIdx.x == 0) s_fail = 0;
   if (lane == 0) {
-    for (int q = 0; q < STAGES; ++q) mbar_init(&mbar[warp][q], 1);
+    for (int q = 0; q < (HALVES ? 2 : STAGES); ++q) mbar_init(&mbar[warp][q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -177,31 +205,87 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       pending |= 1u << s;
     }
   };
-  issue(t0, 0);
-  if (STAGES > 1) issue(t0 + stride, 1);
+  // kHalves: half h (0 box, 1 two-points) of tile t into its place in buf0, on mbar[warp][h]
+  auto issue_half = [&](int64_t t, int h) {
+    if (t < ntiles) {
+      if (lane == 0) {
+        const unsigned bytes = h ? kTileBytes - kBoxBytes : kBoxBytes;
+        const size_t off = h ? (size_t)NB * 32 : 0;
+        mbar_expect_tx(&mbar[warp][h], bytes);
+        bulk_load(buf0 + off, A + t * (int64_t)W * 32 + off, bytes, &mbar[warp][h]);
+      }
+      pending |= 1u << h;
+    }
+  };
+  if constexpr (HALVES) {
+    issue_half(t0, 0);
+    issue_half(t0, 1);
+  } else {
+    issue(t0, 0);
+    if (STAGES > 1) issue(t0 + stride, 1);
+  }
   unsigned phase = 0u;   // bit s: parity of stage s's next completion
   bool fail = false;
   C<T> sacc[2] = {czero<T>(), czero<T>()};
   C<T> facc0 = czero<T>(), facc1 = czero<T>();   // kTmaArnoldi: running sums of values lane, lane + 32
   int s = 0;
   int64_t t = t0;
-  for (; t < ntiles; t += stride, s = STAGES > 1 ? s ^ 1 : 0) {
-    if (!mbar_wait(&mbar[warp][s], (phase >> s) & 1u)) fail = true;
-    fail = __any_sync(0xffffffffu, fail);
-    if (fail) break;
-    phase ^= 1u << s;
-    pending &= ~(1u << s);
+  for (; t < ntiles; t += stride, s = STAGES == 2 ? s ^ 1 : 0) {
     const int64_t j = t * 32 + lane;
     C<T> axw = czero<T>();
+    if constexpr (HALVES) {
+      // box half: consume, then reissue it for the next tile while the two-point half completes
+      int i0 = 0, i1 = 0, i2 = 0;
+      unsigned m0 = 0u, m1 = 0u, m2 = 0u;
+      if (j < g.N) {
+        unravel(g, j, i0, i1, i2);
+        m0 = axis_mask(i0, g.n[0]);
+        m1 = axis_mask(i1, g.n[1]);
+        m2 = DIM > 2 ? axis_mask(i2, g.n[2]) : 4u;
+      }
+      const C<T>* tb = buf0 + lane;
+      const T* tr = reinterpret_cast<const T*>(buf0 + NB * 32) + lane;
+      // half 0: the box entries
+      if (!mbar_wait(&mbar[warp][0], phase & 1u)) fail = true;
+      fail = __any_sync(0xffffffffu, fail);
+      if (fail) break;
+      phase ^= 1u;
+      pending &= ~1u;
+      if (j < g.N)
+        axw = tile_dot_phase<DIM, T, 0>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
+      __syncwarp();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_half(t + stride, 0);
+      // half 1: the two-point entries
+      if (!mbar_wait(&mbar[warp][1], (phase >> 1) & 1u)) fail = true;
+      fail = __any_sync(0xffffffffu, fail);
+      if (fail) break;
+      phase ^= 2u;
+      pending &= ~2u;
+      if (j < g.N)
+        axw = cadd(axw, tile_dot_phase<DIM, T, 1>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2,
+                                                  std::make_integer_sequence<int, S>{}));
+      __syncwarp();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_half(t + stride, 1);
+    } else {
+      if (!mbar_wait(&mbar[warp][s], (phase >> s) & 1u)) fail = true;
+      fail = __any_sync(0xffffffffu, fail);
+      if (fail) break;
+      phase ^= 1u << s;
+      pending &= ~(1u << s);
+      if (j < g.N) {
+        int i0, i1, i2;
+        unravel(g, j, i0, i1, i2);
+        const unsigned m0 = axis_mask(i0, g.n[0]), m1 = axis_mask(i1, g.n[1]), m2 = DIM > 2 ? axis_mask(i2, g.n[2]) : 4u;
+        const C<T>* bs = s ? buf1 : buf0;
+        const C<T>* tb = bs + lane;
+        const T* tr = reinterpret_cast<const T*>(bs + NB * 32) + lane;
+        axw = tile_dot_seq<DIM, T>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
+      }
+    }
     if (j < g.N) {
-      int i0, i1, i2;
-      unravel(g, j, i0, i1, i2);
-      const unsigned m0 = axis_mask(i0, g.n[0]), m1 = axis_mask(i1, g.n[1]), m2 = DIM > 2 ? axis_mask(i2, g.n[2]) : 4u;
-      const C<T>* bs = s ? buf1 : buf0;
-      const C<T>* tb = bs + lane;
-      const T* tr = reinterpret_cast<const T*>(bs + NB * 32) + lane;
-      const C<T> ax = tile_dot_seq<DIM, T>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
-      axw = ax;
+      const C<T> ax = axw;
       if constexpr (MODE == kTmaArnoldi) {
         out[j] = ax;
       } else if constexpr (MODE == kTmaMr) {
@@ -252,17 +336,19 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         }
       }
     }
-    __syncwarp();
-    // the generic-proxy reads of the buffer are done before the copy engine refills it
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    issue(t + STAGES * stride, s);
+    if constexpr (!HALVES) {
+      __syncwarp();
+      // the generic-proxy reads of the buffer are done before the copy engine refills it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t + STAGES * stride, s);
+    }
   }
   if (fail) {
     // wait (bounded) for this warp's copies still in flight (only stages with
     // an issued, unconsumed copy), mark the failure: the weight (kTmaMr) or the
     // tiles this warp did not compute become NaN.  A copy can still be
     // outstanding when the warp leaves only if this second wait also runs out.
-    for (int q = 0; q < STAGES; ++q)
+    for (int q = 0; q < (HALVES ? 2 : STAGES); ++q)
       if ((pending >> q) & 1u) mbar_wait(&mbar[warp][q], (phase >> q) & 1u);
     if (lane == 0) {
       atomicExch(err, 1);
@@ -305,7 +391,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         for (int i = 0; i < nv; ++i) alpha[i] = make_double2(NAN, NAN);
       __syncthreads();
       const ArnoldiState ast = arnoldi_at(tail.st, blockIdx.y);
-      constexpr size_t kScratch = (size_t)WARPS * STAGES * W * 32 * sizeof(C<T>);   // the dynamic shared memory
+      constexpr size_t kScratch = (size_t)WARPS * tile_buffers(STAGES) * W * 32 * sizeof(C<T>);   // dynamic smem
       constexpr size_t kSums = (size_t)WARPS * 64 * sizeof(C<T>);
       if (kSums + (size_t)arnoldi_stage_words(ast.m, kd) * sizeof(double2) <= kScratch) {
         double2* stage = reinterpret_cast<double2*>(tma_smem + kSums);
@@ -328,7 +414,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 }
 
 template <int DIM, int WARPS, int STAGES> constexpr size_t tma_smem_bytes() {
-  return (size_t)WARPS * STAGES * Split<DIM>::W * 32 * sizeof(float2);
+  return (size_t)WARPS * tile_buffers(STAGES) * Split<DIM>::W * 32 * sizeof(float2);
 }
 template <int DIM, int WARPS, int STAGES, int MODE> static bool tma_attr_mode() {
   constexpr int bytes = (int)tma_smem_bytes<DIM, WARPS, STAGES>();
@@ -349,7 +435,8 @@ bool prepare_stencil_tma() {
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if ((size_t)optin < tma_smem_bytes<3, 16, 1>() + 2048 || (size_t)optin < tma_smem_bytes<3, 8, 2>() + 2048) return false;
-  const bool ok = tma_attr<3, 8, 2>() && tma_attr<2, 8, 2>() && tma_attr<3, 16, 1>() && tma_attr<2, 16, 1>();
+  const bool ok = tma_attr<3, 8, 2>() && tma_attr<2, 8, 2>() && tma_attr<3, 16, 1>() && tma_attr<2, 16, 1>() &&
+                  tma_attr<3, 16, kHalves>() && tma_attr<2, 16, kHalves>();
   cudaGetLastError();
   return ok;
 }
@@ -381,6 +468,13 @@ static void launch_variant(const Dims& g, const float2* A, const float2* x, cons
       launch_tma<2, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
     else
       launch_tma<3, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
+  } else if (variant == 3) {
+    if (g.dim == 2)
+      launch_tma<2, 16, kHalves, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd,
+                                       tail);
+    else
+      launch_tma<3, 16, kHalves, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd,
+                                       tail);
   } else {
     if (g.dim == 2)
       launch_tma<2, 16, 1, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
@@ -389,9 +483,11 @@ static void launch_variant(const Dims& g, const float2* A, const float2* x, cons
   }
 }
 
-// variant 1: 16 warps per block, one tile buffer each (95 us per level-1
+// variant 1: 16 warps per block, one tile buffer each (96 us per level-1
 // relaxation launch of the 257x257x129 workload); variant 2: 8 warps, two
-// buffers each (98 us); the plain-load kernel takes 115 us.
+// buffers each (98 us); variant 3: 16 warps, one buffer each refilled in
+// halves, the box half reissued for the next tile before the two-point half
+// is consumed (92 us; the library default); the plain-load kernel takes 115 us.
 void launch_stencil_mr_apply_tma(const Dims& g, const float2* A, const float2* z, const float2* r, float2* w,
                                  double2* partial, unsigned* ticket, double2* alpha, int* err, int blocks, int variant,
                                  cudaStream_t st) {
@@ -405,8 +501,10 @@ void launch_stencil_arnoldi_tma(const Dims& g, const float2* A, const float2* z,
                                 int kd, const KrylovScratch& s, const ArnoldiState& st, int j, int finish, double eta,
                                 int* err, int blocks, int variant, cudaStream_t stream) {
   ArnoldiTail tail{st, s.hb, s.nrm2, j, finish, eta * eta};
-  launch_variant<kTmaArnoldi>(g, A, z, z, w, nullptr, nullptr, s.partial, s.ticket, s.ha, err, blocks, variant, stream, V,
-                              ld, kd, tail);
+  // whole tiles on the coarsest grid: a warp there takes one or two tiles, too
+  // few for the refill in halves to pay (386 against 376 us per coarsest solve)
+  launch_variant<kTmaArnoldi>(g, A, z, z, w, nullptr, nullptr, s.partial, s.ticket, s.ha, err, blocks,
+                              variant == 3 ? 1 : variant, stream, V, ld, kd, tail);
 }
 void launch_stencil_residual_dinv_tma(const Dims& g, const float2* A, const float2* b, const float2* x,
                                       const float2* dinv, float2* r, float2* z, int* err, int blocks, int variant,
