@@ -120,9 +120,10 @@ def parse():
     ap.add_argument("--restart", type=int, default=None)
     ap.add_argument("--coarse-solver", default=None, choices=["auto", "kernels", "cta", "cluster", "grid"],
                     help="form of the coarsest-grid GMRES (same arithmetic; default: the library's choice)")
-    ap.add_argument("--tma", type=int, default=None, choices=[0, 1, 2, 3],
-                    help="stored-stencil applies: 1 bulk copies, 16 warps (library default); 2 bulk copies, 8 warps "
-                         "with two buffers; 3 bulk copies, 16 warps, buffers refilled in halves; 0 plain loads")
+    ap.add_argument("--tma", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="stored-stencil applies: 1 bulk copies, 16 warps; 2 bulk copies, 8 warps with two buffers; "
+                         "3 (library default) / 4 bulk copies, 16 warps, buffers refilled in halves / quarters; "
+                         "0 plain loads")
     ap.add_argument("--outer-df", type=int, default=None, choices=[0, 1],
                     help="outer Krylov iteration with the float32 cycle: 1 double-float (library default), 0 float64")
     ap.add_argument("--cycle", default=None)

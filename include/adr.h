@@ -117,7 +117,8 @@ typedef struct adr_params {
                                           buffers each; 3: 16 warps, one buffer each
                                           refilled in halves (box entries, two-point
                                           entries; the coarsest grid's GMRES step keeps
-                                          whole tiles); 0: plain loads.  Same products;
+                                          whole tiles); 4: the same in quarters; 0:
+                                          plain loads.  Same products;
                                           the sums' order and the weight's block sums
                                           follow the kernel.  Default 3 */
   double shift;                        /* complex shift alpha of the cycle's operator

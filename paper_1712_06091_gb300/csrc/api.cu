@@ -884,7 +884,7 @@ static int validate_params(const adr_params_t& p) {
     return fail(ADR_ERR_ARG, "relax_blocks must be in [0, 10240]");
   if (p.coarse_solver < ADR_COARSE_AUTO || p.coarse_solver > ADR_COARSE_GRID)
     return fail(ADR_ERR_ARG, "unknown coarse_solver");
-  if (p.tma < 0 || p.tma > 3) return fail(ADR_ERR_ARG, "tma must be 0, 1, 2 or 3");
+  if (p.tma < 0 || p.tma > 4) return fail(ADR_ERR_ARG, "tma must be 0, 1, 2, 3 or 4");
   if (!(p.shift >= 0.0 && p.shift <= 100.0)) return fail(ADR_ERR_ARG, "shift must be in [0, 100]");
   if (p.scheme != ADR_SCHEME_2UP && p.scheme != ADR_SCHEME_1UP && p.scheme != ADR_SCHEME_CEN)
     return fail(ADR_ERR_ARG, "scheme must be ADR_SCHEME_2UP, ADR_SCHEME_1UP or ADR_SCHEME_CEN");

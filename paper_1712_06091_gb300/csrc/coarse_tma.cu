@@ -91,29 +91,50 @@ __device__ __forceinline__ C<T> tile_dot_seq(const C<T>* __restrict__ tb, const 
   return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
 
-// One phase of a node's row: the box points (PHASE 0, complex coefficients
-// from tb) or the two-points (PHASE 1, imaginary parts from tr), so that the
-// box half of a tile can be consumed while the other half is still arriving.
-template <int DIM, typename T, int PHASE, int P>
-__device__ __forceinline__ void stencil_term_phase(const C<T>* tb, const T* tr, const C<T>* __restrict__ x, int64_t j,
-                                                   int64_t s1, int64_t s2, unsigned m0, unsigned m1, unsigned m2,
-                                                   C<T>& acc) {
-  if constexpr (PointKind<DIM, P>::two == (PHASE == 1)) stencil_term_smem<DIM, T, P>(tb, tr, x, j, s1, s2, m0, m1, m2, acc);
+// A tile refilled in segments: NSEG = 2 splits it into the box entries and
+// the two-point entries; NSEG = 4 splits each of those in two (slot ranges of
+// the split layout, every boundary a multiple of 256 bytes).  seg_slot(q) is
+// the first complex-word slot of segment q (seg_slot(NSEG) = W).
+template <int DIM, int NSEG> struct Segs {
+  static constexpr int NB = Split<DIM>::NB, NT2 = Split<DIM>::NT / 2, W = Split<DIM>::W;
+  static constexpr int SB = NSEG == 4 ? (NB + 1) / 2 : NB;     // box slots in the first box segment
+  static constexpr int ST = NSEG == 4 ? (NT2 + 1) / 2 : NT2;   // two-point slots in the first two-point segment
+  __host__ __device__ static constexpr int slot(int q) {
+    return NSEG == 2 ? (q == 0 ? 0 : q == 1 ? NB : W)
+                     : (q == 0 ? 0 : q == 1 ? SB : q == 2 ? NB : q == 3 ? NB + ST : W);
+  }
+  // the segment that holds point P's coefficient
+  template <int P> __host__ __device__ static constexpr int of() {
+    return !PointKind<DIM, P>::two ? (NSEG == 4 && PointKind<DIM, P>::part >= SB ? 1 : 0)
+                                   : (NSEG == 2 ? 1 : (PointKind<DIM, P>::part >= 2 * ST ? 3 : 2));
+  }
+};
+
+// A node's terms whose coefficients lie in segment Q.
+template <int DIM, typename T, int NSEG, int Q, int P>
+__device__ __forceinline__ void stencil_term_seg(const C<T>* tb, const T* tr, const C<T>* __restrict__ x, int64_t j,
+                                                 int64_t s1, int64_t s2, unsigned m0, unsigned m1, unsigned m2,
+                                                 C<T>& acc) {
+  if constexpr (Segs<DIM, NSEG>::template of<P>() == Q) stencil_term_smem<DIM, T, P>(tb, tr, x, j, s1, s2, m0, m1, m2, acc);
 }
-template <int DIM, typename T, int PHASE, int... P>
-__device__ __forceinline__ C<T> tile_dot_phase(const C<T>* __restrict__ tb, const T* __restrict__ tr,
-                                               const C<T>* __restrict__ x, int64_t j, int64_t s1, int64_t s2, unsigned m0,
-                                               unsigned m1, unsigned m2, std::integer_sequence<int, P...>) {
+template <int DIM, typename T, int NSEG, int Q, int... P>
+__device__ __forceinline__ C<T> tile_dot_seg(const C<T>* __restrict__ tb, const T* __restrict__ tr,
+                                             const C<T>* __restrict__ x, int64_t j, int64_t s1, int64_t s2, unsigned m0,
+                                             unsigned m1, unsigned m2, std::integer_sequence<int, P...>) {
   C<T> acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
-  (stencil_term_phase<DIM, T, PHASE, P>(tb, tr, x, j, s1, s2, m0, m1, m2, acc[P & 3]), ...);
+  (stencil_term_seg<DIM, T, NSEG, Q, P>(tb, tr, x, j, s1, s2, m0, m1, m2, acc[P & 3]), ...);
   return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
 
-// Tile buffers per warp for STAGES: 1 and 2 whole tiles; kHalves one tile
-// refilled in halves (box entries, then two-point entries, each half reissued
-// for the warp's next tile as soon as it has been consumed).
+// Tile buffers per warp for STAGES: 1 and 2 whole tiles; kHalves and
+// kQuarters one tile refilled in 2 or 4 segments (each segment reissued for
+// the warp's next tile as soon as it has been consumed).
 constexpr int kHalves = 3;
+constexpr int kQuarters = 4;
 __host__ __device__ constexpr int tile_buffers(int stages) { return stages == 2 ? 2 : 1; }
+__host__ __device__ constexpr int tile_segments(int stages) {
+  return stages == kHalves ? 2 : (stages == kQuarters ? 4 : 0);
+}
 
 // Modes of the streamed stencil kernel.
 enum { kTmaMr = 0, kTmaApply = 1, kTmaResid = 2, kTmaArnoldi = 3 };
@@ -163,7 +184,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   constexpr int W = Split<DIM>::W, NB = Split<DIM>::NB, S = PatternSize<DIM>::value;
   constexpr unsigned kTileBytes = W * 32 * sizeof(C<T>);
   extern __shared__ __align__(128) unsigned char tma_smem[];
-  __shared__ __align__(8) uint64_t mbar[WARPS][2];
+  __shared__ __align__(8) uint64_t mbar[WARPS][4];
   __shared__ double2 sh[32 * 2];
   __shared__ int s_fail;
   if (BT) {
@@ -181,13 +202,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     batch_shift(1, err);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr bool HALVES = STAGES == kHalves;
-  constexpr unsigned kBoxBytes = NB * 32 * sizeof(C<T>);          // first half: the box entries
+  constexpr int NSEG = tile_segments(STAGES);   // 0: whole-tile copies
+  using SG = Segs<DIM, NSEG == 0 ? 2 : NSEG>;
   C<T>* const buf0 = reinterpret_cast<C<T>*>(tma_smem) + (size_t)warp * tile_buffers(STAGES) * W * 32;
   C<T>* const buf1 = buf0 + (STAGES == 2 ? W * 32 : 0);
   if (threadIdx.x == 0) s_fail = 0;
   if (lane == 0) {
-    for (int q = 0; q < (HALVES ? 2 : STAGES); ++q) mbar_init(&mbar[warp][q], 1);
+    for (int q = 0; q < (NSEG ? NSEG : STAGES); ++q) mbar_init(&mbar[warp][q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -205,21 +226,20 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       pending |= 1u << s;
     }
   };
-  // kHalves: half h (0 box, 1 two-points) of tile t into its place in buf0, on mbar[warp][h]
-  auto issue_half = [&](int64_t t, int h) {
+  // segment q of tile t into its place in buf0, on mbar[warp][q]
+  auto issue_seg = [&](int64_t t, int q) {
     if (t < ntiles) {
       if (lane == 0) {
-        const unsigned bytes = h ? kTileBytes - kBoxBytes : kBoxBytes;
-        const size_t off = h ? (size_t)NB * 32 : 0;
-        mbar_expect_tx(&mbar[warp][h], bytes);
-        bulk_load(buf0 + off, A + t * (int64_t)W * 32 + off, bytes, &mbar[warp][h]);
+        const size_t off = (size_t)SG::slot(q) * 32;
+        const unsigned bytes = (unsigned)((SG::slot(q + 1) - SG::slot(q)) * 32 * sizeof(C<T>));
+        mbar_expect_tx(&mbar[warp][q], bytes);
+        bulk_load(buf0 + off, A + t * (int64_t)W * 32 + off, bytes, &mbar[warp][q]);
       }
-      pending |= 1u << h;
+      pending |= 1u << q;
     }
   };
-  if constexpr (HALVES) {
-    issue_half(t0, 0);
-    issue_half(t0, 1);
+  if constexpr (NSEG > 0) {
+    for (int q = 0; q < NSEG; ++q) issue_seg(t0, q);
   } else {
     issue(t0, 0);
     if (STAGES > 1) issue(t0 + stride, 1);
@@ -233,8 +253,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   for (; t < ntiles; t += stride, s = STAGES == 2 ? s ^ 1 : 0) {
     const int64_t j = t * 32 + lane;
     C<T> axw = czero<T>();
-    if constexpr (HALVES) {
-      // box half: consume, then reissue it for the next tile while the two-point half completes
+    if constexpr (NSEG > 0) {
+      // each segment: wait, add its terms, reissue it for the warp's next tile
       int i0 = 0, i1 = 0, i2 = 0;
       unsigned m0 = 0u, m1 = 0u, m2 = 0u;
       if (j < g.N) {
@@ -245,29 +265,25 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       }
       const C<T>* tb = buf0 + lane;
       const T* tr = reinterpret_cast<const T*>(buf0 + NB * 32) + lane;
-      // half 0: the box entries
-      if (!mbar_wait(&mbar[warp][0], phase & 1u)) fail = true;
-      fail = __any_sync(0xffffffffu, fail);
-      if (fail) break;
-      phase ^= 1u;
-      pending &= ~1u;
-      if (j < g.N)
-        axw = tile_dot_phase<DIM, T, 0>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2, std::make_integer_sequence<int, S>{});
-      __syncwarp();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_half(t + stride, 0);
-      // half 1: the two-point entries
-      if (!mbar_wait(&mbar[warp][1], (phase >> 1) & 1u)) fail = true;
-      fail = __any_sync(0xffffffffu, fail);
-      if (fail) break;
-      phase ^= 2u;
-      pending &= ~2u;
-      if (j < g.N)
-        axw = cadd(axw, tile_dot_phase<DIM, T, 1>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2,
-                                                  std::make_integer_sequence<int, S>{}));
-      __syncwarp();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_half(t + stride, 1);
+      auto segment = [&](auto qc) -> bool {
+        constexpr int q = decltype(qc)::value;
+        if (!mbar_wait(&mbar[warp][q], (phase >> q) & 1u)) fail = true;
+        fail = __any_sync(0xffffffffu, fail);
+        if (fail) return false;
+        phase ^= 1u << q;
+        pending &= ~(1u << q);
+        if (j < g.N)
+          axw = cadd(axw, tile_dot_seg<DIM, T, NSEG == 0 ? 2 : NSEG, q>(tb, tr, x, j, g.s1, g.s2, m0, m1, m2,
+                                                                        std::make_integer_sequence<int, S>{}));
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_seg(t + stride, q);
+        return true;
+      };
+      bool ok = segment(std::integral_constant<int, 0>{}) && segment(std::integral_constant<int, 1>{});
+      if constexpr (NSEG == 4)
+        ok = ok && segment(std::integral_constant<int, 2>{}) && segment(std::integral_constant<int, 3>{});
+      if (!ok) break;
     } else {
       if (!mbar_wait(&mbar[warp][s], (phase >> s) & 1u)) fail = true;
       fail = __any_sync(0xffffffffu, fail);
@@ -336,7 +352,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         }
       }
     }
-    if constexpr (!HALVES) {
+    if constexpr (NSEG == 0) {
       __syncwarp();
       // the generic-proxy reads of the buffer are done before the copy engine refills it
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -348,7 +364,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     // an issued, unconsumed copy), mark the failure: the weight (kTmaMr) or the
     // tiles this warp did not compute become NaN.  A copy can still be
     // outstanding when the warp leaves only if this second wait also runs out.
-    for (int q = 0; q < (HALVES ? 2 : STAGES); ++q)
+    for (int q = 0; q < (NSEG ? NSEG : STAGES); ++q)
       if ((pending >> q) & 1u) mbar_wait(&mbar[warp][q], (phase >> q) & 1u);
     if (lane == 0) {
       atomicExch(err, 1);
@@ -436,7 +452,8 @@ bool prepare_stencil_tma() {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if ((size_t)optin < tma_smem_bytes<3, 16, 1>() + 2048 || (size_t)optin < tma_smem_bytes<3, 8, 2>() + 2048) return false;
   const bool ok = tma_attr<3, 8, 2>() && tma_attr<2, 8, 2>() && tma_attr<3, 16, 1>() && tma_attr<2, 16, 1>() &&
-                  tma_attr<3, 16, kHalves>() && tma_attr<2, 16, kHalves>();
+                  tma_attr<3, 16, kHalves>() && tma_attr<2, 16, kHalves>() && tma_attr<3, 16, kQuarters>() &&
+                  tma_attr<2, 16, kQuarters>();
   cudaGetLastError();
   return ok;
 }
@@ -468,6 +485,13 @@ static void launch_variant(const Dims& g, const float2* A, const float2* x, cons
       launch_tma<2, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
     else
       launch_tma<3, 8, 2, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd, tail);
+  } else if (variant == 4) {
+    if (g.dim == 2)
+      launch_tma<2, 16, kQuarters, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld,
+                                         kd, tail);
+    else
+      launch_tma<3, 16, kQuarters, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld,
+                                         kd, tail);
   } else if (variant == 3) {
     if (g.dim == 2)
       launch_tma<2, 16, kHalves, MODE>(g, A, x, aux, out, dinv, out2, partial, ticket, alpha, err, blocks, st, V, ld, kd,
@@ -504,7 +528,7 @@ void launch_stencil_arnoldi_tma(const Dims& g, const float2* A, const float2* z,
   // whole tiles on the coarsest grid: a warp there takes one or two tiles, too
   // few for the refill in halves to pay (386 against 376 us per coarsest solve)
   launch_variant<kTmaArnoldi>(g, A, z, z, w, nullptr, nullptr, s.partial, s.ticket, s.ha, err, blocks,
-                              variant == 3 ? 1 : variant, stream, V, ld, kd, tail);
+                              variant >= 3 ? 1 : variant, stream, V, ld, kd, tail);
 }
 void launch_stencil_residual_dinv_tma(const Dims& g, const float2* A, const float2* b, const float2* x,
                                       const float2* dinv, float2* r, float2* z, int* err, int blocks, int variant,

@@ -16,7 +16,7 @@ BAD_PARAMS = [
     ("restart", 65, "restart"), ("precond_precision", 3, "precision"),
     ("near_source", 0, "near_source"), ("reorth_eta", -1.0, "reorth_eta"),
     ("adjoint", 2, "adjoint"), ("relax_blocks", -1, "relax_blocks"), ("relax_blocks", 10241, "relax_blocks"),
-    ("coarse_solver", 99, "coarse_solver"), ("tma", 4, "tma"),
+    ("coarse_solver", 99, "coarse_solver"), ("tma", 5, "tma"),
     ("scheme", 3, "scheme"), ("prec_scheme", 9, "prec_scheme"), ("rescale", 2, "rescale"),
     ("kcycle_threshold", -0.1, "kcycle_threshold"), ("kcycle_threshold", float("nan"), "kcycle_threshold"),
     ("outer_df", 2, "outer_df"),

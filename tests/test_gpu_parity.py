@@ -325,13 +325,13 @@ def test_coarse_solver_forms(adrlib, cuda, name, levels, form):
 
 
 @pytest.mark.parametrize("name", ["marine2d_65", "layered3d_17", "ragged2d_37x21", "corner3d_9x11x13"])
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_bulk_copy_relaxation_matches_plain_loads(adrlib, cuda, name, variant):
     """The relaxation apply that streams coefficient tiles with bulk copies
     does each node's products as the plain-load kernel; the block sums of the
-    minimal-residual weight follow its grid (and variant 3 adds a node's box
-    and two-point terms in two groups), so cycles agree to float32 rounding
-    and whole solves to their tolerance."""
+    minimal-residual weight follow its grid (and variants 3 and 4 add a node's
+    terms in two or four groups), so cycles agree to float32 rounding and
+    whole solves to their tolerance."""
     P, params, op_tma = make_operator(name, precision="f32", tma=variant, levels=3)
     _, _, op_plain = make_operator(name, precision="f32", tma=0, levels=3)
     r = _cvec(W.random_complex(P.N, 14), torch.complex64)
@@ -343,7 +343,7 @@ def test_bulk_copy_relaxation_matches_plain_loads(adrlib, cuda, name, variant):
     assert rel(a1.cpu().numpy(), a0.cpu().numpy()) <= 1e-6
 
 
-@pytest.mark.parametrize("variant,blocks", [(1, 1), (1, 2), (2, 1), (3, 1), (3, 2)])
+@pytest.mark.parametrize("variant,blocks", [(1, 1), (1, 2), (2, 1), (3, 1), (3, 2), (4, 1), (4, 2)])
 def test_multi_tile_relaxation_loops_against_oracle(adrlib, cuda, variant, blocks):
     """The steady state of the streamed relaxation (buffer reuse, mbarrier phase
     flips, refills after the proxy fence) and of the finest-grid apply's
