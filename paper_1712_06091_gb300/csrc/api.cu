@@ -1356,8 +1356,8 @@ static int fgmres(Op& op, bool adj, const double2* b, double2* a, int use_x0, do
         const int pk = prof_begin(op, ADR_PROF_OUTER_APPLY, st);
         launch_packed_apply_df(op.g0, fo, op.packed_df, op.h32.lv[0].x, w, NB, Zf + (int64_t)j * NB, st);
         prof_end(op, pk, st);
-        launch_df_selective(Vf, 2 * NB, NB, j + 1, w, op.g0, op.ks, op.ost, j, op.p.reorth_eta, st);
-        launch_df_scale(w, NB, op.ks.nrm2, j + 1 < m ? cyc : nullptr, op.g0, st);
+        launch_df_selective(Vf, 2 * NB, NB, j + 1, w, j + 1 < m ? cyc : nullptr, op.g0, op.ks, op.ost, j,
+                            op.p.reorth_eta, st);
       } else {
         double2* vj = op.V + (int64_t)j * NB;
         double2* zj = op.Z + (int64_t)j * NB;

@@ -159,38 +159,75 @@ __device__ __forceinline__ bool df_update_norm(const float2* __restrict__ V, int
   return last_block_rt(1, blk, partial, ticket, nrm2, sh);
 }
 
-// The four passes of launch_cgs_selective (krylov.cu), same scalar logic:
-//   A: ha = V^H w, ha[k] = |w|^2
-//   B: w -= V ha, |w'|^2, keep the column when |w'|^2 >= eta^2 |w|^2
+// The selective Gram-Schmidt step in four passes:
+//   A: ha = V^H w, ha[k] = |w|^2; the last block takes the selective
+//      decision from Pythagoras, |w - V ha|^2 = |w|^2 - |ha|^2 (V
+//      orthonormal; reading M2's test, as on the coarsest grid): a single
+//      pass keeps the column, writes the Arnoldi column and 1/|w'|;
+//   B: w' = w - V ha, normalised on the way when the single pass holds (the
+//      normalisation pass disappears), its high plane into the cycle's input;
 //   C: (only if flagged) hb = V^H w'
-//   D: (only if flagged) w' -= V hb, |w''|^2, the Arnoldi column from ha + hb
+//   D: (only if flagged) w' -= V hb, |w''|^2, the Arnoldi column from ha + hb;
+//      k_df_scale then normalises (it returns at once after a single pass).
 __global__ void __launch_bounds__(256, 4) k_df_dots_norm(const float2* __restrict__ V, int64_t ld, int64_t lo, int k,
-                                                      const float2* w, Dims g, KrylovScratch s) {
+                                                      const float2* w, Dims g, KrylovScratch s, ArnoldiState st, int j,
+                                                      double eta2) {
   if (resolve(g)) return;
   __shared__ double2 sh[32 * (kDfChunk + 1)];
   __shared__ double2 blk[kMaxKrylov + 2];
   shift_nodes(g, V, w);
   s = scratch_at(s, blockIdx.y);
   df_block_dots(V, ld, lo, k, w, g.N, true, blk, reinterpret_cast<float4*>(sh));
-  last_block_rt(k + 1, blk, s.partial, s.ticket, s.ha, sh);
+  if (last_block_rt(k + 1, blk, s.partial, s.ticket, s.ha, sh) && threadIdx.x == 0)
+    coarse_select_dev(s.ha, s.hb, k, eta2, arnoldi_at(st, blockIdx.y), j, 0, s.nrm2);
 }
 
-__global__ void __launch_bounds__(256) k_df_update_test(const float2* __restrict__ V, int64_t ld, int64_t lo, int k,
-                                                        float2* w, Dims g, KrylovScratch s, ArnoldiState st, int j,
-                                                        double eta2) {
+// w' = w - V ha; after a single pass also w' / |w'| and its high plane into
+// cyc (when not null).
+__global__ void __launch_bounds__(256) k_df_update(const float2* __restrict__ V, int64_t ld, int64_t lo, int k, float2* w,
+                                                   float2* cyc, Dims g, KrylovScratch s) {
   if (resolve(g)) return;
   shift_nodes(g, V, w);
+  shift_nodes_opt(g, cyc);
   s = scratch_at(s, blockIdx.y);
-  if (df_update_norm(V, ld, lo, k, w, g.N, s.ha, s.partial, s.ticket, s.nrm2) && threadIdx.x == 0) {
-    const double t = s.nrm2->x;
-    if (t >= eta2 * s.ha[k].x) {
-      s.ha[k].y = 0.0;
-      for (int i = 0; i < k; ++i) s.hb[i] = make_double2(0.0, 0.0);
-      s.nrm2->y = t > 0.0 ? rsqrt(t) : 0.0;
-      if (st.m > 0) arnoldi_column_dev(arnoldi_at(st, blockIdx.y), j, s.ha, s.hb, t);
-    } else {
-      s.ha[k].y = 1.0;
+  __shared__ float4 coef[kMaxKrylov + 1];   // -ha_i: (re hi, re lo, im hi, im lo)
+  __shared__ float2 s_inv;
+  __shared__ int s_norm;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const float2 r = df_split(-s.ha[i].x), m = df_split(-s.ha[i].y);
+    coef[i] = make_float4(r.x, r.y, m.x, m.y);
+  }
+  if (threadIdx.x == 0) {
+    s_norm = s.ha[k].y == 0.0;
+    s_inv = df_split(s.nrm2->y);
+  }
+  __syncthreads();
+  const bool norm = s_norm;
+  const float2 inv = s_inv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.N; e += (int64_t)gridDim.x * blockDim.x) {
+    const float2 wh = w[e], wl = w[e + lo];
+    DfSum ar{wh.x, wl.x}, ai{wh.y, wl.y};
+#pragma unroll 4
+    for (int i = 0; i < k; ++i) {
+      const float4 cc = coef[i];
+      const float2* v = V + (int64_t)i * ld + e;
+      const float2 vh = __ldg(v), vl = __ldg(v + lo);
+      df_add_prod2(ar, vh.x, vl.x, cc.x, cc.y);
+      df_add_prod2(ar, -vh.y, -vl.y, cc.z, cc.w);
+      df_add_prod2(ai, vh.x, vl.x, cc.z, cc.w);
+      df_add_prod2(ai, vh.y, vl.y, cc.x, cc.y);
     }
+    float2 r = df_pair(ar), m = df_pair(ai);
+    if (norm) {
+      DfSum a{0.f, 0.f}, b{0.f, 0.f};
+      df_add_prod2(a, r.x, r.y, inv.x, inv.y);
+      df_add_prod2(b, m.x, m.y, inv.x, inv.y);
+      r = df_pair(a);
+      m = df_pair(b);
+      if (cyc) cyc[e] = make_float2(r.x, m.x);
+    }
+    w[e] = make_float2(r.x, m.x);
+    w[e + lo] = make_float2(r.y, m.y);
   }
 }
 
@@ -219,25 +256,28 @@ __global__ void __launch_bounds__(256) k_df_reorth_update(const float2* __restri
   }
 }
 
-// w = w / |w| (reciprocal norm from nrm2->y), and its high plane into cyc
-// when cyc is not null.
-__global__ void k_df_scale(float2* w, int64_t lo, const double2* __restrict__ nrm2, float2* cyc, Dims g) {
+// After a second Gram-Schmidt pass: w = w / |w| (reciprocal norm from
+// nrm2->y) and its high plane into cyc when cyc is not null.  After a single
+// pass (ha[k].y == 0) k_df_update has normalised already: nothing to do.
+__global__ void k_df_scale(float2* w, int64_t lo, const double2* __restrict__ nrm2, float2* cyc, Dims g,
+                           KrylovScratch s, int k) {
   if (resolve(g)) return;
+  if (scratch_at(s, blockIdx.y).ha[k].y == 0.0) return;   // uniform over the problem's blocks
   __shared__ float2 inv;
   if (threadIdx.x == 0) inv = df_split(nrm2[blockIdx.y].y);
   __syncthreads();
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= g.N) return;
   shift_nodes(g, w);
   shift_nodes_opt(g, cyc);
-  const float2 wh = w[e], wl = w[e + lo];
-  DfSum a{0.f, 0.f}, b{0.f, 0.f};
-  df_add_prod2(a, wh.x, wl.x, inv.x, inv.y);
-  df_add_prod2(b, wh.y, wl.y, inv.x, inv.y);
-  const float2 r = df_pair(a), m = df_pair(b);
-  w[e] = make_float2(r.x, m.x);
-  w[e + lo] = make_float2(r.y, m.y);
-  if (cyc) cyc[e] = make_float2(r.x, m.x);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.N; e += (int64_t)gridDim.x * blockDim.x) {
+    const float2 wh = w[e], wl = w[e + lo];
+    DfSum a{0.f, 0.f}, b{0.f, 0.f};
+    df_add_prod2(a, wh.x, wl.x, inv.x, inv.y);
+    df_add_prod2(b, wh.y, wl.y, inv.x, inv.y);
+    const float2 r = df_pair(a), m = df_pair(b);
+    w[e] = make_float2(r.x, m.x);
+    w[e + lo] = make_float2(r.y, m.y);
+    if (cyc) cyc[e] = make_float2(r.x, m.x);
+  }
 }
 
 // out = r / |r| for a float64 r, as double-float planes (high plane also into
@@ -287,19 +327,17 @@ __global__ void k_df_combine(double2* x, const float2* __restrict__ Z, int64_t l
   x[e] = v;
 }
 
-void launch_df_selective(const float2* V, int64_t ld, int64_t lo, int k, float2* w, const Dims& g,
+void launch_df_selective(const float2* V, int64_t ld, int64_t lo, int k, float2* w, float2* cyc, const Dims& g,
                          const KrylovScratch& s, const ArnoldiState& st, int j, double eta, cudaStream_t stream) {
   // eta >= 1: the second pass always runs (as launch_cgs2)
   const double eta2 = eta < 1.0 ? eta * eta : INFINITY;
   const dim3 gdots(df_blocks(g.N, k + 2, 4), g.B), gupd(df_blocks(g.N, k + 2, 4), g.B);
-  count_launches(1), k_df_dots_norm<<<gdots, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
-  count_launches(1), k_df_update_test<<<gupd, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j, eta2);
+  count_launches(1), k_df_dots_norm<<<gdots, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j, eta2);
+  count_launches(1), k_df_update<<<gupd, 256, 0, stream>>>(V, ld, lo, k, w, cyc, g, s);
   count_launches(1), k_df_reorth_dots<<<gdots, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
   count_launches(1), k_df_reorth_update<<<gupd, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j);
-}
-
-void launch_df_scale(float2* w, int64_t lo, const double2* nrm2, float2* cyc, const Dims& g, cudaStream_t st) {
-  count_launches(1), k_df_scale<<<dim3(blocks_for(g.N, 256), g.B), 256, 0, st>>>(w, lo, nrm2, cyc, g);
+  // grid-stride over one resident wave: after a single pass every block returns at once
+  count_launches(1), k_df_scale<<<gupd, 256, 0, stream>>>(w, lo, s.nrm2, cyc, g, s, k);
 }
 
 void launch_df_from_double(const double2* r, float2* out, int64_t lo, const double2* nrm2, float2* cyc, const Dims& g,

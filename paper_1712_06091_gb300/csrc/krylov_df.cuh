@@ -9,14 +9,12 @@
 namespace adr {
 
 // Gram-Schmidt step j of the outer FGMRES on the double-float basis V (k
-// vectors) and the new vector w: the selective passes of
-// launch_cgs_selective (eta >= 1: the second pass always), the Arnoldi
-// column and its Givens rotation in st, |w|^2 and 1/|w| in s.nrm2.
-void launch_df_selective(const float2* V, int64_t ld, int64_t lo, int k, float2* w, const Dims& g,
+// vectors) and the new vector w: the selective passes (the decision from
+// Pythagoras after the first pass's dots; eta >= 1: the second pass always),
+// the Arnoldi column and its Givens rotation in st, |w|^2 and 1/|w| in
+// s.nrm2, and w normalised in place with its high plane in cyc (may be null).
+void launch_df_selective(const float2* V, int64_t ld, int64_t lo, int k, float2* w, float2* cyc, const Dims& g,
                          const KrylovScratch& s, const ArnoldiState& st, int j, double eta, cudaStream_t stream);
-// w = w / |w| in place (1/|w| from nrm2->y per problem); the high plane also
-// into cyc (float32, may be null).
-void launch_df_scale(float2* w, int64_t lo, const double2* nrm2, float2* cyc, const Dims& g, cudaStream_t st);
 // out = r / |r| from a float64 r (1/|r| from nrm2->y per problem); the high
 // plane also into cyc (may be null).
 void launch_df_from_double(const double2* r, float2* out, int64_t lo, const double2* nrm2, float2* cyc, const Dims& g,
