@@ -23,48 +23,66 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#ifndef __CUDA_ARCH__
+#include <cmath>
+#endif
 
 namespace adr {
 
 struct DfSum { float s, t; };   // value s + t
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+// Round-to-nearest float32 operations: the device intrinsics (never
+// contracted into an FMA), or plain IEEE operations when this header is
+// compiled for the host (the host-side checks of the transformations).
+#ifdef __CUDA_ARCH__
+#define ADR_DF_ADD(a, b) __fadd_rn(a, b)
+#define ADR_DF_SUB(a, b) __fsub_rn(a, b)
+#define ADR_DF_MUL(a, b) __fmul_rn(a, b)
+#define ADR_DF_FMA(a, b, c) __fmaf_rn(a, b, c)
+#else
+#define ADR_DF_ADD(a, b) ((a) + (b))
+#define ADR_DF_SUB(a, b) ((a) - (b))
+#define ADR_DF_MUL(a, b) ((a) * (b))
+#define ADR_DF_FMA(a, b, c) std::fmaf(a, b, c)
+#endif
+
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = ADR_DF_ADD(a, b);
+  const float bb = ADR_DF_SUB(s, a);
+  e = ADR_DF_ADD(ADR_DF_SUB(a, ADR_DF_SUB(s, bb)), ADR_DF_SUB(b, bb));
 }
 
 // a += p + q, p added exactly, q (small) into the tail.
-__device__ __forceinline__ void df_acc(DfSum& a, float p, float q) {
+__host__ __device__ __forceinline__ void df_acc(DfSum& a, float p, float q) {
   float s, u;
   two_sum(a.s, p, s, u);
   a.s = s;
-  a.t = __fadd_rn(a.t, __fadd_rn(u, q));
+  a.t = ADR_DF_ADD(a.t, ADR_DF_ADD(u, q));
 }
 
 // a += (c_hi + c_lo) x for a float32 x.
-__device__ __forceinline__ void df_add_prod(DfSum& a, float c_hi, float c_lo, float x) {
-  const float p = __fmul_rn(c_hi, x);
-  float e = __fmaf_rn(c_hi, x, -p);
-  e = __fmaf_rn(c_lo, x, e);
+__host__ __device__ __forceinline__ void df_add_prod(DfSum& a, float c_hi, float c_lo, float x) {
+  const float p = ADR_DF_MUL(c_hi, x);
+  float e = ADR_DF_FMA(c_hi, x, -p);
+  e = ADR_DF_FMA(c_lo, x, e);
   df_acc(a, p, e);
 }
 
 // a += (x_hi + x_lo)(y_hi + y_lo).
-__device__ __forceinline__ void df_add_prod2(DfSum& a, float xh, float xl, float yh, float yl) {
-  const float p = __fmul_rn(xh, yh);
-  float e = __fmaf_rn(xh, yh, -p);
-  e = __fmaf_rn(xh, yl, e);
-  e = __fmaf_rn(xl, yh, e);
+__host__ __device__ __forceinline__ void df_add_prod2(DfSum& a, float xh, float xl, float yh, float yl) {
+  const float p = ADR_DF_MUL(xh, yh);
+  float e = ADR_DF_FMA(xh, yh, -p);
+  e = ADR_DF_FMA(xh, yl, e);
+  e = ADR_DF_FMA(xl, yh, e);
   df_acc(a, p, e);
 }
 
 // a += b
-__device__ __forceinline__ void df_add(DfSum& a, const DfSum& b) { df_acc(a, b.s, b.t); }
+__host__ __device__ __forceinline__ void df_add(DfSum& a, const DfSum& b) { df_acc(a, b.s, b.t); }
 
 // The normalised pair (hi, lo) of s + t: hi = fl(s + t).  Two-sum, not the
 // fast form: after cancellation the tail can exceed s.
-__device__ __forceinline__ float2 df_pair(const DfSum& a) {
+__host__ __device__ __forceinline__ float2 df_pair(const DfSum& a) {
   float h, l;
   two_sum(a.s, a.t, h, l);
   return make_float2(h, l);
@@ -72,7 +90,7 @@ __device__ __forceinline__ float2 df_pair(const DfSum& a) {
 
 // Widened to float64 (two conversions and an add: per thread once, not per
 // element).
-__device__ __forceinline__ double df_double(const DfSum& a) { return (double)a.s + (double)a.t; }
+__host__ __device__ __forceinline__ double df_double(const DfSum& a) { return (double)a.s + (double)a.t; }
 
 // The float32 pair of a float64 value (|v - hi - lo| <= 2^-48 |v|).
 __host__ __device__ __forceinline__ float2 df_split(double v) {

@@ -21,3 +21,20 @@ def test_fast_division_matches_integer_division(tmp_path):
                     os.path.join(HERE, "native", "fast_div_check.cu")], check=True, capture_output=True)
     out = subprocess.run([exe], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
+def test_double_float_transformations(tmp_path):
+    """The double-float primitives of the outer Krylov kernels (two-sum,
+    the FMA two-product, the float64 split and the normalisation), compiled
+    for the host from the library's own header: exactness where the
+    transformations are exact, and a running sum of 256 products within
+    256 x 2^-46 of the terms' magnitude sum against an exact long double
+    reference."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "df_check")
+    subprocess.run([nvcc, "-std=c++17", "-Xcompiler", "-ffp-contract=off", "-o", exe,
+                    os.path.join(HERE, "native", "df_check.cu")], check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
