@@ -42,3 +42,20 @@ def test_unknown_iterations(bench):
 def test_scale_to_workload(bench):
     # 10 s for 100 nodes x 5 iterations, scaled to 1000 nodes x 50 iterations
     assert bench.scale_to_workload(10.0, 100, 5, 1000, 50) == pytest.approx((100 * 5 / 10.0) / (1000 * 50))
+
+
+def test_cycle_bytes_two_level_v_cycle(bench):
+    # 3D, 1000 fine and 125 coarse nodes, one sweep each side, a 2-step coarsest GMRES (selective
+    # second pass not counted at eta 0.1).  Per fine node: pre-smoothing 24 (z = D^{-1} b) + 56 (packed
+    # row) + 24 (z, r, w) + 40 (x = alpha z, r -= alpha w, no next z) = 144; post-smoothing 56 + 40
+    # (residual with D^{-1}) + 56 + 24 + 48 = 224.  Transfers 8 + 8/8 and 8/8 + 16 per fine node.
+    # Coarsest per node: 40 (|b|, V_0, z) + 456 (step 0: 432 stencil + z, w + V_0) + 48 (V_1, z)
+    # + 464 (step 1) + 32 (x = D^{-1} V y) = 1040.
+    pd = {"cycle": "V", "pre_sweeps": [1, 1], "post_sweeps": [1, 1], "coarse_iterations": 2, "kcycle_iterations": 2,
+          "reorth_eta": 0.1}
+    levels = [{"nodes": 1000}, {"nodes": 125}]
+    assert bench.cycle_bytes(levels, pd) == 144 * 1000 + (8 * 1000 + 8 * 125) + 1040 * 125 + (8 * 125 + 16 * 1000) \
+        + 224 * 1000
+    # classical Gram-Schmidt twice on the coarsest grid adds 2 C + 2 (j + 1) C per node and step
+    pd2 = dict(pd, reorth_eta=2.0)
+    assert bench.cycle_bytes(levels, pd2) - bench.cycle_bytes(levels, pd) == (32 + 48) * 125
