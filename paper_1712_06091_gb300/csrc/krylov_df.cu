@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256, 4) k_df_dots_norm(const float2* __restric
 
 // w' = w - V ha; after a single pass also w' / |w'| and its high plane into
 // cyc (when not null).
-__global__ void __launch_bounds__(256) k_df_update(const float2* __restrict__ V, int64_t ld, int64_t lo, int k, float2* w,
+__global__ void __launch_bounds__(256, 6) k_df_update(const float2* __restrict__ V, int64_t ld, int64_t lo, int k, float2* w,
                                                    float2* cyc, Dims g, KrylovScratch s) {
   if (resolve(g)) return;
   shift_nodes(g, V, w);
@@ -332,8 +332,13 @@ void launch_df_selective(const float2* V, int64_t ld, int64_t lo, int k, float2*
   // eta >= 1: the second pass always runs (as launch_cgs2)
   const double eta2 = eta < 1.0 ? eta * eta : INFINITY;
   const dim3 gdots(df_blocks(g.N, k + 2, 4), g.B), gupd(df_blocks(g.N, k + 2, 4), g.B);
+  // the update holds 40 registers, so six blocks fit on an SM where the dots'
+  // 64 allow four: a grid of four per SM left it at half occupancy, waiting on
+  // its loads (long-scoreboard stalls; elementwise, so the grid does not
+  // change its result)
+  const dim3 gew(df_blocks(g.N, k + 2, 6), g.B);
   count_launches(1), k_df_dots_norm<<<gdots, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j, eta2);
-  count_launches(1), k_df_update<<<gupd, 256, 0, stream>>>(V, ld, lo, k, w, cyc, g, s);
+  count_launches(1), k_df_update<<<gew, 256, 0, stream>>>(V, ld, lo, k, w, cyc, g, s);
   count_launches(1), k_df_reorth_dots<<<gdots, 256, 0, stream>>>(V, ld, lo, k, w, g, s);
   count_launches(1), k_df_reorth_update<<<gupd, 256, 0, stream>>>(V, ld, lo, k, w, g, s, st, j);
   // grid-stride over one resident wave: after a single pass every block returns at once
