@@ -3,9 +3,21 @@
 // back substitution for the least-squares coefficients.
 #pragma once
 
+#include <cmath>
+
 #include "krylov.cuh"
 
 namespace adr {
+
+// 1/sqrt(v): the device's reciprocal square root, or 1/sqrt on the host
+// (where these helpers are compiled for the host-side checks).
+__host__ __device__ __forceinline__ double arnoldi_rsqrt(double v) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(v);
+#else
+  return 1.0 / std::sqrt(v);
+#endif
+}
 
 // These run on one thread, so their cost is the latency of a float64
 // dependency chain.  Measured on GB300 (one thread, clock64): a dependent
@@ -17,12 +29,12 @@ namespace adr {
 // scaling.
 
 // Complex Givens rotation with real cosine: [c s; -conj(s) c] [a; b] = [r; 0].
-__device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2& s, double2& r) {
+__host__ __device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2& s, double2& r) {
   const double a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y;
   if (b2 == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); r = a; return; }
   if (a2 == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); r = b; return; }
   const double n2 = a2 + b2;
-  const double ia = rsqrt(a2), inu = rsqrt(n2);   // 1/|a|, 1/nu
+  const double ia = arnoldi_rsqrt(a2), inu = arnoldi_rsqrt(n2);   // 1/|a|, 1/nu
   c = (a2 * ia) * inu;
   const double2 ph = make_double2(a.x * ia, a.y * ia);
   const double2 cb = make_double2(b.x * inu, -b.y * inu);
@@ -32,13 +44,13 @@ __device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2&
 }
 
 // sqrt(v) and 1/sqrt(v) for v >= 0 (both 0 at 0; a NaN stays NaN in the first).
-__device__ __forceinline__ void sqrt_pair(double v, double& root, double& inv) {
-  inv = v > 0.0 ? rsqrt(v) : 0.0;
+__host__ __device__ __forceinline__ void sqrt_pair(double v, double& root, double& inv) {
+  inv = v > 0.0 ? arnoldi_rsqrt(v) : 0.0;
   root = v * inv;
 }
 
 // |h|^2 - sum_{i<k} |c_i|^2 with two interleaved partial sums (half the chain).
-__device__ __forceinline__ double pythagoras_remainder(double s2, const double2* c, int k) {
+__host__ __device__ __forceinline__ double pythagoras_remainder(double s2, const double2* c, int k) {
   double t0 = 0.0, t1 = 0.0;
   int i = 0;
   for (; i + 1 < k; i += 2) {
@@ -50,7 +62,7 @@ __device__ __forceinline__ double pythagoras_remainder(double s2, const double2*
 }
 
 // Arnoldi column j from ha + hb and |w|^2, Givens update (one thread).
-__device__ __forceinline__ void arnoldi_column_dev(ArnoldiState st, int j, const double2* ha, const double2* hb, double nrm2) {
+__host__ __device__ __forceinline__ void arnoldi_column_dev(ArnoldiState st, int j, const double2* ha, const double2* hb, double nrm2) {
   const int m1 = st.m + 1;
   double2* H = st.H + (int64_t)j * m1;
   if (st.iscal[kIScalStop] >= 0) {
@@ -91,7 +103,7 @@ __device__ __forceinline__ void arnoldi_column_dev(ArnoldiState st, int j, const
 
 // y = R^{-1} g for the leading k x k block of the rotated Hessenberg matrix
 // (k is cut to the breakdown or the convergence column if there was one).
-__device__ __forceinline__ void backsolve_dev(ArnoldiState st, int k) {
+__host__ __device__ __forceinline__ void backsolve_dev(ArnoldiState st, int k) {
   const int m1 = st.m + 1;
   const int stop = st.iscal[kIScalStop];
   if (stop >= 0 && stop < k) k = stop;
@@ -116,7 +128,7 @@ __device__ __forceinline__ void backsolve_dev(ArnoldiState st, int k) {
 // keeps the single pass (hb = 0, Arnoldi column j, reciprocal norm in nrm2,
 // ha[k].y = 0, and on the last step the back substitution over `finish`
 // columns); below it, ha[k].y = 1 requests the second pass.
-__device__ __forceinline__ void coarse_select_dev(double2* ha, double2* hb, int k, double eta2, ArnoldiState st, int j,
+__host__ __device__ __forceinline__ void coarse_select_dev(double2* ha, double2* hb, int k, double eta2, ArnoldiState st, int j,
                                                   int finish, double2* nrm2) {
   const double s2 = ha[k].x;
   double t = pythagoras_remainder(s2, ha, k);
@@ -136,7 +148,7 @@ __device__ __forceinline__ void coarse_select_dev(double2* ha, double2* hb, int 
 }
 // After the second pass: hb[0..k) = V^H w', hb[k].x = |w'|^2 with w' = w - V ha;
 // |w' - V hb|^2 = |w'|^2 - |hb|^2 (hb is at rounding level, no cancellation).
-__device__ __forceinline__ void coarse_reorth_dev(const double2* ha, const double2* hb, int k, ArnoldiState st, int j,
+__host__ __device__ __forceinline__ void coarse_reorth_dev(const double2* ha, const double2* hb, int k, ArnoldiState st, int j,
                                                   int finish, double2* nrm2) {
   double t = pythagoras_remainder(hb[k].x, hb, k);
   if (!(t > 0.0)) t = t == t ? 0.0 : t;

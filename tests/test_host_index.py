@@ -38,3 +38,20 @@ def test_double_float_transformations(tmp_path):
                     os.path.join(HERE, "native", "df_check.cu")], check=True, capture_output=True)
     out = subprocess.run([exe], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
+def test_arnoldi_scalar_helpers(tmp_path):
+    """The single-thread parts of the GMRES iterations (complex Givens
+    rotations, the Hessenberg column update with its running residual
+    estimate, the back substitution, the breakdown stop and the selective
+    second-pass decision from Pythagoras), compiled for the host from the
+    library's own header, against a modified Gram-Schmidt least-squares
+    solve in long double (Sec. 3.1: FGMRES and the coarsest GMRES)."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "krylov_check")
+    subprocess.run([nvcc, "-std=c++17", "-I" + os.path.join(ROOT, "include"), "-o", exe,
+                    os.path.join(HERE, "native", "krylov_check.cu")], check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
